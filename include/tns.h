@@ -1,0 +1,177 @@
+/*
+ * tns.h -- C ABI of the GB300 two-site DMRG H_eff*psi engine.
+ *
+ * The engine implements the projected superblock product of two-site DMRG for
+ * the general long-range Hamiltonian of Eq. (1) (Sec. III) under U(1)xU(1)
+ * symmetry (particle number n, 2*S_z).  With the two dots' local spaces split
+ * into one-dimensional sectors, H_eff*psi reduces to a sum of products
+ * B += alpha * sum_i L_i A R_i^T (Eq. 2), one per symmetry block and per
+ * left/right operator pair; the operators come from normal/complementary
+ * operator partial summation (Sec. III.A.2, "Independent operational tasks").
+ *
+ * Conventions
+ *  - All functions return TNS_OK (0) or a negative TNS_ERR_* code; nothing
+ *    aborts or throws across the ABI.  tns_last_error() describes the last
+ *    failure of a context.
+ *  - Orbitals 0..N-1, spin-orbital p = 2*i + s (s = 0 up, 1 down), Jordan-
+ *    Wigner order (0up, 0dn, 1up, ...).  Site basis |0>,|up>,|dn>,|updn> with
+ *    |updn> = c+_up c+_dn |0>.  Quantum number (n, two_sz) = (0,0),(1,1),
+ *    (1,-1),(2,0) per site state.
+ *  - Bond b (0..N) is labelled by the quantum numbers of orbitals 0..b-1
+ *    ("left counted").
+ *  - Host pointers are read during the call and never retained; the caller
+ *    keeps ownership.  Device pointers passed to tns_heff_apply are owned by
+ *    the caller and must stay valid until the call's work on the context's
+ *    stream has finished (all entry points synchronise the stream before
+ *    returning, except where stated).
+ *  - One context is bound to one CUDA device and one stream; a context must
+ *    not be used from two host threads at once.
+ */
+#ifndef TNS_H
+#define TNS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TNS_OK 0
+#define TNS_ERR_ARG (-1)            /* invalid argument (size, index, symmetry of v, ...) */
+#define TNS_ERR_STATE (-2)          /* call made out of order */
+#define TNS_ERR_OOM (-3)            /* device (or host) allocation failed */
+#define TNS_ERR_NOCONV (-4)         /* Davidson did not reach the tolerance; best estimate kept */
+#define TNS_ERR_DEVICE_TIMEOUT (-5) /* a bounded device wait gave up; context stays usable */
+#define TNS_ERR_CUDA (-6)           /* a CUDA runtime call failed */
+
+/* arithmetic of the sector GEMMs in tns_heff_apply */
+#define TNS_FP64 0    /* native FP64 (DFMA) */
+#define TNS_TF32 1    /* tcgen05 kind::tf32, FP32 accumulation */
+#define TNS_BF16X3 2  /* split-BF16 hi/lo, 3 products, FP32 accumulation */
+
+typedef struct tns_ctx tns_ctx;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (NULL: the context creates and owns a non-blocking stream).  *out is set on
+ * success. */
+int tns_create(tns_ctx** out, int device, void* cuda_stream);
+
+/* Release every device and host resource of the context.  NULL is ignored. */
+void tns_destroy(tns_ctx* ctx);
+
+/* Text of the last error of this context ("" if none).  Valid until the next
+ * call on the same context. */
+const char* tns_last_error(const tns_ctx* ctx);
+
+/* Integrals of Eq. (1) (Sec. III): h[i*N+j] = h_ij (symmetric) and
+ * v[((i*N+j)*N+k)*N+l] = (ij|kl) in chemist order with the 8-fold symmetry;
+ * e_core is added to every energy.  Both arrays are host, row-major, copied.
+ * Returns TNS_ERR_ARG if N < 2, N > 128, h is not symmetric or v breaks the
+ * 8-fold symmetry by more than 1e-12 (absolute). */
+int tns_load_integrals(tns_ctx* ctx, int N, const double* h, const double* v, double e_core);
+
+/* Initial MPS in the (n_elec, two_sz) sector with bond dimension at most D
+ * (D sets the accuracy, Sec. III).  Every bond gets all symmetry sectors the
+ * sector can reach, with dims bounded by the Schmidt rank and scaled to D;
+ * site tensors are 0/1 right-canonical isometries (each right basis state is a
+ * distinct determinant), chosen with a seed-driven counter-based shuffle.
+ * Requires tns_load_integrals.  TNS_ERR_ARG for an unreachable sector. */
+int tns_mps_init(tns_ctx* ctx, int N, int n_elec, int two_sz, int D, unsigned long long seed);
+
+/* Replace the MPS by a caller-given one (import / restart).  First
+ * tns_mps_define(N, n_elec, two_sz, D); then, for every bond b in 0..N,
+ * tns_mps_set_bond(b, nsec, sectors, dims) with sectors = nsec (n, two_sz)
+ * pairs (left counted, strictly increasing by (n, two_sz)) and dims = nsec
+ * positive dimensions; then, for every site b in 0..N-1, tns_mps_set_site(b,
+ * blocks, len) where `blocks` concatenates, for each bond-b sector q_l in bond
+ * order and each site state s = 0..3 whose q_l+qn(s) is a bond-(b+1) sector,
+ * the dim(q_l) x dim(q_l+qn(s)) row-major block (len = total doubles).
+ * Site tensors left of the two-site step used must be left-canonical and
+ * those right of it right-canonical for H_eff to be the projected
+ * Hamiltonian; the arithmetic of tns_build_env / tns_heff_apply does not
+ * depend on it.  tns_mps_get_site copies the same layout back to the host
+ * (len must equal the size; pass blocks=NULL to query it in *len_out). */
+int tns_mps_define(tns_ctx* ctx, int N, int n_elec, int two_sz, int D);
+int tns_mps_set_bond(tns_ctx* ctx, int bond, int nsec, const int* sectors, const int* dims);
+int tns_mps_set_site(tns_ctx* ctx, int site, const double* blocks, long long len);
+int tns_mps_get_bond(tns_ctx* ctx, int bond, int* nsec, int* sectors, int* dims, int cap);
+int tns_mps_get_site(tns_ctx* ctx, int site, double* blocks, long long len, long long* len_out);
+
+/* Build the left block of orbitals 0..site-1 and the right block of orbitals
+ * site+2..N-1 (blocking + renormalisation, Sec. III; complementary operator
+ * partial sums, Sec. III.A.2), then the operator table x task table of the
+ * two-site step (site, site+1) (Sec. III.A.2: operator-table rows, task-table
+ * rows, position index).  Blocks already built for the current MPS are
+ * reused.  0 <= site <= N-2. */
+int tns_build_env(tns_ctx* ctx, int site);
+
+/* Layout of the two-site wavefunction at step (site, site+1), valid after
+ * tns_build_env(site).  *desc points to n_blocks rows of 9 int64 values
+ * (n_l, two_sz_l, s1, s2, n_r, two_sz_r, m, n, offset): q_l = (n_l, two_sz_l)
+ * is a bond-`site` sector (left counted), q_r = (n_r, two_sz_r) the particle
+ * content of orbitals site+2..N-1, the block is m x n row-major at element
+ * `offset` of a vector of *length doubles.  Blocks are ordered by (q_l in
+ * bond order, s1, s2, q_r).  The pointer stays valid until the next
+ * tns_build_env or MPS change. */
+int tns_psi_layout(tns_ctx* ctx, int site, int* n_blocks, const long long** desc, long long* length);
+
+/* Y = H_eff X at step (site, site+1) (Eq. 2 summed over all operator pairs and
+ * symmetry blocks; Alg. 2 computes the same sums).  X and Y are DEVICE
+ * pointers to nvec vectors of `length` doubles each (vector j at offset
+ * j*length), in the layout of tns_psi_layout; they must not overlap.  Y is
+ * overwritten.  precision: TNS_FP64, TNS_TF32 or TNS_BF16X3 (the latter two
+ * run the sector products on tensor cores with FP32 accumulation).  Requires
+ * tns_build_env(site).  Runs on the context stream and synchronises it. */
+int tns_heff_apply(tns_ctx* ctx, int site, const double* X, double* Y, int nvec, int precision);
+
+/* Diagonal of H_eff at step (site, site+1) into the DEVICE vector diag
+ * (length doubles).  Used as the Davidson preconditioner. */
+int tns_heff_diag(tns_ctx* ctx, int site, double* diag);
+
+/* Lowest eigenpair of H_eff at step (site, site+1) by block Davidson on the
+ * device (FP64 orthogonalisation, Rayleigh quotient and residual).  X is a
+ * DEVICE vector of `length` doubles: on entry the start vector (zero vector:
+ * a default start is used), on exit the normalised eigenvector.  *energy
+ * receives the eigenvalue + e_core, *iters the number of matrix-vector
+ * products.  precision as in tns_heff_apply; reduced precisions are
+ * corrected with FP64 residuals.  TNS_ERR_NOCONV if tol is not reached in
+ * max_iter products (X and *energy hold the best estimate). */
+int tns_davidson(tns_ctx* ctx, int site, double* X, double tol, int max_iter, int precision,
+                 double* energy, int* iters);
+
+typedef struct tns_sweep_opts {
+  int nsweeps;          /* full sweeps (left->right then right->left) */
+  int D;                /* bond dimension cap (<= the D of the MPS) */
+  double tol;           /* Davidson residual tolerance (2-norm, normalised vector) */
+  int max_iter;         /* Davidson matrix-vector products per step */
+  int precision;        /* TNS_FP64 / TNS_TF32 / TNS_BF16X3 */
+  double cutoff;        /* singular values <= cutoff are dropped (e.g. 1e-14) */
+  int verbose;          /* print one line per step on stdout */
+} tns_sweep_opts;
+
+typedef struct tns_sweep_stats {
+  double energy;            /* lowest energy seen in the last sweep (incl. e_core) */
+  double max_discarded;     /* largest discarded weight of the last sweep */
+  long long matvecs;        /* H_eff*psi products over the whole call */
+  double heff_flops;        /* useful FP64-equivalent flops of those products */
+  double heff_seconds;      /* device time inside H_eff*psi */
+  double env_seconds;       /* device time of environment builds */
+  double svd_seconds;       /* device time of truncations */
+  double seconds;           /* wall time of the call */
+  int steps;                /* two-site steps done */
+  int max_bond;             /* largest bond dimension after the call */
+} tns_sweep_stats;
+
+/* Two-site DMRG sweeps over the current MPS (tns_mps_init or an import):
+ * per step environment build, Davidson on H_eff, SVD truncation to at most D
+ * states, renormalisation.  *energy_out receives the final energy.  stats is
+ * optional (NULL). */
+int tns_sweep(tns_ctx* ctx, const tns_sweep_opts* opts, double* energy_out, tns_sweep_stats* stats);
+
+/* Useful FP64-equivalent flop count of one tns_heff_apply(site) for nvec = 1:
+ * sum over products of p * min(2mr(n+q), 2qn(m+r)) (best chain order, the
+ * matrix-chain choice of Sec. III.B), and the number of block products. */
+int tns_heff_flops(tns_ctx* ctx, int site, double* flops, long long* nproducts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNS_H */

@@ -1,0 +1,222 @@
+"""ctypes binding of the C ABI in include/tns.h (argument marshalling only).
+
+Every computation happens inside the shared library; this module converts
+Python arguments to pointers and sizes and turns error codes into
+exceptions.  Device pointers are plain integers (e.g. ``tensor.data_ptr()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+TNS_FP64, TNS_TF32, TNS_BF16X3 = 0, 1, 2
+ERRORS = {-1: "TNS_ERR_ARG", -2: "TNS_ERR_STATE", -3: "TNS_ERR_OOM", -4: "TNS_ERR_NOCONV",
+          -5: "TNS_ERR_DEVICE_TIMEOUT", -6: "TNS_ERR_CUDA"}
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_LIB = os.path.join(HERE, "libtns.so")
+
+# every entry point of include/tns.h
+SYMBOLS = ["create", "destroy", "last_error", "load_integrals", "mps_init", "mps_define",
+           "mps_set_bond", "mps_set_site", "mps_get_bond", "mps_get_site", "build_env",
+           "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops"]
+
+
+class TnsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SweepOpts(C.Structure):
+    _fields_ = [("nsweeps", C.c_int), ("D", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
+                ("precision", C.c_int), ("cutoff", C.c_double), ("verbose", C.c_int)]
+
+
+class SweepStats(C.Structure):
+    _fields_ = [("energy", C.c_double), ("max_discarded", C.c_double), ("matvecs", C.c_longlong),
+                ("heff_flops", C.c_double), ("heff_seconds", C.c_double), ("env_seconds", C.c_double),
+                ("svd_seconds", C.c_double), ("seconds", C.c_double), ("steps", C.c_int),
+                ("max_bond", C.c_int)]
+
+
+_LIBS = {}
+
+
+def load_library(path: str = DEFAULT_LIB, prefix: str = "tns_"):
+    key = (path, prefix)
+    if key in _LIBS:
+        return _LIBS[key]
+    if not os.path.exists(path):
+        raise OSError(f"shared library {path} not found: build it first "
+                      "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    f = lambda n: getattr(lib, prefix + n)
+    vp, ip, dp, llp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_longlong)
+    sig = {
+        "create": (C.c_int, [C.POINTER(vp), C.c_int, vp]),
+        "destroy": (None, [vp]),
+        "last_error": (C.c_char_p, [vp]),
+        "load_integrals": (C.c_int, [vp, C.c_int, dp, dp, C.c_double]),
+        "mps_init": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_ulonglong]),
+        "mps_define": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "mps_set_bond": (C.c_int, [vp, C.c_int, C.c_int, ip, ip]),
+        "mps_set_site": (C.c_int, [vp, C.c_int, dp, C.c_longlong]),
+        "mps_get_bond": (C.c_int, [vp, C.c_int, ip, ip, ip, C.c_int]),
+        "mps_get_site": (C.c_int, [vp, C.c_int, dp, C.c_longlong, llp]),
+        "build_env": (C.c_int, [vp, C.c_int]),
+        "psi_layout": (C.c_int, [vp, C.c_int, ip, C.POINTER(llp), llp]),
+        "heff_apply": (C.c_int, [vp, C.c_int, vp, vp, C.c_int, C.c_int]),
+        "heff_diag": (C.c_int, [vp, C.c_int, vp]),
+        "davidson": (C.c_int, [vp, C.c_int, vp, C.c_double, C.c_int, C.c_int, dp, ip]),
+        "sweep": (C.c_int, [vp, C.POINTER(SweepOpts), dp, C.POINTER(SweepStats)]),
+        "heff_flops": (C.c_int, [vp, C.c_int, dp, llp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = f(name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIBS[key] = (lib, prefix)
+    return _LIBS[key]
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Context:
+    """One engine context (one device, one stream)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None, path: str = DEFAULT_LIB,
+                 prefix: str = "tns_"):
+        self._lib, self._pfx = load_library(path, prefix)
+        h = C.c_void_p()
+        rc = self._fn("create")(C.byref(h), device, C.c_void_p(stream) if stream else None)
+        if rc != 0:
+            raise TnsError(rc, "create failed")
+        self._h = h
+
+    def _fn(self, name):
+        return getattr(self._lib, self._pfx + name)
+
+    def _check(self, rc):
+        if rc != 0:
+            msg = self._fn("last_error")(self._h).decode()
+            raise TnsError(rc, msg)
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._fn("destroy")(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- problem definition -------------------------------------------------
+    def load_integrals(self, h, v, e_core: float = 0.0):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        self._check(self._fn("load_integrals")(self._h, h.shape[0], _dptr(h), _dptr(v), float(e_core)))
+
+    def mps_init(self, N, n_elec, two_sz, D, seed=0):
+        self._check(self._fn("mps_init")(self._h, N, n_elec, two_sz, D, seed))
+
+    def mps_import(self, N, n_elec, two_sz, D, bonds, sites):
+        """bonds[b] = [((n, 2sz), dim)], sites[b] = {(q_l, s): array} (see synth)."""
+        self._check(self._fn("mps_define")(self._h, N, n_elec, two_sz, D))
+        for b, bond in enumerate(bonds):
+            sec = np.array([x for (q, d) in bond for x in q], dtype=np.int32)
+            dims = np.array([d for (q, d) in bond], dtype=np.int32)
+            self._check(self._fn("mps_set_bond")(self._h, b, len(bond), sec.ctypes.data_as(C.POINTER(C.c_int)),
+                                                  dims.ctypes.data_as(C.POINTER(C.c_int))))
+        qn = [(0, 0), (1, 1), (1, -1), (2, 0)]
+        for b in range(N):
+            right = {q for q, _ in bonds[b + 1]}
+            parts = []
+            for ql, dl in bonds[b]:
+                for s in range(4):
+                    qr = (ql[0] + qn[s][0], ql[1] + qn[s][1])
+                    if qr in right:
+                        parts.append(np.ascontiguousarray(sites[b][(ql, s)], dtype=np.float64).ravel())
+            data = np.concatenate(parts) if parts else np.zeros(0)
+            self._check(self._fn("mps_set_site")(self._h, b, _dptr(data), data.size))
+
+    def get_bond(self, b):
+        n = C.c_int()
+        self._check(self._fn("mps_get_bond")(self._h, b, C.byref(n), None, None, 0))
+        sec = np.zeros(2 * n.value, dtype=np.int32)
+        dims = np.zeros(n.value, dtype=np.int32)
+        self._check(self._fn("mps_get_bond")(self._h, b, C.byref(n), sec.ctypes.data_as(C.POINTER(C.c_int)),
+                                              dims.ctypes.data_as(C.POINTER(C.c_int)), n.value))
+        return [((int(sec[2 * i]), int(sec[2 * i + 1])), int(dims[i])) for i in range(n.value)]
+
+    def get_site(self, b):
+        n = C.c_longlong()
+        self._check(self._fn("mps_get_site")(self._h, b, None, 0, C.byref(n)))
+        out = np.zeros(n.value)
+        self._check(self._fn("mps_get_site")(self._h, b, _dptr(out), n.value, None))
+        return out
+
+    # -- two-site step --------------------------------------------------------
+    def build_env(self, site):
+        self._check(self._fn("build_env")(self._h, site))
+
+    def psi_layout(self, site):
+        nb = C.c_int()
+        p = C.POINTER(C.c_longlong)()
+        ln = C.c_longlong()
+        self._check(self._fn("psi_layout")(self._h, site, C.byref(nb), C.byref(p), C.byref(ln)))
+        desc = np.ctypeslib.as_array(p, shape=(nb.value * 9,)).reshape(nb.value, 9).copy()
+        return desc, ln.value
+
+    def heff_apply_ptr(self, site, x_ptr: int, y_ptr: int, nvec: int = 1, precision: int = TNS_FP64):
+        self._check(self._fn("heff_apply")(self._h, site, C.c_void_p(x_ptr), C.c_void_p(y_ptr), nvec, precision))
+
+    def heff_diag_ptr(self, site, d_ptr: int):
+        self._check(self._fn("heff_diag")(self._h, site, C.c_void_p(d_ptr)))
+
+    def heff_flops(self, site):
+        f = C.c_double()
+        n = C.c_longlong()
+        self._check(self._fn("heff_flops")(self._h, site, C.byref(f), C.byref(n)))
+        return f.value, n.value
+
+    def davidson_ptr(self, site, x_ptr: int, tol=1e-8, max_iter=200, precision=TNS_FP64):
+        e = C.c_double()
+        it = C.c_int()
+        rc = self._fn("davidson")(self._h, site, C.c_void_p(x_ptr), tol, max_iter, precision, C.byref(e), C.byref(it))
+        if rc not in (0, -4):
+            self._check(rc)
+        return e.value, it.value, rc == 0
+
+    def sweep(self, nsweeps, D, tol=1e-8, max_iter=100, precision=TNS_FP64, cutoff=1e-14, verbose=False):
+        o = SweepOpts(nsweeps, D, tol, max_iter, precision, cutoff, int(verbose))
+        e = C.c_double()
+        st = SweepStats()
+        self._check(self._fn("sweep")(self._h, C.byref(o), C.byref(e), C.byref(st)))
+        return e.value, st
+
+
+def blocks_to_vector(desc, length, blocks: dict) -> np.ndarray:
+    """Pack {(q_l, s1, s2, q_r): array} into the flat layout of psi_layout."""
+    x = np.zeros(length)
+    for row in desc:
+        nl, sl, s1, s2, nr, sr, m, n, off = (int(v) for v in row)
+        key = ((nl, sl), s1, s2, (nr, sr))
+        if key in blocks:
+            x[off:off + m * n] = np.asarray(blocks[key]).ravel()
+    return x
+
+
+def vector_to_blocks(desc, x) -> dict:
+    out = {}
+    for row in desc:
+        nl, sl, s1, s2, nr, sr, m, n, off = (int(v) for v in row)
+        out[((nl, sl), s1, s2, (nr, sr))] = np.asarray(x[off:off + m * n]).reshape(m, n)
+    return out

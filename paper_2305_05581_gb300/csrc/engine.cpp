@@ -1,0 +1,1451 @@
+// engine.cpp -- integrals, MPS, operator catalogues, enlarged operators and
+// the work lists of the environment build and of H_eff*psi.
+//
+// Derivation of the enlarged operators (blocking).  For two adjacent parts
+// of the orbital chain, a product of full-space operators (X)_first (Y)_second
+// equals (X P_first^{|Y|}) (x) Y with block-local operators (Jordan-Wigner
+// string inside each part), P = (-1)^n and |Y| the fermionic parity of Y.
+// The two-site Hamiltonian is split at the bond between LL = L + dot k and
+// RR = dot k+1 + R (normal operators left, complementary right):
+//   H = H_LL + H_RR + sum_{a in LL}[c+_a S_a + h.c.] + sum_{x in RR}[T_x c_x + h.c.]
+//       + sum_{a<b in LL}[A_ab P_ab + h.c.] + sum_{a,b in LL} B_ab Q_ab,
+// and each LL (RR) operator is expanded over L (R) operators and 4x4 dot
+// operators with the same rule; the dot factors are scalars per dot block
+// (Sec. III.A.2), which gives the tasks B += alpha L A R^T of Eq. (2).
+#include "engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+namespace tns {
+
+const QN kSiteQN[4] = {{0, 0}, {1, 1}, {1, -1}, {2, 0}};
+
+// ---------------------------------------------------------------------------
+// dot operators (site basis |0>,|up>,|dn>,|updn>, |updn> = c+_up c+_dn |0>)
+// ---------------------------------------------------------------------------
+namespace {
+struct DotOps {
+  M4 cd[2], c[2], P, I;
+  DotOps() {
+    cd[0].a[1][0] = 1.0;   // c+_up |0>  = |up>
+    cd[0].a[3][2] = 1.0;   // c+_up |dn> = |updn>
+    cd[1].a[2][0] = 1.0;   // c+_dn |0>  = |dn>
+    cd[1].a[3][1] = -1.0;  // c+_dn |up> = -|updn>
+    c[0] = cd[0].T();
+    c[1] = cd[1].T();
+    P.a[0][0] = 1.0;
+    P.a[1][1] = -1.0;
+    P.a[2][2] = -1.0;
+    P.a[3][3] = 1.0;
+    I = M4::eye();
+  }
+};
+const DotOps& dot() {
+  static DotOps d;
+  return d;
+}
+inline int spin2(int p) { return (p & 1) ? -1 : 1; }
+inline double sgn_n(int n) { return (n & 1) ? -1.0 : 1.0; }
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// layouts and catalogues
+// ---------------------------------------------------------------------------
+void make_layout(const Basis& b, QN dq, Layout& L) {
+  L.dq = dq;
+  L.in.clear();
+  L.out.clear();
+  L.off.clear();
+  L.size = 0;
+  L.blk_of_in.assign(b.size(), -1);
+  for (int i = 0; i < b.size(); ++i) {
+    int o = b.find(b.q[i] + dq);
+    if (o < 0) continue;
+    L.blk_of_in[i] = (int)L.in.size();
+    L.in.push_back(i);
+    L.out.push_back(o);
+    L.off.push_back(L.size);
+    L.size += (long long)b.dim[o] * b.dim[i];
+  }
+}
+
+static int blk_of_out(const Basis& b, const Layout& L, int out) {
+  int in = b.find(b.q[out] - L.dq);
+  return in < 0 ? -1 : L.blk_of_in[in];
+}
+
+int Catalogue::layout_for(QN dq) {
+  auto it = layout_of.find(dq);
+  if (it != layout_of.end()) return it->second;
+  Layout L;
+  make_layout(basis, dq, L);
+  layouts.push_back(L);
+  int id = (int)layouts.size() - 1;
+  layout_of[dq] = id;
+  return id;
+}
+
+int Catalogue::add_op(int kind, int i, int j, QN dq) {
+  CatOp o;
+  o.kind = kind;
+  o.i = i;
+  o.j = j;
+  o.dq = dq;
+  o.layout = layout_for(dq);
+  o.off = 0;
+  ops.push_back(o);
+  int id = (int)ops.size() - 1;
+  index[key(kind, i, j)] = id;
+  return id;
+}
+
+void Catalogue::assign_offsets() {
+  long long o = 0;
+  for (auto& op : ops) {
+    op.off = o;
+    o += layouts[op.layout].size;
+  }
+  size = o;
+}
+
+static QN dq_of(int kind, int i, int j) {
+  switch (kind) {
+    case K_H: return {0, 0};
+    case K_C: return {1, spin2(i)};
+    case K_A: return {2, spin2(i) + spin2(j)};
+    case K_B: return {0, spin2(i) - spin2(j)};
+    case K_T: return {1, spin2(i)};
+    case K_S: return {-1, -spin2(i)};
+    case K_P: return {-2, -(spin2(i) + spin2(j))};
+    case K_Q: return {0, spin2(j) - spin2(i)};
+  }
+  return {0, 0};
+}
+
+// ---------------------------------------------------------------------------
+// engine basics
+// ---------------------------------------------------------------------------
+Engine::~Engine() {
+  for (auto& c : Lcat_) free_cat(c);
+  for (auto& c : Rcat_) free_cat(c);
+  free_side(step_.L);
+  free_side(step_.R);
+  for (auto& s : sites_)
+    if (s.d) be_->release(s.d);
+}
+
+void Engine::free_cat(Catalogue& c) {
+  if (c.d) be_->release(c.d);
+  c.d = nullptr;
+  c.valid = false;
+  c.ops.clear();
+  c.index.clear();
+  c.layouts.clear();
+  c.layout_of.clear();
+  c.size = 0;
+}
+
+void Engine::free_side(Side& s) {
+  if (s.d) be_->release(s.d);
+  s.d = nullptr;
+  s.size = 0;
+  s.exprs.clear();
+  s.eops.clear();
+  s.eop_index.clear();
+  s.mats.clear();
+}
+
+int Engine::alloc_cat(Catalogue& c, std::string& err) {
+  c.assign_offsets();
+  if (c.d) be_->release(c.d);
+  c.d = be_->alloc(std::max(c.size, 1LL));
+  if (!c.d) {
+    err = "device allocation of " + std::to_string(c.size * 8) + " bytes failed (operator catalogue)";
+    return -3;
+  }
+  return 0;
+}
+
+double Engine::t(int p, int q) const {
+  if ((p & 1) != (q & 1)) return 0.0;
+  return h_[(p >> 1) * N_ + (q >> 1)];
+}
+
+double Engine::W(int p, int q, int r, int s) const {
+  if ((p & 1) != (s & 1) || (q & 1) != (r & 1)) return 0.0;
+  const long long N = N_;
+  return v_[(((long long)(p >> 1) * N + (s >> 1)) * N + (q >> 1)) * N + (r >> 1)];
+}
+
+int Engine::load_integrals(int N, const double* h, const double* v, double e_core, std::string& err) {
+  if (N < 2 || N > 128 || !h || !v) {
+    err = "load_integrals: need 2 <= N <= 128 and non-null h, v";
+    return -1;
+  }
+  const long long n = N;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j)
+      if (std::fabs(h[i * N + j] - h[j * N + i]) > 1e-12) {
+        err = "load_integrals: h is not symmetric";
+        return -1;
+      }
+  auto V = [&](long long i, long long j, long long k, long long l) { return v[((i * n + j) * n + k) * n + l]; };
+  for (long long i = 0; i < n; ++i)
+    for (long long j = 0; j < n; ++j)
+      for (long long k = 0; k < n; ++k)
+        for (long long l = 0; l < n; ++l) {
+          double x = V(i, j, k, l);
+          if (std::fabs(x - V(j, i, k, l)) > 1e-12 || std::fabs(x - V(i, j, l, k)) > 1e-12 ||
+              std::fabs(x - V(k, l, i, j)) > 1e-12) {
+            err = "load_integrals: v lacks the 8-fold permutational symmetry";
+            return -1;
+          }
+        }
+  if (have_mps_ && N != N_) have_mps_ = false;
+  N_ = N;
+  h_.assign(h, h + n * n);
+  v_.assign(v, v + n * n * n * n);
+  e_core_ = e_core;
+  have_ints_ = true;
+  for (auto& c : Lcat_) free_cat(c);
+  for (auto& c : Rcat_) free_cat(c);
+  step_.valid = false;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// MPS
+// ---------------------------------------------------------------------------
+int Engine::mps_define(int N, int n_elec, int two_sz, int D, std::string& err) {
+  if (!have_ints_) {
+    err = "mps_define: load integrals first";
+    return -2;
+  }
+  if (N != N_ || D < 1 || n_elec < 0 || n_elec > 2 * N || std::abs(two_sz) > n_elec ||
+      ((n_elec + two_sz) & 1)) {
+    err = "mps_define: inconsistent N / n_elec / two_sz / D";
+    return -1;
+  }
+  for (auto& s : sites_)
+    if (s.d) be_->release(s.d);
+  sites_.assign(N, Site());
+  bonds_.assign(N + 1, Basis());
+  target_ = {n_elec, two_sz};
+  D_ = D;
+  for (auto& c : Lcat_) free_cat(c);
+  for (auto& c : Rcat_) free_cat(c);
+  Lcat_.assign(N + 1, Catalogue());
+  Rcat_.assign(N + 1, Catalogue());
+  step_.valid = false;
+  have_mps_ = true;
+  return 0;
+}
+
+void Engine::set_bond_basis(int b, const Basis& basis) { bonds_[b] = basis; }
+
+int Engine::mps_set_bond(int b, int nsec, const int* sec, const int* dims, std::string& err) {
+  if (!have_mps_ || b < 0 || b > N_ || nsec < 1 || !sec || !dims) {
+    err = "mps_set_bond: bad bond index or arguments";
+    return -1;
+  }
+  Basis B;
+  for (int i = 0; i < nsec; ++i) {
+    QN q{sec[2 * i], sec[2 * i + 1]};
+    if (dims[i] < 1 || (i > 0 && !(B.q.back() < q))) {
+      err = "mps_set_bond: sectors must be strictly increasing with positive dims";
+      return -1;
+    }
+    B.add(q, dims[i]);
+  }
+  bonds_[b] = B;
+  invalidate_left_from(b);
+  invalidate_right_from(b);
+  return 0;
+}
+
+int Engine::site_from_host(int b, const std::vector<SiteBlock>& blocks, const std::vector<double>& data,
+                           std::string& err) {
+  Site& S = sites_[b];
+  if (S.d) be_->release(S.d);
+  S.blocks = blocks;
+  S.index.assign(bonds_[b].size() * 4, -1);
+  long long o = 0;
+  for (size_t i = 0; i < S.blocks.size(); ++i) {
+    S.blocks[i].off = o;
+    o += (long long)S.blocks[i].m * S.blocks[i].n;
+    S.index[S.blocks[i].ql * 4 + S.blocks[i].s] = (int)i;
+  }
+  S.size = o;
+  S.d = be_->alloc(std::max(o, 1LL));
+  if (!S.d) {
+    err = "device allocation failed (site tensor)";
+    return -3;
+  }
+  if (!data.empty()) be_->upload(S.d, data.data(), o);
+  return 0;
+}
+
+static void site_layout(const Basis& l, const Basis& r, std::vector<SiteBlock>& out) {
+  out.clear();
+  for (int i = 0; i < l.size(); ++i)
+    for (int s = 0; s < 4; ++s) {
+      int j = r.find(l.q[i] + kSiteQN[s]);
+      if (j < 0) continue;
+      SiteBlock sb;
+      sb.ql = i;
+      sb.s = s;
+      sb.qr = j;
+      sb.m = l.dim[i];
+      sb.n = r.dim[j];
+      sb.off = 0;
+      out.push_back(sb);
+    }
+}
+
+int Engine::mps_set_site(int b, const double* x, long long len, std::string& err) {
+  if (!have_mps_ || b < 0 || b >= N_ || !x || bonds_[b].size() == 0 || bonds_[b + 1].size() == 0) {
+    err = "mps_set_site: bad site index, or bonds b and b+1 not set";
+    return -1;
+  }
+  std::vector<SiteBlock> blocks;
+  site_layout(bonds_[b], bonds_[b + 1], blocks);
+  long long tot = 0;
+  for (auto& sb : blocks) tot += (long long)sb.m * sb.n;
+  if (tot != len) {
+    err = "mps_set_site: length " + std::to_string(len) + " != expected " + std::to_string(tot);
+    return -1;
+  }
+  std::vector<double> data(x, x + len);
+  int rc = site_from_host(b, blocks, data, err);
+  invalidate_left_from(b + 1);
+  invalidate_right_from(b);
+  return rc;
+}
+
+int Engine::mps_get_site(int b, double* x, long long len, long long* len_out, std::string& err) {
+  if (!have_mps_ || b < 0 || b >= N_ || !sites_[b].d) {
+    err = "mps_get_site: site not set";
+    return -1;
+  }
+  if (len_out) *len_out = sites_[b].size;
+  if (!x) return 0;
+  if (len != sites_[b].size) {
+    err = "mps_get_site: wrong length";
+    return -1;
+  }
+  be_->download(x, sites_[b].d, len);
+  be_->sync();
+  return 0;
+}
+
+// splitmix64: counter-based generator (Steele, Lea, Flood 2014)
+static unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+
+static double count_dets(int nsites, int n, int s2) {
+  if ((n + s2) & 1) return 0.0;
+  int nu = (n + s2) / 2, nd = (n - s2) / 2;
+  if (nu < 0 || nd < 0 || nu > nsites || nd > nsites) return 0.0;
+  auto binom = [](int a, int b) {
+    double r = 1.0;
+    for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+    return r;
+  };
+  return binom(nsites, nu) * binom(nsites, nd);
+}
+
+int Engine::mps_init(int N, int n_elec, int two_sz, int D, unsigned long long seed, std::string& err) {
+  int rc = mps_define(N, n_elec, two_sz, D, err);
+  if (rc) return rc;
+  // sector dims per bond: Schmidt-rank bound, proportional share of D,
+  // then made consistent so every site tensor can be a right isometry
+  std::vector<std::map<QN, long long>> dims(N + 1);
+  for (int b = 0; b <= N; ++b) {
+    std::map<QN, double> full;
+    double tot = 0;
+    for (int n = 0; n <= 2 * b; ++n)
+      for (int s = -b; s <= b; ++s) {
+        double cl = count_dets(b, n, s), cr = count_dets(N - b, n_elec - n, two_sz - s);
+        if (cl > 0 && cr > 0) {
+          full[{n, s}] = std::min(cl, cr);
+          tot += std::min(cl, cr);
+        }
+      }
+    if (full.empty()) {
+      err = "mps_init: target sector unreachable";
+      return -1;
+    }
+    std::map<QN, long long> d;
+    if (tot <= D) {
+      for (auto& kv : full) d[kv.first] = (long long)kv.second;
+    } else {
+      std::vector<std::pair<double, QN>> frac;
+      long long used = 0;
+      for (auto& kv : full) {
+        double share = D * kv.second / tot;
+        long long a = (long long)share;
+        d[kv.first] = a;
+        used += a;
+        frac.push_back({-(share - a), kv.first});
+      }
+      std::sort(frac.begin(), frac.end(), [](const std::pair<double, QN>& x, const std::pair<double, QN>& y) {
+        return x.first < y.first || (x.first == y.first && x.second < y.second);
+      });
+      for (long long i = 0; i < D - used && i < (long long)frac.size(); ++i) d[frac[i].second] += 1;
+    }
+    dims[b] = d;
+  }
+  for (bool changed = true; changed;) {
+    changed = false;
+    for (int b = N - 1; b >= 0; --b)
+      for (auto& kv : dims[b]) {
+        long long avail = 0;
+        for (int s = 0; s < 4; ++s) {
+          auto it = dims[b + 1].find(kv.first + kSiteQN[s]);
+          if (it != dims[b + 1].end()) avail += it->second;
+        }
+        if (kv.second > avail) {
+          kv.second = avail;
+          changed = true;
+        }
+      }
+    for (int b = 1; b <= N; ++b)
+      for (auto& kv : dims[b]) {
+        long long avail = 0;
+        for (int s = 0; s < 4; ++s) {
+          auto it = dims[b - 1].find(kv.first - kSiteQN[s]);
+          if (it != dims[b - 1].end()) avail += it->second;
+        }
+        if (kv.second > avail) {
+          kv.second = avail;
+          changed = true;
+        }
+      }
+  }
+  for (int b = 0; b <= N; ++b) {
+    Basis B;
+    for (auto& kv : dims[b])
+      if (kv.second > 0) B.add(kv.first, (int)kv.second);
+    if (B.size() == 0) {
+      err = "mps_init: empty bond after consistency (D too small)";
+      return -1;
+    }
+    bonds_[b] = B;
+  }
+  // 0/1 right isometries: left state i of sector q picks the i-th column of a
+  // seed-dependent ordering of the (s, right state) pairs
+  for (int b = 0; b < N; ++b) {
+    std::vector<SiteBlock> blocks;
+    site_layout(bonds_[b], bonds_[b + 1], blocks);
+    long long tot = 0;
+    std::vector<long long> boff;
+    for (auto& sb : blocks) {
+      boff.push_back(tot);
+      tot += (long long)sb.m * sb.n;
+    }
+    std::vector<double> data(tot, 0.0);
+    const Basis& L = bonds_[b];
+    for (int i = 0; i < L.size(); ++i) {
+      std::vector<std::pair<unsigned long long, std::pair<int, int>>> cols;  // (key, (block, col))
+      for (size_t bi = 0; bi < blocks.size(); ++bi) {
+        if (blocks[bi].ql != i) continue;
+        for (int c = 0; c < blocks[bi].n; ++c) {
+          unsigned long long key = splitmix64(seed ^ splitmix64(((unsigned long long)b << 40) ^
+                                                               ((unsigned long long)blocks[bi].s << 32) ^
+                                                               (unsigned long long)c));
+          cols.push_back({key, {(int)bi, c}});
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      for (int r = 0; r < L.dim[i]; ++r) {
+        int bi = cols[r].second.first, c = cols[r].second.second;
+        data[boff[bi] + (long long)r * blocks[bi].n + c] = 1.0;
+      }
+    }
+    rc = site_from_host(b, blocks, data, err);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+void Engine::invalidate_left_from(int k) {
+  for (int j = std::max(k, 0); j < (int)Lcat_.size(); ++j) free_cat(Lcat_[j]);
+  step_.valid = false;
+}
+void Engine::invalidate_right_from(int k) {
+  for (int j = 0; j <= k && j < (int)Rcat_.size(); ++j) free_cat(Rcat_[j]);
+  step_.valid = false;
+}
+
+// ---------------------------------------------------------------------------
+// empty blocks
+// ---------------------------------------------------------------------------
+void Engine::empty_left(Catalogue& c) {
+  c = Catalogue();
+  c.left = true;
+  c.len = 0;
+  c.basis.add({0, 0}, 1);
+  c.add_op(K_H, -1, -1, {0, 0});
+  for (int x = 0; x < 2 * N_; ++x) c.add_op(K_T, x, -1, dq_of(K_T, x, -1));
+}
+
+void Engine::empty_right(Catalogue& c) {
+  c = Catalogue();
+  c.left = false;
+  c.len = N_;
+  c.basis.add({0, 0}, 1);
+  c.add_op(K_H, -1, -1, {0, 0});
+  for (int a = 0; a < 2 * N_; ++a) c.add_op(K_S, a, -1, dq_of(K_S, a, -1));
+  for (int a = 0; a < 2 * N_; ++a)
+    for (int b = a + 1; b < 2 * N_; ++b) c.add_op(K_P, a, b, dq_of(K_P, a, b));
+  for (int a = 0; a < 2 * N_; ++a)
+    for (int b = 0; b < 2 * N_; ++b) c.add_op(K_Q, a, b, dq_of(K_Q, a, b));
+}
+
+// ---------------------------------------------------------------------------
+// expressions and enlarged operators
+// ---------------------------------------------------------------------------
+namespace {
+struct Builder {
+  Side& S;
+  const Catalogue& cat;
+  std::map<std::tuple<int, int, int>, int> refs;  // (op, tr, par) -> expr
+  Builder(Side& s, const Catalogue& c) : S(s), cat(c) {}
+
+  QN term_dq(const Term& t) const {
+    if (t.op < 0) return {0, 0};
+    QN d = cat.ops[t.op].dq;
+    return t.tr ? -d : d;
+  }
+  int ref(int op, bool tr = false, int par = 0) {
+    auto key = std::make_tuple(op, (int)tr, par);
+    auto it = refs.find(key);
+    if (it != refs.end()) return it->second;
+    Expr e;
+    e.t.push_back({1.0, op, tr, par});
+    e.dq = term_dq(e.t[0]);
+    S.exprs.push_back(e);
+    int id = (int)S.exprs.size() - 1;
+    refs[key] = id;
+    return id;
+  }
+  int ident(int par = 0) { return ref(-1, false, par); }
+  // linear combination; returns -1 if all coefficients vanish
+  int comb(const std::vector<Term>& ts) {
+    Expr e;
+    for (auto& t : ts)
+      if (t.c != 0.0) e.t.push_back(t);
+    if (e.t.empty()) return -1;
+    e.dq = term_dq(e.t[0]);
+    S.exprs.push_back(e);
+    return (int)S.exprs.size() - 1;
+  }
+};
+
+QN dot_shift(const M4& y) {
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      if (y.a[i][j] != 0.0) return kSiteQN[i] - kSiteQN[j];
+  return {0, 0};
+}
+
+void add_part(EOp& E, const M4& y, int expr) {
+  if (expr < 0 || y.zero()) return;
+  E.parts.push_back({y, expr});
+}
+}  // namespace
+
+static EOp& new_eop(Side& S, int kind, int i, int j) {
+  EOp E;
+  E.kind = kind;
+  E.i = i;
+  E.j = j;
+  S.eops.push_back(E);
+  S.eop_index[Catalogue::key(kind, i, j)] = (int)S.eops.size() - 1;
+  return S.eops.back();
+}
+
+// LL = L (x) dot `site`; L holds orbitals 0..site-1.  Operators of LL are the
+// catalogue of the left block of orbitals 0..site.
+void Engine::build_left_eops(const Catalogue& L, int site, Side& S) {
+  const DotOps& d = dot();
+  Builder B(S, L);
+  const int m0 = 2 * site, m1 = 2 * site + 1;
+  const int ms[2] = {m0, m1};
+  const int M = 2 * N_;
+  std::vector<int> inL;
+  for (int a = 0; a < 2 * site; ++a) inL.push_back(a);
+  auto op = [&](int kind, int i, int j) { return L.find(kind, i, j); };
+
+  // site Hamiltonian (one- and two-body terms on the dot)
+  M4 hs;
+  for (int p : ms)
+    for (int q : ms) hs = hs + (d.cd[p & 1] * d.c[q & 1]).scale(t(p, q));
+  for (int p : ms)
+    for (int q : ms)
+      for (int r : ms)
+        for (int s : ms) {
+          double w = W(p, q, r, s);
+          if (w != 0.0) hs = hs + (d.cd[p & 1] * d.cd[q & 1] * d.c[r & 1] * d.c[s & 1]).scale(0.5 * w);
+        }
+
+  {  // H
+    EOp& E = new_eop(S, K_H, -1, -1);
+    add_part(E, d.I, B.ref(op(K_H, -1, -1)));
+    add_part(E, hs, B.ident());
+    for (int a : inL) {
+      M4 Sa;
+      for (int q : ms) {
+        Sa = Sa + d.c[q & 1].scale(t(a, q));
+        for (int r : ms)
+          for (int u : ms) {
+            double w = W(a, q, r, u);
+            if (w != 0.0) Sa = Sa + (d.cd[q & 1] * d.c[r & 1] * d.c[u & 1]).scale(w);
+          }
+      }
+      int ca = op(K_C, a, -1);
+      add_part(E, Sa, B.ref(ca, false, 1));
+      add_part(E, Sa.T().scale(-1.0), B.ref(ca, true, 1));
+    }
+    for (int m : ms) {
+      int Tm = op(K_T, m, -1);
+      add_part(E, d.c[m & 1], B.ref(Tm, false, 1));
+      add_part(E, d.cd[m & 1].scale(-1.0), B.ref(Tm, true, 1));
+    }
+    for (size_t ai = 0; ai < inL.size(); ++ai)
+      for (size_t bi = ai + 1; bi < inL.size(); ++bi) {
+        int a = inL[ai], b = inL[bi];
+        M4 Pp;
+        for (int r : ms)
+          for (int u : ms) {
+            double w = W(a, b, r, u);
+            if (w != 0.0) Pp = Pp + (d.c[r & 1] * d.c[u & 1]).scale(w);
+          }
+        int Aab = op(K_A, a, b);
+        add_part(E, Pp, B.ref(Aab));
+        add_part(E, Pp.T(), B.ref(Aab, true));
+      }
+    for (int a : inL)
+      for (int b : inL) {
+        M4 Q;
+        for (int q : ms)
+          for (int r : ms) {
+            double w = W(a, q, r, b) - W(a, q, b, r);
+            if (w != 0.0) Q = Q + (d.cd[q & 1] * d.c[r & 1]).scale(w);
+          }
+        add_part(E, Q, B.ref(op(K_B, a, b)));
+      }
+  }
+  // creation operators
+  for (int a : inL) add_part(new_eop(S, K_C, a, -1), d.I, B.ref(op(K_C, a, -1)));
+  for (int m : ms) add_part(new_eop(S, K_C, m, -1), d.cd[m & 1], B.ident(1));
+  // A_ab
+  for (size_t ai = 0; ai < inL.size(); ++ai)
+    for (size_t bi = ai + 1; bi < inL.size(); ++bi)
+      add_part(new_eop(S, K_A, inL[ai], inL[bi]), d.I, B.ref(op(K_A, inL[ai], inL[bi])));
+  for (int a : inL)
+    for (int m : ms) add_part(new_eop(S, K_A, a, m), d.cd[m & 1], B.ref(op(K_C, a, -1), false, 1));
+  add_part(new_eop(S, K_A, m0, m1), d.cd[0] * d.cd[1], B.ident());
+  // B_ab
+  for (int a : inL)
+    for (int b : inL) add_part(new_eop(S, K_B, a, b), d.I, B.ref(op(K_B, a, b)));
+  for (int a : inL)
+    for (int m : ms) {
+      add_part(new_eop(S, K_B, a, m), d.c[m & 1], B.ref(op(K_C, a, -1), false, 1));
+      add_part(new_eop(S, K_B, m, a), d.cd[m & 1].scale(-1.0), B.ref(op(K_C, a, -1), true, 1));
+    }
+  for (int m : ms)
+    for (int n : ms) add_part(new_eop(S, K_B, m, n), d.cd[m & 1] * d.c[n & 1], B.ident());
+  // T_x for x right of LL
+  for (int x = 2 * site + 2; x < M; ++x) {
+    EOp& E = new_eop(S, K_T, x, -1);
+    add_part(E, d.I, B.ref(op(K_T, x, -1)));
+    for (int m : ms) {
+      std::vector<Term> bs, as;
+      for (int q : inL)
+        for (int r : inL) {
+          double w = W(m, q, r, x) - W(q, m, r, x);
+          if (w != 0.0) bs.push_back({w, op(K_B, q, r), false, 1});
+        }
+      for (size_t pi = 0; pi < inL.size(); ++pi)
+        for (size_t qi = pi + 1; qi < inL.size(); ++qi) {
+          int p = inL[pi], q = inL[qi];
+          double w = W(p, q, m, x) - W(q, p, m, x);
+          if (w != 0.0) as.push_back({w, op(K_A, p, q), false, 1});
+        }
+      add_part(E, d.cd[m & 1], B.comb(bs));
+      add_part(E, d.c[m & 1], B.comb(as));
+    }
+    for (int a : inL) {
+      M4 y1, y2;
+      for (int p : ms)
+        for (int q : ms) {
+          double w1 = W(p, q, a, x);
+          if (w1 != 0.0) y1 = y1 + (d.cd[p & 1] * d.cd[q & 1]).scale(w1);
+          double w2 = W(a, p, q, x) - W(p, a, q, x);
+          if (w2 != 0.0) y2 = y2 + (d.cd[p & 1] * d.c[q & 1]).scale(w2);
+        }
+      int ca = op(K_C, a, -1);
+      add_part(E, y1, B.ref(ca, true));
+      add_part(E, y2, B.ref(ca));
+    }
+    M4 y3;
+    for (int p : ms)
+      for (int q : ms)
+        for (int r : ms) {
+          double w = W(p, q, r, x);
+          if (w != 0.0) y3 = y3 + (d.cd[p & 1] * d.cd[q & 1] * d.c[r & 1]).scale(w);
+        }
+    add_part(E, y3, B.ident(1));
+  }
+}
+
+// RR = dot `site` (x) R; R holds orbitals site+1..N-1.  Operators of RR are
+// the catalogue of the right block of orbitals site..N-1.
+void Engine::build_right_eops(const Catalogue& R, int site, Side& S) {
+  const DotOps& d = dot();
+  Builder B(S, R);
+  const int m0 = 2 * site, m1 = 2 * site + 1;
+  const int ms[2] = {m0, m1};
+  const int M = 2 * N_;
+  std::vector<int> inR;
+  for (int x = 2 * site + 2; x < M; ++x) inR.push_back(x);
+  auto op = [&](int kind, int i, int j) { return R.find(kind, i, j); };
+  const M4& P4 = d.P;
+
+  M4 hs;
+  for (int p : ms)
+    for (int q : ms) hs = hs + (d.cd[p & 1] * d.c[q & 1]).scale(t(p, q));
+  for (int p : ms)
+    for (int q : ms)
+      for (int r : ms)
+        for (int s : ms) {
+          double w = W(p, q, r, s);
+          if (w != 0.0) hs = hs + (d.cd[p & 1] * d.cd[q & 1] * d.c[r & 1] * d.c[s & 1]).scale(0.5 * w);
+        }
+  {  // H
+    EOp& E = new_eop(S, K_H, -1, -1);
+    add_part(E, hs, B.ident());
+    add_part(E, d.I, B.ref(op(K_H, -1, -1)));
+    for (int m : ms) {
+      int Sm = op(K_S, m, -1);
+      add_part(E, d.cd[m & 1] * P4, B.ref(Sm));
+      add_part(E, (d.c[m & 1] * P4).scale(-1.0), B.ref(Sm, true));
+    }
+    for (int x : inR) {
+      M4 Ts;
+      for (int p : ms)
+        for (int q : ms)
+          for (int r : ms) {
+            double w = W(p, q, r, x);
+            if (w != 0.0) Ts = Ts + (d.cd[p & 1] * d.cd[q & 1] * d.c[r & 1]).scale(w);
+          }
+      int cx = op(K_C, x, -1);
+      add_part(E, Ts * P4, B.ref(cx, true));
+      add_part(E, (Ts.T() * P4).scale(-1.0), B.ref(cx));
+    }
+    M4 As = d.cd[0] * d.cd[1];
+    int Pm = op(K_P, m0, m1);
+    add_part(E, As, B.ref(Pm));
+    add_part(E, As.T(), B.ref(Pm, true));
+    for (int m : ms)
+      for (int n : ms) add_part(E, d.cd[m & 1] * d.c[n & 1], B.ref(op(K_Q, m, n)));
+  }
+  for (int m : ms) add_part(new_eop(S, K_C, m, -1), d.cd[m & 1], B.ident());
+  for (int x : inR) add_part(new_eop(S, K_C, x, -1), P4, B.ref(op(K_C, x, -1)));
+  // S_a
+  for (int a = 0; a < 2 * site; ++a) {
+    EOp& E = new_eop(S, K_S, a, -1);
+    add_part(E, P4, B.ref(op(K_S, a, -1)));
+    for (int m : ms) {
+      add_part(E, d.cd[m & 1], B.ref(op(K_P, a, m)));
+      add_part(E, d.c[m & 1], B.ref(op(K_Q, a, m)));
+      if (t(a, m) != 0.0) add_part(E, d.c[m & 1].scale(t(a, m)), B.ident());
+    }
+    for (int x : inR) {
+      M4 y1, y3;
+      for (int q : ms)
+        for (int r : ms) {
+          double w1 = W(a, q, r, x) - W(a, q, x, r);
+          if (w1 != 0.0) y1 = y1 + (d.cd[q & 1] * d.c[r & 1]).scale(w1);
+          double w3 = W(a, x, q, r);
+          if (w3 != 0.0) y3 = y3 + (d.c[q & 1] * d.c[r & 1]).scale(w3);
+        }
+      int cx = op(K_C, x, -1);
+      add_part(E, y1 * P4, B.ref(cx, true));
+      add_part(E, y3 * P4, B.ref(cx));
+    }
+    M4 y;
+    for (int q : ms)
+      for (int r : ms)
+        for (int u : ms) {
+          double w = W(a, q, r, u);
+          if (w != 0.0) y = y + (d.cd[q & 1] * d.c[r & 1] * d.c[u & 1]).scale(w);
+        }
+    add_part(E, y, B.ident());
+  }
+  // P_ab, Q_ab for a, b left of RR
+  for (int a = 0; a < 2 * site; ++a)
+    for (int b = 0; b < 2 * site; ++b) {
+      {
+        EOp& E = new_eop(S, K_Q, a, b);
+        add_part(E, d.I, B.ref(op(K_Q, a, b)));
+        for (int m : ms) {
+          std::vector<Term> cqr, crq;
+          for (int x : inR) {
+            double w1 = W(a, m, x, b) - W(a, m, b, x);  // c+_m c_x
+            double w2 = W(a, x, m, b) - W(a, x, b, m);  // c+_x c_m
+            int cx = op(K_C, x, -1);
+            if (w1 != 0.0) cqr.push_back({w1, cx, true, 0});
+            if (w2 != 0.0) crq.push_back({w2, cx, false, 0});
+          }
+          add_part(E, d.cd[m & 1] * P4, B.comb(cqr));
+          add_part(E, (d.c[m & 1] * P4).scale(-1.0), B.comb(crq));
+        }
+        M4 y;
+        for (int q : ms)
+          for (int r : ms) {
+            double w = W(a, q, r, b) - W(a, q, b, r);
+            if (w != 0.0) y = y + (d.cd[q & 1] * d.c[r & 1]).scale(w);
+          }
+        add_part(E, y, B.ident());
+      }
+      if (a < b) {
+        EOp& E = new_eop(S, K_P, a, b);
+        add_part(E, d.I, B.ref(op(K_P, a, b)));
+        for (int m : ms) {
+          std::vector<Term> cf;
+          for (int x : inR) {
+            double w = W(a, b, m, x) - W(a, b, x, m);
+            if (w != 0.0) cf.push_back({w, op(K_C, x, -1), true, 0});
+          }
+          add_part(E, d.c[m & 1] * P4, B.comb(cf));
+        }
+        M4 y;
+        for (int r : ms)
+          for (int u : ms) {
+            double w = W(a, b, r, u);
+            if (w != 0.0) y = y + (d.c[r & 1] * d.c[u & 1]).scale(w);
+          }
+        add_part(E, y, B.ident());
+      }
+    }
+}
+
+// dot blocks of every enlarged operator; dot blocks with more than two
+// expressions become one materialised expression (partial summation)
+void Engine::compile_side(Side& S, const Catalogue& cat, bool left) {
+  (void)left;
+  Builder B(S, cat);
+  for (auto& E : S.eops) {
+    E.dots.clear();
+    E.dq = {0, 0};
+    bool have_dq = false;
+    for (int so = 0; so < 4; ++so)
+      for (int si = 0; si < 4; ++si) {
+        DotBlock db;
+        db.so = so;
+        db.si = si;
+        for (auto& pr : E.parts) {
+          double y = pr.first.a[so][si];
+          if (y == 0.0) continue;
+          bool merged = false;
+          for (auto& dt : db.t)
+            if (dt.expr == pr.second) {
+              dt.s += y;
+              merged = true;
+            }
+          if (!merged) db.t.push_back({y, pr.second});
+        }
+        std::vector<DotTerm> keep;
+        for (auto& dt : db.t)
+          if (dt.s != 0.0) keep.push_back(dt);
+        db.t = keep;
+        if (db.t.empty()) continue;
+        if (db.t.size() > 2) {
+          std::vector<Term> ts;
+          for (auto& dt : db.t)
+            for (auto& tm : S.exprs[dt.expr].t) ts.push_back({dt.s * tm.c, tm.op, tm.tr, tm.par});
+          int e = B.comb(ts);
+          db.t.clear();
+          if (e < 0) continue;
+          db.t.push_back({1.0, e});
+        }
+        QN dq = S.exprs[db.t[0].expr].dq + kSiteQN[so] - kSiteQN[si];
+        if (!have_dq) {
+          E.dq = dq;
+          have_dq = true;
+        }
+        E.dots.push_back(db);
+      }
+    if (!have_dq) {
+      // structurally zero operator: shift from its catalogue kind
+      E.dq = dq_of(E.kind, E.i, E.j);
+    }
+  }
+}
+
+// materialise every expression with more than one term on the side's block basis
+int Engine::materialize(Side& S, Catalogue& cat, std::string& err) {
+  S.mats.clear();
+  for (size_t e = 0; e < S.exprs.size(); ++e) {
+    Expr& x = S.exprs[e];
+    x.mat = -1;
+    if (x.t.size() <= 1) continue;
+    Mat m;
+    m.layout = cat.layout_for(x.dq);
+    m.off = 0;
+    m.expr = (int)e;
+    x.mat = (int)S.mats.size();
+    S.mats.push_back(m);
+  }
+  long long tot = 0;
+  for (auto& m : S.mats) {
+    m.off = tot;
+    tot += cat.layouts[m.layout].size;
+  }
+  if (S.d) be_->release(S.d);
+  S.d = nullptr;
+  S.size = tot;
+  if (tot == 0) return 0;
+  S.d = be_->alloc(tot);
+  if (!S.d) {
+    err = "device allocation of " + std::to_string(tot * 8) + " bytes failed (partial sums)";
+    return -3;
+  }
+  LCList lc;
+  const Basis& bs = cat.basis;
+  for (auto& m : S.mats) {
+    const Expr& x = S.exprs[m.expr];
+    const Layout& L = cat.layouts[m.layout];
+    for (size_t b = 0; b < L.in.size(); ++b) {
+      int in = L.in[b], out = L.out[b];
+      LCBlock blk;
+      blk.dst = S.d + m.off + L.off[b];
+      blk.rows = bs.dim[out];
+      blk.cols = bs.dim[in];
+      blk.t0 = (int)lc.terms.size();
+      for (auto& tm : x.t) {
+        double sign = tm.par == 1 ? sgn_n(bs.q[in].n) : tm.par == 2 ? sgn_n(bs.q[out].n) : 1.0;
+        if (tm.op < 0) {
+          if (in == out) lc.terms.push_back({tm.c * sign, nullptr, 0});
+          continue;
+        }
+        const CatOp& o = cat.ops[tm.op];
+        const Layout& OL = cat.layouts[o.layout];
+        int ob = tm.tr ? OL.blk_of_in[out] : OL.blk_of_in[in];
+        if (ob < 0) continue;
+        if (tm.tr && OL.out[ob] != in) continue;
+        if (!tm.tr && OL.out[ob] != out) continue;
+        lc.terms.push_back({tm.c * sign, cat.d + o.off + OL.off[ob], tm.tr ? 1 : 0});
+      }
+      blk.t1 = (int)lc.terms.size();
+      lc.blocks.push_back(blk);
+    }
+  }
+  be_->lincomb(lc);
+  return 0;
+}
+
+// operand of a product: expression `e` of side S used plain or transposed,
+// applied to in-sector `in` of the side's basis
+namespace {
+struct Operand {
+  const double* p;
+  int out;
+  bool ident, trans;
+  double sign;
+};
+bool resolve(const Side& S, const Catalogue& cat, int e, bool tr, int in, Operand& r) {
+  const Expr& x = S.exprs[e];
+  const Basis& bs = cat.basis;
+  if (x.mat >= 0) {
+    const Mat& M = S.mats[x.mat];
+    const Layout& L = cat.layouts[M.layout];
+    int b;
+    if (!tr) {
+      b = L.blk_of_in[in];
+      if (b < 0) return false;
+      r.out = L.out[b];
+    } else {
+      b = blk_of_out(bs, L, in);
+      if (b < 0) return false;
+      r.out = L.in[b];
+    }
+    r.p = S.d + M.off + L.off[b];
+    r.ident = false;
+    r.trans = tr;
+    r.sign = 1.0;
+    return true;
+  }
+  const Term& t = x.t[0];
+  bool tt = tr != t.tr;
+  int par = t.par;
+  if (tr && par) par = 3 - par;
+  if (t.op < 0) {
+    r.out = in;
+    r.ident = true;
+    r.trans = false;
+    r.p = nullptr;
+  } else {
+    const CatOp& o = cat.ops[t.op];
+    const Layout& L = cat.layouts[o.layout];
+    int b;
+    if (!tt) {
+      b = L.blk_of_in[in];
+      if (b < 0) return false;
+      r.out = L.out[b];
+    } else {
+      b = blk_of_out(bs, L, in);
+      if (b < 0) return false;
+      r.out = L.in[b];
+    }
+    r.p = cat.d + o.off + L.off[b];
+    r.ident = false;
+    r.trans = tt;
+  }
+  r.sign = t.c * (par == 1 ? sgn_n(bs.q[in].n) : par == 2 ? sgn_n(bs.q[r.out].n) : 1.0);
+  return true;
+}
+
+double chain_flops(const Task& t) {
+  bool li = t.flags & TF_LI, ri = t.flags & TF_RI, xi = t.flags & TF_XI;
+  double q = t.q, m = t.m, n = t.n, r = t.r;
+  if (xi) {
+    if (li || ri) return 2.0 * q * r;  // plain copy-scale / one product
+    return 2.0 * q * m * r;
+  }
+  if (li && ri) return 2.0 * m * n;
+  if (li) return 2.0 * m * n * r;
+  if (ri) return 2.0 * q * m * n;
+  return std::min(2.0 * m * r * (n + q), 2.0 * q * n * (m + r));
+}
+
+void set_order(Task& t) {
+  bool li = t.flags & TF_LI, ri = t.flags & TF_RI;
+  if (li || ri) return;
+  double a = 2.0 * t.m * t.r * ((double)t.n + t.q);  // L (X R^T)
+  double b = 2.0 * t.q * t.n * ((double)t.m + t.r);  // (L X) R^T
+  if (b < a) t.flags |= TF_ORDB;
+}
+}  // namespace
+
+// rotate the enlarged operators of a side into the new block (renormalisation)
+int Engine::rotate(Side& S, const Catalogue& src, Catalogue& dst, int site, bool left, std::string& err) {
+  // dst basis: left -> bond site+1 (left counted); right -> bond `site` right counted
+  dst = Catalogue();
+  dst.left = left;
+  dst.len = left ? site + 1 : site;
+  if (left) {
+    dst.basis = bonds_[site + 1];
+  } else {
+    const Basis& b = bonds_[site];
+    for (int i = 0; i < b.size(); ++i) dst.basis.add(target_ - b.q[i], b.dim[i]);
+  }
+  for (auto& E : S.eops) dst.add_op(E.kind, E.i, E.j, E.dq);
+  int rc = alloc_cat(dst, err);
+  if (rc) return rc;
+  const Site& st = sites_[site];
+  const Basis& sb = bonds_[site];        // site tensor left bond
+  const Basis& sb1 = bonds_[site + 1];   // site tensor right bond
+  TaskList tl;
+  for (size_t ei = 0; ei < S.eops.size(); ++ei) {
+    const EOp& E = S.eops[ei];
+    const CatOp& o = dst.ops[ei];
+    const Layout& OL = dst.layouts[o.layout];
+    for (size_t b = 0; b < OL.in.size(); ++b) {
+      int qin = OL.in[b], qout = OL.out[b];  // sectors of dst basis
+      Group g;
+      g.yoff = o.off + OL.off[b];
+      g.q = dst.basis.dim[qout];
+      g.r = dst.basis.dim[qin];
+      g.row0 = g.col0 = 0;
+      g.nrows = g.q;
+      g.ncols = g.r;
+      g.t0 = (int)tl.tasks.size();
+      for (const auto& db : E.dots) {
+        for (const auto& dt : db.t) {
+          if (left) {
+            // new op (q'' <- q) += A^{so}(ql' -> q'')^T  X(ql' <- ql)  A^{si}(ql -> q)
+            QN qo = dst.basis.q[qout] - kSiteQN[db.so];
+            QN qi = dst.basis.q[qin] - kSiteQN[db.si];
+            int lo = sb.find(qo), li = sb.find(qi);
+            if (lo < 0 || li < 0) continue;
+            int bo = st.index[lo * 4 + db.so], bi = st.index[li * 4 + db.si];
+            if (bo < 0 || bi < 0) continue;
+            Operand X;
+            if (!resolve(S, src, dt.expr, false, li, X)) continue;
+            if (X.out != lo) continue;
+            Task tk;
+            tk.alpha = dt.s * X.sign;
+            tk.L = st.d + st.blocks[bo].off;
+            tk.X = X.p;
+            tk.R = st.d + st.blocks[bi].off;
+            tk.q = g.q;
+            tk.m = sb.dim[lo];
+            tk.n = sb.dim[li];
+            tk.r = g.r;
+            tk.flags = TF_LT | TF_RT | (X.ident ? TF_XI : 0) | (X.trans ? TF_XT : 0);
+            tk.pad = 0;
+            set_order(tk);
+            tl.flops += chain_flops(tk);
+            tl.tasks.push_back(tk);
+          } else {
+            // new op (Q' <- Q) += B^{so}(Q') X(Q'-so <- Q-si) B^{si}(Q)^T ; Q right counted
+            QN Qo = dst.basis.q[qout], Qi = dst.basis.q[qin];
+            int lo = sb.find(target_ - Qo), li = sb.find(target_ - Qi);  // bond `site` (left counted)
+            if (lo < 0 || li < 0) continue;
+            int bo = st.index[lo * 4 + db.so], bi = st.index[li * 4 + db.si];
+            if (bo < 0 || bi < 0) continue;
+            // R-block sectors (own content of orbitals site+1..N-1)
+            int ro = src.basis.find(Qo - kSiteQN[db.so]);
+            int ri = src.basis.find(Qi - kSiteQN[db.si]);
+            if (ro < 0 || ri < 0) continue;
+            Operand X;
+            if (!resolve(S, src, dt.expr, false, ri, X)) continue;
+            if (X.out != ro) continue;
+            Task tk;
+            tk.alpha = dt.s * X.sign;
+            tk.L = st.d + st.blocks[bo].off;
+            tk.X = X.p;
+            tk.R = st.d + st.blocks[bi].off;
+            tk.q = g.q;
+            tk.m = src.basis.dim[ro];
+            tk.n = src.basis.dim[ri];
+            tk.r = g.r;
+            tk.flags = (X.ident ? TF_XI : 0) | (X.trans ? TF_XT : 0);
+            tk.pad = 0;
+            set_order(tk);
+            tl.flops += chain_flops(tk);
+            tl.tasks.push_back(tk);
+            (void)sb1;
+          }
+        }
+      }
+      g.t1 = (int)tl.tasks.size();
+      tl.groups.push_back(g);
+    }
+  }
+  tl.nprod = (long long)tl.tasks.size();
+  be_->run(tl, nullptr, dst.d, 1, 0, 0, 0);
+  dst.valid = true;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// environment
+// ---------------------------------------------------------------------------
+int Engine::ensure_left(int k, std::string& err) {
+  if (Lcat_[k].valid) return 0;
+  int j = k;
+  while (j > 0 && !Lcat_[j].valid) --j;
+  if (j == 0 && !Lcat_[0].valid) {
+    empty_left(Lcat_[0]);
+    int rc = alloc_cat(Lcat_[0], err);
+    if (rc) return rc;
+    be_->zero(Lcat_[0].d, Lcat_[0].size);
+    Lcat_[0].valid = true;
+  }
+  for (; j < k; ++j) {
+    if (!sites_[j].d) {
+      err = "site tensor " + std::to_string(j) + " not set";
+      return -2;
+    }
+    Side S;
+    build_left_eops(Lcat_[j], j, S);
+    compile_side(S, Lcat_[j], true);
+    int rc = materialize(S, Lcat_[j], err);
+    if (!rc) rc = rotate(S, Lcat_[j], Lcat_[j + 1], j, true, err);
+    be_->sync();
+    free_side(S);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+int Engine::ensure_right(int k, std::string& err) {
+  if (Rcat_[k].valid) return 0;
+  int j = k;
+  while (j < N_ && !Rcat_[j].valid) ++j;
+  if (j == N_ && !Rcat_[N_].valid) {
+    empty_right(Rcat_[N_]);
+    int rc = alloc_cat(Rcat_[N_], err);
+    if (rc) return rc;
+    be_->zero(Rcat_[N_].d, Rcat_[N_].size);
+    Rcat_[N_].valid = true;
+  }
+  for (; j > k; --j) {
+    if (!sites_[j - 1].d) {
+      err = "site tensor " + std::to_string(j - 1) + " not set";
+      return -2;
+    }
+    Side S;
+    build_right_eops(Rcat_[j], j - 1, S);
+    compile_side(S, Rcat_[j], false);
+    int rc = materialize(S, Rcat_[j], err);
+    if (!rc) rc = rotate(S, Rcat_[j], Rcat_[j - 1], j - 1, false, err);
+    be_->sync();
+    free_side(S);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+void Engine::build_psi(int k) {
+  Step& st = step_;
+  st.psi.clear();
+  st.desc.clear();
+  const Basis& L = bonds_[k];
+  const Catalogue& R = Rcat_[k + 2];
+  int nqr = R.basis.size();
+  st.psi_index.assign((size_t)L.size() * 16 * nqr, -1);
+  long long off = 0;
+  for (int ql = 0; ql < L.size(); ++ql)
+    for (int s1 = 0; s1 < 4; ++s1)
+      for (int s2 = 0; s2 < 4; ++s2) {
+        QN need = target_ - L.q[ql] - kSiteQN[s1] - kSiteQN[s2];
+        int qr = R.basis.find(need);
+        if (qr < 0) continue;
+        PsiBlock pb;
+        pb.ql = ql;
+        pb.s1 = s1;
+        pb.s2 = s2;
+        pb.qr = qr;
+        pb.m = L.dim[ql];
+        pb.n = R.basis.dim[qr];
+        pb.off = off;
+        off += (long long)pb.m * pb.n;
+        st.psi_index[((size_t)(ql * 4 + s1) * 4 + s2) * nqr + qr] = (int)st.psi.size();
+        st.psi.push_back(pb);
+        long long d9[9] = {L.q[ql].n, L.q[ql].s, s1, s2, R.basis.q[qr].n, R.basis.q[qr].s, pb.m, pb.n, pb.off};
+        st.desc.insert(st.desc.end(), d9, d9 + 9);
+      }
+  st.length = off;
+}
+
+// operator-table x task-table: every pair of the LL|RR split, every dot
+// block pair, every symmetry block of psi
+void Engine::build_heff_tasks() {
+  Step& st = step_;
+  const int k = st.k;
+  const Catalogue& Lc = Lcat_[k];
+  const Catalogue& Rc = Rcat_[k + 2];
+  const Basis& Lb = Lc.basis;
+  const int nqr = Rc.basis.size();
+  TaskList& tl = st.heff;
+  tl.clear();
+
+  struct Pair {
+    int eL;
+    bool trL;
+    int eR;
+    bool trR;
+    double c;
+    int f;
+  };
+  std::vector<Pair> pairs;
+  auto eL = [&](int kind, int i, int j) {
+    auto it = st.L.eop_index.find(Catalogue::key(kind, i, j));
+    return it == st.L.eop_index.end() ? -1 : it->second;
+  };
+  auto eR = [&](int kind, int i, int j) {
+    auto it = st.R.eop_index.find(Catalogue::key(kind, i, j));
+    return it == st.R.eop_index.end() ? -1 : it->second;
+  };
+  const int nLL = 2 * (k + 1);
+  const int M = 2 * N_;
+  // H_LL (x) 1 and 1 (x) H_RR use a virtual identity operator (index -2)
+  pairs.push_back({eL(K_H, -1, -1), false, -2, false, 1.0, 0});
+  pairs.push_back({-2, false, eR(K_H, -1, -1), false, 1.0, 0});
+  for (int a = 0; a < nLL; ++a) {
+    int l = eL(K_C, a, -1), r = eR(K_S, a, -1);
+    pairs.push_back({l, false, r, false, 1.0, 1});
+    pairs.push_back({l, true, r, true, -1.0, 1});
+  }
+  for (int x = nLL; x < M; ++x) {
+    int l = eL(K_T, x, -1), r = eR(K_C, x, -1);
+    pairs.push_back({l, false, r, true, 1.0, 1});
+    pairs.push_back({l, true, r, false, -1.0, 1});
+  }
+  for (int a = 0; a < nLL; ++a)
+    for (int b = a + 1; b < nLL; ++b) {
+      int l = eL(K_A, a, b), r = eR(K_P, a, b);
+      pairs.push_back({l, false, r, false, 1.0, 0});
+      pairs.push_back({l, true, r, true, 1.0, 0});
+    }
+  for (int a = 0; a < nLL; ++a)
+    for (int b = 0; b < nLL; ++b) pairs.push_back({eL(K_B, a, b), false, eR(K_Q, a, b), false, 1.0, 0});
+
+  // per output block task buckets
+  std::vector<std::vector<Task>> bucket(st.psi.size());
+  static const DotBlock kIdent[4] = {{0, 0, {{1.0, -1}}}, {1, 1, {{1.0, -1}}}, {2, 2, {{1.0, -1}}}, {3, 3, {{1.0, -1}}}};
+
+  for (const Pair& pr : pairs) {
+    if (pr.eL == -1 || pr.eR == -1) continue;
+    std::vector<DotBlock> dl, dr;
+    if (pr.eL == -2) dl.assign(kIdent, kIdent + 4);
+    else dl = st.L.eops[pr.eL].dots;
+    if (pr.eR == -2) dr.assign(kIdent, kIdent + 4);
+    else dr = st.R.eops[pr.eR].dots;
+    for (const auto& a : dl) {
+      int s1o = pr.trL ? a.si : a.so, s1i = pr.trL ? a.so : a.si;
+      for (const auto& b : dr) {
+        int s2o = pr.trR ? b.si : b.so, s2i = pr.trR ? b.so : b.si;
+        for (const auto& ta : a.t)
+          for (const auto& tb : b.t) {
+            for (int ql = 0; ql < Lb.size(); ++ql) {
+              Operand Lo;
+              if (ta.expr == -1) {
+                Lo.p = nullptr;
+                Lo.out = ql;
+                Lo.ident = true;
+                Lo.trans = false;
+                Lo.sign = 1.0;
+              } else if (!resolve(st.L, Lc, ta.expr, pr.trL, ql, Lo)) {
+                continue;
+              }
+              double pl = pr.f ? sgn_n(Lb.q[ql].n + kSiteQN[s1i].n) : 1.0;
+              for (int qr = 0; qr < nqr; ++qr) {
+                int xb = st.psi_index[((size_t)(ql * 4 + s1i) * 4 + s2i) * nqr + qr];
+                if (xb < 0) continue;
+                Operand Ro;
+                if (tb.expr == -1) {
+                  Ro.p = nullptr;
+                  Ro.out = qr;
+                  Ro.ident = true;
+                  Ro.trans = false;
+                  Ro.sign = 1.0;
+                } else if (!resolve(st.R, Rc, tb.expr, pr.trR, qr, Ro)) {
+                  continue;
+                }
+                int yb = st.psi_index[((size_t)(Lo.out * 4 + s1o) * 4 + s2o) * nqr + Ro.out];
+                if (yb < 0) continue;
+                const PsiBlock& X = st.psi[xb];
+                const PsiBlock& Y = st.psi[yb];
+                Task tk;
+                tk.alpha = pr.c * ta.s * tb.s * Lo.sign * Ro.sign * pl;
+                if (tk.alpha == 0.0) continue;
+                tk.L = Lo.p;
+                tk.X = reinterpret_cast<const double*>((uintptr_t)X.off);
+                tk.R = Ro.p;
+                tk.q = Y.m;
+                tk.m = X.m;
+                tk.n = X.n;
+                tk.r = Y.n;
+                tk.flags = TF_XV | (Lo.ident ? TF_LI : 0) | (Lo.trans ? TF_LT : 0) | (Ro.ident ? TF_RI : 0) |
+                           (Ro.trans ? TF_RT : 0);
+                tk.pad = xb;
+                set_order(tk);
+                bucket[yb].push_back(tk);
+              }
+            }
+          }
+      }
+    }
+  }
+  for (size_t yb = 0; yb < st.psi.size(); ++yb) {
+    const PsiBlock& Y = st.psi[yb];
+    Group g;
+    g.yoff = Y.off;
+    g.q = Y.m;
+    g.r = Y.n;
+    g.row0 = g.col0 = 0;
+    g.nrows = Y.m;
+    g.ncols = Y.n;
+    g.t0 = (int)tl.tasks.size();
+    for (auto& tk : bucket[yb]) {
+      tl.flops += chain_flops(tk);
+      tl.tasks.push_back(tk);
+    }
+    g.t1 = (int)tl.tasks.size();
+    tl.groups.push_back(g);
+  }
+  tl.nprod = (long long)tl.tasks.size();
+  st.diag_tasks.clear();
+  for (int g = 0; g < (int)tl.groups.size(); ++g)
+    for (int i = tl.groups[g].t0; i < tl.groups[g].t1; ++i)
+      if (tl.tasks[i].pad == g) st.diag_tasks.push_back(i);
+}
+
+int Engine::prepare_step(int k, std::string& err) {
+  free_side(step_.L);
+  free_side(step_.R);
+  step_.valid = false;
+  step_.k = k;
+  build_left_eops(Lcat_[k], k, step_.L);
+  compile_side(step_.L, Lcat_[k], true);
+  int rc = materialize(step_.L, Lcat_[k], err);
+  if (rc) return rc;
+  build_right_eops(Rcat_[k + 2], k + 1, step_.R);
+  compile_side(step_.R, Rcat_[k + 2], false);
+  rc = materialize(step_.R, Rcat_[k + 2], err);
+  if (rc) return rc;
+  build_psi(k);
+  build_heff_tasks();
+  be_->sync();
+  std::string e = be_->error();
+  if (!e.empty()) {
+    err = e;
+    return -6;
+  }
+  step_.valid = true;
+  return 0;
+}
+
+int Engine::build_env(int k, std::string& err) {
+  if (!have_ints_ || !have_mps_) {
+    err = "build_env: load integrals and an MPS first";
+    return -2;
+  }
+  if (k < 0 || k > N_ - 2) {
+    err = "build_env: site out of range";
+    return -1;
+  }
+  int rc = ensure_left(k, err);
+  if (!rc) rc = ensure_right(k + 2, err);
+  if (!rc) rc = prepare_step(k, err);
+  if (!rc) {
+    std::string e = be_->error();
+    if (!e.empty()) {
+      err = e;
+      rc = -6;
+    }
+  }
+  return rc;
+}
+
+int Engine::grow_left(int k, std::string& err) {
+  // L_{k+1} from the step's LL operators and the (new) site tensor k
+  int rc = rotate(step_.L, Lcat_[k], Lcat_[k + 1], k, true, err);
+  be_->sync();
+  return rc;
+}
+
+int Engine::grow_right(int k, std::string& err) {
+  int rc = rotate(step_.R, Rcat_[k + 2], Rcat_[k + 1], k + 1, false, err);
+  be_->sync();
+  return rc;
+}
+
+int Engine::heff(const double* X, double* Y, int nvec, int precision, std::string& err) {
+  if (!step_.valid) {
+    err = "heff: call build_env first";
+    return -2;
+  }
+  be_->run(step_.heff, X, Y, nvec, step_.length, step_.length, precision);
+  std::string e = be_->error();
+  if (!e.empty()) {
+    err = e;
+    return -6;
+  }
+  return 0;
+}
+
+}  // namespace tns

@@ -1,0 +1,386 @@
+// engine.h -- symbolic layer of the two-site DMRG H_eff*psi engine.
+//
+// Block-sparse layout (Sec. III.A.1): an operator on a block basis is stored
+// as the dense blocks (out-sector <- in-sector) allowed by its quantum-number
+// shift dq, each block row-major, blocks of one operator contiguous.
+//
+// Operator catalogues (Sec. III.A.2, partial summation N^4 -> N^2):
+//   left block  L (orbitals 0..len-1):  H, c+_a, A_ab = c+_a c+_b (a<b),
+//       B_ab = c+_a c_b, T_x = sum_{pqr in L} W_pqrx c+_p c+_q c_r  (x >= 2*len)
+//   right block R (orbitals len..N-1):  H, c+_x, S_a, P_ab (a<b), Q_ab  (a,b < 2*len)
+//       S_a  = sum_{qru in R} W_aqru c+_q c_r c_u + sum_{x in R} t_ax c_x
+//       P_ab = sum_{ru in R} W_abru c_r c_u
+//       Q_ab = sum_{qr in R} (W_aqrb - W_aqbr) c+_q c_r
+// with spin-orbital integrals t_pq = h_{i_p i_q} d(s_p,s_q) and
+// W_pqrs = (i_p i_s | i_q i_r) d(s_p,s_s) d(s_q,s_r) of Eq. (1).
+//
+// Enlarged operators (blocking of a block with one dot) are sums of
+// (D-basis expression) (x) (4x4 dot operator); the dot's one-dimensional
+// sectors turn every dot factor into scalars (Sec. III.A.2), so an enlarged
+// operator is a set of "dot blocks" (s' <- s), each a short list of
+// scalar x expression.  Expressions are a catalogue operator (optionally
+// transposed, optionally times the block parity), the identity, or a
+// materialised linear combination (partial sum).
+//
+// Every product the engine executes has the form of Eq. (2):
+//     Y_blk += alpha * op(L) * op(X) * op(R)^T
+// (op = identity, plain or transposed), grouped by output block.
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+namespace tns {
+
+struct QN {
+  int n = 0, s = 0;
+};
+inline bool operator<(QN a, QN b) { return a.n < b.n || (a.n == b.n && a.s < b.s); }
+inline bool operator==(QN a, QN b) { return a.n == b.n && a.s == b.s; }
+inline bool operator!=(QN a, QN b) { return !(a == b); }
+inline QN operator+(QN a, QN b) { return {a.n + b.n, a.s + b.s}; }
+inline QN operator-(QN a, QN b) { return {a.n - b.n, a.s - b.s}; }
+inline QN operator-(QN a) { return {-a.n, -a.s}; }
+
+extern const QN kSiteQN[4];
+
+struct Basis {
+  std::vector<QN> q;
+  std::vector<int> dim;
+  std::vector<long long> off;
+  long long total = 0;
+  std::map<QN, int> idx;
+  void clear() { q.clear(); dim.clear(); off.clear(); total = 0; idx.clear(); }
+  void add(QN x, int d) {
+    idx[x] = (int)q.size();
+    q.push_back(x);
+    dim.push_back(d);
+    off.push_back(total);
+    total += d;
+  }
+  int find(QN x) const {
+    auto it = idx.find(x);
+    return it == idx.end() ? -1 : it->second;
+  }
+  int size() const { return (int)q.size(); }
+};
+
+// blocks of an operator with shift dq on a basis: block b maps in[b] -> out[b]
+struct Layout {
+  QN dq;
+  std::vector<int> in, out;
+  std::vector<long long> off;
+  std::vector<int> blk_of_in;  // in-sector index -> block index, -1 if none
+  long long size = 0;
+};
+void make_layout(const Basis& b, QN dq, Layout& L);
+
+enum OpKind { K_H = 0, K_C, K_A, K_B, K_T, K_S, K_P, K_Q };
+
+struct CatOp {
+  int kind, i, j;
+  QN dq;
+  int layout;
+  long long off;  // element offset in the catalogue arena
+};
+
+struct Catalogue {
+  bool left = true;
+  int len = 0;   // left: orbitals 0..len-1, right: orbitals len..N-1
+  Basis basis;   // own content of the block (particles inside it)
+  std::vector<Layout> layouts;
+  std::map<QN, int> layout_of;
+  std::vector<CatOp> ops;
+  std::unordered_map<long long, int> index;
+  double* d = nullptr;  // arena (device for the CUDA backend)
+  long long size = 0;
+  bool valid = false;
+  static long long key(int kind, int i, int j) {
+    return ((long long)kind << 40) | ((long long)(i + 1) << 20) | (long long)(j + 1);
+  }
+  int layout_for(QN dq);
+  int find(int kind, int i = -1, int j = -1) const {
+    auto it = index.find(key(kind, i, j));
+    return it == index.end() ? -1 : it->second;
+  }
+  int add_op(int kind, int i, int j, QN dq);  // appends, assigns offsets later
+  void assign_offsets();
+};
+
+struct M4 {
+  double a[4][4];
+  M4() {
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) a[i][j] = 0.0;
+  }
+  static M4 eye() {
+    M4 m;
+    for (int i = 0; i < 4; ++i) m.a[i][i] = 1.0;
+    return m;
+  }
+  M4 operator*(const M4& b) const {
+    M4 r;
+    for (int i = 0; i < 4; ++i)
+      for (int k = 0; k < 4; ++k)
+        if (a[i][k] != 0.0)
+          for (int j = 0; j < 4; ++j) r.a[i][j] += a[i][k] * b.a[k][j];
+    return r;
+  }
+  M4 operator+(const M4& b) const {
+    M4 r;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) r.a[i][j] = a[i][j] + b.a[i][j];
+    return r;
+  }
+  M4 scale(double c) const {
+    M4 r;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) r.a[i][j] = c * a[i][j];
+    return r;
+  }
+  M4 T() const {
+    M4 r;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) r.a[i][j] = a[j][i];
+    return r;
+  }
+  bool zero() const {
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j)
+        if (a[i][j] != 0.0) return false;
+    return true;
+  }
+};
+
+// one term of an expression: c * op^(T) * P^(par)
+//   op = -1: identity; par: 0 none, 1 parity of the in-sector, 2 of the out-sector
+struct Term {
+  double c;
+  int op;
+  bool tr;
+  int par;
+};
+
+struct Expr {
+  std::vector<Term> t;
+  QN dq;          // shift of the expression (in -> in + dq)
+  int mat = -1;   // materialised: index into Step::mats
+};
+
+// enlarged operator = sum_parts (expr (x) y) ; dot blocks compiled from it
+struct DotTerm {
+  double s;
+  int expr;
+};
+struct DotBlock {
+  int so, si;
+  std::vector<DotTerm> t;
+};
+struct EOp {
+  int kind, i, j;   // catalogue key of the enlarged block this operator belongs to
+  QN dq;            // total shift (expr dq + dot shift)
+  std::vector<std::pair<M4, int>> parts;  // (dot operator, expr id)
+  std::vector<DotBlock> dots;
+};
+
+// a materialised expression: its own operator on the block basis
+struct Mat {
+  int layout;      // index into the owning side's catalogue layouts
+  long long off;   // element offset in the step scratch arena
+  int expr;
+};
+
+// ---------------------------------------------------------------------------
+// work lists
+// ---------------------------------------------------------------------------
+enum TaskFlags {
+  TF_LI = 1,      // L is the identity
+  TF_LT = 2,      // L stored transposed (m x q)
+  TF_XI = 4,      // X is the identity (m == n)
+  TF_XT = 8,      // X stored transposed (n x m)
+  TF_XV = 16,     // X pointer is an element offset into the launch's X vector
+  TF_RI = 32,     // R is the identity
+  TF_RT = 64,     // R stored transposed (n x r)
+  TF_ORDB = 128,  // evaluate (L X) R^T instead of L (X R^T)
+};
+
+struct Task {
+  double alpha;
+  const double* L;
+  const double* X;  // pointer, or element offset cast to pointer when TF_XV
+  const double* R;
+  int q, m, n, r;
+  int flags;
+  int pad;
+};
+
+struct Group {  // one output block (or tile of it) and its task range
+  long long yoff;  // element offset (H_eff: into Y vector; env: into the arena given at launch)
+  int q, r;        // full block dims (row-major q x r)
+  int row0, col0, nrows, ncols;
+  int t0, t1;
+};
+
+struct TaskList {
+  std::vector<Task> tasks;
+  std::vector<Group> groups;
+  double flops = 0.0;
+  long long nprod = 0;
+  void clear() { tasks.clear(); groups.clear(); flops = 0; nprod = 0; }
+};
+
+struct LCTerm {
+  double c;
+  const double* src;  // nullptr: identity
+  int tr;             // source block stored transposed (cols x rows)
+};
+struct LCBlock {
+  double* dst;
+  int rows, cols;
+  int t0, t1;
+};
+struct LCList {
+  std::vector<LCBlock> blocks;
+  std::vector<LCTerm> terms;
+};
+
+// ---------------------------------------------------------------------------
+// backend: device memory and the kernels (CUDA in the product library)
+// ---------------------------------------------------------------------------
+struct Backend {
+  virtual ~Backend() {}
+  virtual double* alloc(long long n) = 0;  // nullptr on failure
+  virtual void release(double* p) = 0;
+  virtual void upload(double* dst, const double* src, long long n) = 0;
+  virtual void download(double* dst, const double* src, long long n) = 0;
+  virtual void zero(double* p, long long n) = 0;
+  virtual void lincomb(const LCList& l) = 0;
+  // run a task list: each group's output (tile) is overwritten with the sum of
+  // its tasks.  xv/yv: bases for TF_XV offsets and group yoff.
+  virtual void run(const TaskList& tl, const double* xv, double* yv, int nvec,
+                   long long xstride, long long ystride, int precision) = 0;
+  virtual void sync() = 0;
+  virtual std::string error() = 0;  // "" if fine
+};
+
+// ---------------------------------------------------------------------------
+// MPS
+// ---------------------------------------------------------------------------
+struct SiteBlock {
+  int ql, s, qr;  // bond-b sector index, site state, bond-(b+1) sector index
+  int m, n;
+  long long off;  // element offset in the site array
+};
+struct Site {
+  std::vector<SiteBlock> blocks;
+  std::vector<int> index;  // ql*4+s -> block or -1
+  double* d = nullptr;
+  long long size = 0;
+};
+
+// ---------------------------------------------------------------------------
+// per two-site step state
+// ---------------------------------------------------------------------------
+struct Side {  // enlarged operators of one side for a step
+  std::vector<Expr> exprs;
+  std::vector<EOp> eops;
+  std::map<long long, int> eop_index;  // catalogue key -> eop
+  std::vector<Mat> mats;
+  double* d = nullptr;  // materialised arena
+  long long size = 0;
+};
+
+struct PsiBlock {
+  int ql, s1, s2, qr;  // ql: bond-k sector index; qr: index in the right block basis
+  int m, n;
+  long long off;
+};
+
+struct Step {
+  int k = -1;
+  Side L, R;
+  std::vector<PsiBlock> psi;
+  std::vector<int> psi_index;  // ((ql*4+s1)*4+s2)*nqr+qr -> block
+  std::vector<long long> desc;
+  long long length = 0;
+  TaskList heff;
+  std::vector<int> diag_tasks;  // tasks contributing to the diagonal
+  bool valid = false;
+};
+
+class Engine {
+ public:
+  explicit Engine(Backend* be) : be_(be) {}
+  ~Engine();
+
+  int load_integrals(int N, const double* h, const double* v, double e_core, std::string& err);
+  int mps_define(int N, int n_elec, int two_sz, int D, std::string& err);
+  int mps_set_bond(int b, int nsec, const int* sec, const int* dims, std::string& err);
+  int mps_set_site(int b, const double* x, long long len, std::string& err);
+  int mps_get_site(int b, double* x, long long len, long long* len_out, std::string& err);
+  int mps_init(int N, int n_elec, int two_sz, int D, unsigned long long seed, std::string& err);
+
+  int build_env(int k, std::string& err);        // L_k, R_{k+2}, step k tables
+  int heff(const double* X, double* Y, int nvec, int precision, std::string& err);
+  double e_core() const { return e_core_; }
+
+  // accessors for the API layer
+  Step& step() { return step_; }
+  int N() const { return N_; }
+  QN target() const { return target_; }
+  int D() const { return D_; }
+  std::vector<Basis>& bonds() { return bonds_; }
+  std::vector<Site>& sites() { return sites_; }
+  Backend* be() { return be_; }
+  Catalogue& left(int k) { return Lcat_[k]; }
+  Catalogue& right(int k) { return Rcat_[k]; }
+
+  // pieces used by the sweep driver
+  int ensure_left(int k, std::string& err);
+  int ensure_right(int k, std::string& err);
+  int prepare_step(int k, std::string& err);
+  int grow_left(int k, std::string& err);   // L_{k+1} from L_k, site k (needs step k)
+  int grow_right(int k, std::string& err);  // R_{k+1} from R_{k+2}, site k+1 (needs step k)
+  void invalidate_left_from(int k);
+  void invalidate_right_from(int k);  // R_j for j <= k
+  int site_from_host(int b, const std::vector<SiteBlock>& blocks, const std::vector<double>& data,
+                     std::string& err);
+  void set_bond_basis(int b, const Basis& basis);
+
+  // integrals
+  double t(int p, int q) const;
+  double W(int p, int q, int r, int s) const;
+
+ private:
+  Backend* be_;
+  int N_ = 0;
+  std::vector<double> h_, v_;
+  double e_core_ = 0.0;
+  bool have_ints_ = false;
+  QN target_;
+  int D_ = 0;
+  bool have_mps_ = false;
+  std::vector<Basis> bonds_;  // left counted, 0..N
+  std::vector<Site> sites_;
+  std::vector<Catalogue> Lcat_;  // Lcat_[k]: orbitals 0..k-1
+  std::vector<Catalogue> Rcat_;  // Rcat_[k]: orbitals k..N-1
+  Step step_;
+
+  void free_cat(Catalogue& c);
+  void free_side(Side& s);
+  int alloc_cat(Catalogue& c, std::string& err);
+  void empty_left(Catalogue& c);
+  void empty_right(Catalogue& c);
+  void build_left_eops(const Catalogue& L, int site, Side& S);
+  void build_right_eops(const Catalogue& R, int site, Side& S);
+  void compile_side(Side& S, const Catalogue& cat, bool left);
+  int materialize(Side& S, Catalogue& cat, std::string& err);
+  int rotate(Side& S, const Catalogue& src, Catalogue& dst, int site, bool left, std::string& err);
+  void build_psi(int k);
+  void build_heff_tasks();
+};
+
+}  // namespace tns

@@ -1,0 +1,100 @@
+// hostcheck.cpp -- test-only build of the engine's host logic.
+//
+// Compiles the product's symbolic layer (engine.cpp: catalogues, enlarged
+// operators, work lists) against a plain-loop executor so that the CPU test
+// suite can check the operator algebra and the work lists against the
+// oracle without a GPU.  This library is built only by tests/ (symbols
+// tnshc_*); the product library never contains or loads it, and it is not a
+// fallback for anything: it has no Davidson, truncation or sweep.
+#include <cstdlib>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+
+#include "../../include/tns.h"
+#include "../../paper_2305_05581_gb300/csrc/engine.h"
+
+namespace {
+struct HostBackend : tns::Backend {
+  double* alloc(long long n) override { return (double*)std::calloc((size_t)n, sizeof(double)); }
+  void release(double* p) override { std::free(p); }
+  void upload(double* d, const double* s, long long n) override { std::memcpy(d, s, (size_t)n * 8); }
+  void download(double* d, const double* s, long long n) override { std::memcpy(d, s, (size_t)n * 8); }
+  void zero(double* p, long long n) override { std::memset(p, 0, (size_t)n * 8); }
+  void lincomb(const tns::LCList& l) override {
+    for (const auto& b : l.blocks)
+      for (int i = 0; i < b.rows; ++i)
+        for (int j = 0; j < b.cols; ++j) {
+          double s = 0.0;
+          for (int t = b.t0; t < b.t1; ++t) {
+            const auto& tm = l.terms[t];
+            if (!tm.src) s += (i == j) ? tm.c : 0.0;
+            else s += tm.c * (tm.tr ? tm.src[(long long)j * b.rows + i] : tm.src[(long long)i * b.cols + j]);
+          }
+          b.dst[(long long)i * b.cols + j] = s;
+        }
+  }
+  static double opL(const tns::Task& t, int i, int k) {
+    if (t.flags & tns::TF_LI) return i == k ? 1.0 : 0.0;
+    return (t.flags & tns::TF_LT) ? t.L[(long long)k * t.q + i] : t.L[(long long)i * t.m + k];
+  }
+  static double opX(const tns::Task& t, const double* X, int i, int j) {
+    if (t.flags & tns::TF_XI) return i == j ? 1.0 : 0.0;
+    return (t.flags & tns::TF_XT) ? X[(long long)j * t.m + i] : X[(long long)i * t.n + j];
+  }
+  static double opR(const tns::Task& t, int j, int k) {
+    if (t.flags & tns::TF_RI) return j == k ? 1.0 : 0.0;
+    return (t.flags & tns::TF_RT) ? t.R[(long long)k * t.r + j] : t.R[(long long)j * t.n + k];
+  }
+  void run(const tns::TaskList& tl, const double* xv, double* yv, int nvec, long long xs, long long ys,
+           int precision) override {
+    (void)precision;
+    for (int v = 0; v < nvec; ++v)
+      for (const auto& g : tl.groups) {
+        double* Y = yv + (long long)v * ys + g.yoff;
+        for (int i = 0; i < g.q * g.r; ++i) Y[i] = 0.0;
+        for (int ti = g.t0; ti < g.t1; ++ti) {
+          const tns::Task& t = tl.tasks[ti];
+          const double* X = (t.flags & tns::TF_XV) ? xv + (long long)v * xs + (long long)(uintptr_t)t.X : t.X;
+          for (int i = 0; i < t.q; ++i)
+            for (int j = 0; j < t.r; ++j) {
+              double s = 0.0;
+              for (int a = 0; a < t.m; ++a) {
+                double la = opL(t, i, a);
+                if (la == 0.0) continue;
+                for (int b = 0; b < t.n; ++b) s += la * opX(t, X, a, b) * opR(t, j, b);
+              }
+              Y[(long long)i * g.r + j] += t.alpha * s;
+            }
+        }
+      }
+  }
+  void sync() override {}
+  std::string error() override { return ""; }
+};
+}  // namespace
+
+static tns::Backend* make_backend(int, void*, std::string&) { return new HostBackend(); }
+static int backend_davidson(tns::Engine&, double*, double, int, int, double*, int*, std::string& err) {
+  err = "not available in the host-logic check library";
+  return -2;
+}
+static int backend_sweep(tns::Engine&, const tns_sweep_opts*, double*, tns_sweep_stats*, std::string& err) {
+  err = "not available in the host-logic check library";
+  return -2;
+}
+static int backend_diag(tns::Engine& e, double* diag, std::string&) {
+  tns::Step& st = e.step();
+  std::memset(diag, 0, (size_t)st.length * 8);
+  for (int ti : st.diag_tasks) {
+    const tns::Task& t = st.heff.tasks[ti];
+    const tns::PsiBlock& Y = st.psi[t.pad];
+    for (int i = 0; i < t.q; ++i)
+      for (int j = 0; j < t.r; ++j)
+        diag[Y.off + (long long)i * t.r + j] += t.alpha * HostBackend::opL(t, i, i) * HostBackend::opR(t, j, j);
+  }
+  return 0;
+}
+
+#define PFX(name) tnshc_##name
+#include "../../paper_2305_05581_gb300/csrc/api_impl.inc"
