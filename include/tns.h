@@ -166,6 +166,32 @@ typedef struct tns_sweep_stats {
  * optional (NULL). */
 int tns_sweep(tns_ctx* ctx, const tns_sweep_opts* opts, double* energy_out, tns_sweep_stats* stats);
 
+typedef struct tns_step_stats {
+  double energy;            /* Davidson eigenvalue (incl. e_core) */
+  double discarded;         /* discarded weight of the truncation */
+  int iters;                /* H_eff*psi products of the step */
+  int converged;            /* 1 if the Davidson tolerance was reached */
+  double heff_flops;        /* useful FP64-equivalent flops of those products */
+  double heff_seconds;      /* device time inside H_eff*psi (CUDA events on the context stream) */
+  double env_seconds;       /* partial sums, work lists and renormalisation */
+  double svd_seconds;       /* truncation */
+  double seconds;           /* wall time of the call */
+  long long length;         /* two-site wavefunction length */
+  int bond_dim;             /* new dimension of bond site+1 */
+} tns_step_stats;
+
+/* One two-site step of a sweep at (site, site+1) (one "DMRG iteration cycle",
+ * Sec. IV.A): environment (reused if current), Davidson on H_eff, truncation
+ * at bond site+1 to at most opts->D states, and renormalisation of the
+ * block that grows (left block if left_to_right, else right block).
+ * x0_host: optional HOST start vector in the layout of tns_psi_layout(site)
+ * (NULL: the two-site product of the current site tensors); psi_host:
+ * optional HOST output of the converged two-site wavefunction (same layout).
+ * Both are copied synchronously inside the call.  opts->nsweeps is ignored.
+ * Returns TNS_OK also when Davidson stops at max_iter (stats->converged = 0). */
+int tns_step(tns_ctx* ctx, int site, int left_to_right, const tns_sweep_opts* opts, const double* x0_host,
+             double* psi_host, tns_step_stats* stats);
+
 /* Useful FP64-equivalent flop count of one tns_heff_apply(site) for nvec = 1:
  * sum over products of p * min(2mr(n+q), 2qn(m+r)) (best chain order, the
  * matrix-chain choice of Sec. III.B), and the number of block products. */

@@ -21,7 +21,7 @@ DEFAULT_LIB = os.path.join(HERE, "libtns.so")
 # every entry point of include/tns.h
 SYMBOLS = ["create", "destroy", "last_error", "load_integrals", "mps_init", "mps_define",
            "mps_set_bond", "mps_set_site", "mps_get_bond", "mps_get_site", "build_env",
-           "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops"]
+           "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops", "step"]
 
 
 class TnsError(RuntimeError):
@@ -40,6 +40,13 @@ class SweepStats(C.Structure):
                 ("heff_flops", C.c_double), ("heff_seconds", C.c_double), ("env_seconds", C.c_double),
                 ("svd_seconds", C.c_double), ("seconds", C.c_double), ("steps", C.c_int),
                 ("max_bond", C.c_int)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("energy", C.c_double), ("discarded", C.c_double), ("iters", C.c_int), ("converged", C.c_int),
+                ("heff_flops", C.c_double), ("heff_seconds", C.c_double), ("env_seconds", C.c_double),
+                ("svd_seconds", C.c_double), ("seconds", C.c_double), ("length", C.c_longlong),
+                ("bond_dim", C.c_int)]
 
 
 _LIBS = {}
@@ -73,6 +80,7 @@ def load_library(path: str = DEFAULT_LIB, prefix: str = "tns_"):
         "davidson": (C.c_int, [vp, C.c_int, vp, C.c_double, C.c_int, C.c_int, dp, ip]),
         "sweep": (C.c_int, [vp, C.POINTER(SweepOpts), dp, C.POINTER(SweepStats)]),
         "heff_flops": (C.c_int, [vp, C.c_int, dp, llp]),
+        "step": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(SweepOpts), vp, vp, C.POINTER(StepStats)]),
     }
     for name, (res, args) in sig.items():
         fn = f(name)
@@ -201,6 +209,17 @@ class Context:
         st = SweepStats()
         self._check(self._fn("sweep")(self._h, C.byref(o), C.byref(e), C.byref(st)))
         return e.value, st
+
+
+    def step(self, site, left_to_right, D, tol=1e-8, max_iter=100, precision=TNS_FP64, cutoff=1e-14,
+             x0_host_ptr: int = 0, psi_host_ptr: int = 0):
+        """One two-site step; host pointers (0 = none) for the start vector / result."""
+        o = SweepOpts(1, D, tol, max_iter, precision, cutoff, 0)
+        st = StepStats()
+        self._check(self._fn("step")(self._h, site, int(left_to_right), C.byref(o),
+                                     C.c_void_p(x0_host_ptr) if x0_host_ptr else None,
+                                     C.c_void_p(psi_host_ptr) if psi_host_ptr else None, C.byref(st)))
+        return st
 
 
 def blocks_to_vector(desc, length, blocks: dict) -> np.ndarray:

@@ -1,0 +1,96 @@
+// cuda_backend.h -- CUDA backend of the engine (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+namespace tns {
+
+struct Tile {  // an output tile of a group: rows [row0, row0+nrows), cols [col0, col0+ncols)
+  int g;
+  int row0, col0, nrows, ncols;
+};
+
+// device copy of a work list; tiles split into size classes
+struct DevList {
+  long long gen = -1;
+  Task* tasks = nullptr;
+  Group* groups = nullptr;
+  Tile* tiles = nullptr;
+  int ncls[3] = {0, 0, 0};   // tiles per size class (contiguous, class 0 first)
+  int ntiles = 0;
+  // tensor-core form (precision != FP64)
+  void* tc = nullptr;
+  long long tc_gen = -1;
+};
+
+class CudaBackend : public Backend {
+ public:
+  CudaBackend(int device, cudaStream_t s, bool own) : device_(device), stream_(s), own_(own) {}
+  ~CudaBackend() override;
+  double* alloc(long long n) override;
+  void release(double* p) override;
+  void upload(double* dst, const double* src, long long n) override;
+  void download(double* dst, const double* src, long long n) override;
+  void zero(double* p, long long n) override;
+  void lincomb(const LCList& l) override;
+  void run(const TaskList& tl, const double* xv, double* yv, int nvec, long long xs, long long ys,
+           int precision) override;
+  void sync() override;
+  std::string error() override;
+
+  cudaStream_t stream() const { return stream_; }
+  int device() const { return device_; }
+  void note(cudaError_t e, const char* what);
+  // persistent device copy of a task list (uploaded when tl.gen changes)
+  DevList& dev(const TaskList& tl);
+  void drop(const TaskList& tl);
+  // scratch device memory owned by the backend (grows, never shrinks)
+  void* scratch(size_t bytes, int slot);
+  // counted launches of the engine's own kernels
+  long long launches = 0;
+  float last_ms = 0.f;
+
+ private:
+  int device_;
+  cudaStream_t stream_;
+  bool own_;
+  std::string err_;
+  std::map<const TaskList*, DevList> lists_;
+  std::vector<std::pair<void*, size_t>> scratch_ = std::vector<std::pair<void*, size_t>>(8, {nullptr, 0});
+  void upload_list(const TaskList& tl, DevList& d);
+  void free_list(DevList& d);
+};
+
+// kernels used by the solver (defined in kernels.cu)
+void launch_heff_diag(CudaBackend& be, const Task* d_tasks, const int* d_idx, const int* d_rng, int ngroups,
+                      const Group* d_groups, double* diag);
+void launch_multidot(CudaBackend& be, const double* V, long long ldv, int k, const double* w, long long n,
+                     double* out);
+void launch_axpy_multi(CudaBackend& be, const double* V, long long ldv, int k, const double* coef, double sign,
+                       double* w, long long n);
+void launch_combine(CudaBackend& be, const double* V, long long ldv, int k, const double* coef, double* out,
+                    long long n);
+void launch_scale(CudaBackend& be, double* x, const double* num, int inv_sqrt, long long n);
+void launch_precond(CudaBackend& be, const double* r, const double* diag, const double* theta, double* t,
+                    long long n);
+void launch_residual(CudaBackend& be, const double* AVs, const double* x, const double* theta, double* r,
+                     long long n);
+// batched symmetric eigensolver (cyclic Jacobi), matrices column-major == row-major (symmetric)
+// A: nmat matrices at A + off[i] with size n[i]; V: eigenvectors (columns) at V + off[i]; w: eigenvalues at w + woff[i]
+void launch_jacobi(CudaBackend& be, double* A, double* V, double* w, const long long* off, const int* n,
+                   const int* woff, int nmat, int maxn, int* sweeps_out);
+void launch_select(CudaBackend& be, const double* w, const int* sec_of, int total, int keep_max, double cut,
+                   int* keep_flag, double* disc);
+void launch_gather(CudaBackend& be, const double* src, const long long* so, const int* sld, double* dst,
+                   const long long* dof, const int* dld, const int* rows, const int* cols, const int* trans,
+                   int nblk);
+void launch_argmin(CudaBackend& be, const double* x, long long n, long long* idx);
+void launch_fill_unit(CudaBackend& be, double* x, long long n, const long long* idx);
+
+}  // namespace tns

@@ -305,6 +305,14 @@ static void site_layout(const Basis& l, const Basis& r, std::vector<SiteBlock>& 
     }
 }
 
+int Engine::alloc_site(int b, std::string& err) {
+  std::vector<SiteBlock> blocks;
+  site_layout(bonds_[b], bonds_[b + 1], blocks);
+  int rc = site_from_host(b, blocks, std::vector<double>(), err);
+  if (!rc) be_->zero(sites_[b].d, std::max(sites_[b].size, 1LL));
+  return rc;
+}
+
 int Engine::mps_set_site(int b, const double* x, long long len, std::string& err) {
   if (!have_mps_ || b < 0 || b >= N_ || !x || bonds_[b].size() == 0 || bonds_[b + 1].size() == 0) {
     err = "mps_set_site: bad site index, or bonds b and b+1 not set";
@@ -1369,9 +1377,13 @@ void Engine::build_heff_tasks() {
   }
   tl.nprod = (long long)tl.tasks.size();
   st.diag_tasks.clear();
-  for (int g = 0; g < (int)tl.groups.size(); ++g)
+  st.diag_rng.assign(1, 0);
+  for (int g = 0; g < (int)tl.groups.size(); ++g) {
     for (int i = tl.groups[g].t0; i < tl.groups[g].t1; ++i)
       if (tl.tasks[i].pad == g) st.diag_tasks.push_back(i);
+    st.diag_rng.push_back((int)st.diag_tasks.size());
+  }
+  tl.persistent = true;
 }
 
 int Engine::prepare_step(int k, std::string& err) {
@@ -1440,6 +1452,7 @@ int Engine::heff(const double* X, double* Y, int nvec, int precision, std::strin
     return -2;
   }
   be_->run(step_.heff, X, Y, nvec, step_.length, step_.length, precision);
+  be_->sync();
   std::string e = be_->error();
   if (!e.empty()) {
     err = e;

@@ -229,7 +229,9 @@ struct TaskList {
   std::vector<Group> groups;
   double flops = 0.0;
   long long nprod = 0;
-  void clear() { tasks.clear(); groups.clear(); flops = 0; nprod = 0; }
+  long long gen = 0;        // bumped on every rebuild (device copies keyed on it)
+  bool persistent = false;  // kept on the device between runs
+  void clear() { tasks.clear(); groups.clear(); flops = 0; nprod = 0; ++gen; }
 };
 
 struct LCTerm {
@@ -307,7 +309,8 @@ struct Step {
   std::vector<long long> desc;
   long long length = 0;
   TaskList heff;
-  std::vector<int> diag_tasks;  // tasks contributing to the diagonal
+  std::vector<int> diag_tasks;  // tasks contributing to the diagonal, in group order
+  std::vector<int> diag_rng;    // per group: range [diag_rng[g], diag_rng[g+1]) of diag_tasks
   bool valid = false;
 };
 
@@ -348,6 +351,7 @@ class Engine {
   void invalidate_right_from(int k);  // R_j for j <= k
   int site_from_host(int b, const std::vector<SiteBlock>& blocks, const std::vector<double>& data,
                      std::string& err);
+  int alloc_site(int b, std::string& err);  // layout from bonds b, b+1; zeroed device storage
   void set_bond_basis(int b, const Basis& basis);
 
   // integrals

@@ -1,0 +1,785 @@
+// kernels.cu -- FP64 kernels of the engine and the CUDA backend (sm_103a).
+//
+// The grouped triple product (Eq. 2, Alg. 2):
+//     Y_tile = sum_{tasks of the tile's output block} alpha * op(L) op(X) op(R)^T
+// One CTA owns one output tile (<= 64 x 64) of one output block and walks
+// that block's task list in a fixed order, so every run is bitwise
+// reproducible and no atomics are needed.  The position sum of Eq. (2) (and
+// the sum over all operator pairs and dot blocks that hit the block) is the
+// K loop of the accumulation, as in Alg. 2 where the sum over i becomes the
+// inner dimension of one GEMM.  Each task is evaluated in the cheaper chain
+// order: L (X R^T) or (L X) R^T, with the intermediate chunk in shared
+// memory.  FP64 on GB300 is DFMA-issue bound, so the kernel keeps every
+// DFMA useful (loops run to the exact block sizes, no zero padding) and
+// sizes its CTA to the tile so that few lanes idle.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "cuda_backend.h"
+
+namespace tns {
+
+// ---------------------------------------------------------------------------
+// operand access
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double opL(const Task& t, int i, int k) {
+  if (t.flags & TF_LI) return i == k ? 1.0 : 0.0;
+  return (t.flags & TF_LT) ? __ldg(t.L + (long long)k * t.q + i) : __ldg(t.L + (long long)i * t.m + k);
+}
+__device__ __forceinline__ double opX(const Task& t, const double* X, int i, int j) {
+  if (t.flags & TF_XI) return i == j ? 1.0 : 0.0;
+  return (t.flags & TF_XT) ? __ldg(X + (long long)j * t.m + i) : __ldg(X + (long long)i * t.n + j);
+}
+__device__ __forceinline__ double opR(const Task& t, int j, int k) {
+  if (t.flags & TF_RI) return j == k ? 1.0 : 0.0;
+  return (t.flags & TF_RT) ? __ldg(t.R + (long long)k * t.r + j) : __ldg(t.R + (long long)j * t.n + k);
+}
+
+constexpr int CH = 32;          // chunk of the contracted middle dimension
+constexpr int SPITCH = 65;      // shared-memory pitch of the intermediate (64 cols + 1)
+constexpr int SMEM_D = 64 * SPITCH;
+
+template <int NT, int ACC>
+__global__ void __launch_bounds__(NT) k_tasks_fp64(const Task* __restrict__ tasks, const Group* __restrict__ groups,
+                                                   const Tile* __restrict__ tiles, int tile0, const double* xv,
+                                                   double* yv, long long xs, long long ys) {
+  __shared__ double S[SMEM_D];
+  const Tile T = tiles[tile0 + blockIdx.x];
+  const Group G = groups[T.g];
+  const int vec = blockIdx.y;
+  const double* X0 = xv ? xv + (long long)vec * xs : nullptr;
+  double* Y = yv + (long long)vec * ys + G.yoff;
+  const int nc = T.ncols, nr = T.nrows;
+  const int nout = nr * nc;
+  double acc[ACC];
+#pragma unroll
+  for (int u = 0; u < ACC; ++u) acc[u] = 0.0;
+
+  for (int ti = G.t0; ti < G.t1; ++ti) {
+    const Task tk = tasks[ti];
+    const double* Xp = (tk.flags & TF_XV) ? X0 + (long long)(size_t)tk.X : tk.X;
+    const double a = tk.alpha;
+    const int f = tk.flags;
+    if ((f & TF_LI) && (f & TF_RI)) {
+#pragma unroll
+      for (int u = 0; u < ACC; ++u) {
+        int e = threadIdx.x + u * NT;
+        if (e < nout) acc[u] += a * opX(tk, Xp, T.row0 + e / nc, T.col0 + e % nc);
+      }
+    } else if (f & (TF_LI | TF_RI | TF_XI)) {
+      // two-factor products: contract directly
+#pragma unroll
+      for (int u = 0; u < ACC; ++u) {
+        int e = threadIdx.x + u * NT;
+        if (e >= nout) continue;
+        int i = T.row0 + e / nc, j = T.col0 + e % nc;
+        double s = 0.0;
+        if (f & TF_LI) {
+          for (int k = 0; k < tk.n; ++k) s = fma(opX(tk, Xp, i, k), opR(tk, j, k), s);
+        } else if (f & TF_RI) {
+          for (int k = 0; k < tk.m; ++k) s = fma(opL(tk, i, k), opX(tk, Xp, k, j), s);
+        } else {
+          for (int k = 0; k < tk.m; ++k) s = fma(opL(tk, i, k), opR(tk, j, k), s);
+        }
+        acc[u] = fma(a, s, acc[u]);
+      }
+    } else if (!(f & TF_ORDB)) {
+      // L (X R^T): chunks of CH rows of X
+      for (int m0 = 0; m0 < tk.m; m0 += CH) {
+        const int mc = min(CH, tk.m - m0);
+        for (int e = threadIdx.x; e < mc * nc; e += NT) {
+          int i = e / nc, j = e % nc;
+          double s = 0.0;
+          for (int k = 0; k < tk.n; ++k) s = fma(opX(tk, Xp, m0 + i, k), opR(tk, T.col0 + j, k), s);
+          S[i * SPITCH + j] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < ACC; ++u) {
+          int e = threadIdx.x + u * NT;
+          if (e >= nout) continue;
+          int i = e / nc, j = e % nc;
+          double s = 0.0;
+          for (int k = 0; k < mc; ++k) s = fma(opL(tk, T.row0 + i, m0 + k), S[k * SPITCH + j], s);
+          acc[u] = fma(a, s, acc[u]);
+        }
+        __syncthreads();
+      }
+    } else {
+      // (L X) R^T: chunks of CH columns of X
+      for (int n0 = 0; n0 < tk.n; n0 += CH) {
+        const int ncc = min(CH, tk.n - n0);
+        for (int e = threadIdx.x; e < nr * ncc; e += NT) {
+          int i = e / ncc, j = e % ncc;
+          double s = 0.0;
+          for (int k = 0; k < tk.m; ++k) s = fma(opL(tk, T.row0 + i, k), opX(tk, Xp, k, n0 + j), s);
+          S[i * (CH + 1) + j] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < ACC; ++u) {
+          int e = threadIdx.x + u * NT;
+          if (e >= nout) continue;
+          int i = e / nc, j = e % nc;
+          double s = 0.0;
+          for (int k = 0; k < ncc; ++k) s = fma(S[i * (CH + 1) + k], opR(tk, T.col0 + j, n0 + k), s);
+          acc[u] = fma(a, s, acc[u]);
+        }
+        __syncthreads();
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < ACC; ++u) {
+    int e = threadIdx.x + u * NT;
+    if (e < nout) Y[(long long)(T.row0 + e / nc) * G.r + T.col0 + e % nc] = acc[u];
+  }
+}
+
+// size classes: (threads, outputs per thread)
+constexpr int C0_NT = 32, C0_ACC = 4;    // <= 128 outputs
+constexpr int C1_NT = 128, C1_ACC = 8;   // <= 1024 outputs
+constexpr int C2_NT = 256, C2_ACC = 16;  // <= 4096 outputs (64 x 64)
+
+// ---------------------------------------------------------------------------
+// partial sums (materialised linear combinations of operator blocks)
+// ---------------------------------------------------------------------------
+__global__ void k_lincomb(const LCBlock* __restrict__ blocks, int nb, const LCTerm* __restrict__ terms) {
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    const LCBlock B = blocks[b];
+    const int n = B.rows * B.cols;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int i = e / B.cols, j = e % B.cols;
+      double s = 0.0;
+      for (int t = B.t0; t < B.t1; ++t) {
+        const LCTerm T = terms[t];
+        double x;
+        if (!T.src) x = (i == j) ? 1.0 : 0.0;
+        else x = T.tr ? __ldg(T.src + (long long)j * B.rows + i) : __ldg(T.src + e);
+        s = fma(T.c, x, s);
+      }
+      B.dst[e] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// H_eff diagonal: diag(Y_blk)_{ij} = sum alpha op(L)_ii op(R)_jj over the
+// tasks mapping a block onto itself (fixed order per block)
+// ---------------------------------------------------------------------------
+__global__ void k_heff_diag(const Task* __restrict__ tasks, const int* __restrict__ idx, const int* __restrict__ rng,
+                            int ngroups, const Group* __restrict__ groups, double* diag) {
+  for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const Group G = groups[g];
+    const int n = G.q * G.r;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int i = e / G.r, j = e % G.r;
+      double s = 0.0;
+      for (int t = rng[g]; t < rng[g + 1]; ++t) {
+        const Task tk = tasks[idx[t]];
+        s = fma(tk.alpha, opL(tk, i, i) * opR(tk, j, j), s);
+      }
+      diag[G.yoff + e] = s;
+    }
+  }
+}
+
+void launch_heff_diag(CudaBackend& be, const Task* d_tasks, const int* d_idx, const int* d_rng, int ngroups,
+                      const Group* d_groups, double* diag) {
+  if (ngroups <= 0) return;
+  k_heff_diag<<<std::min(ngroups, 65535), 128, 0, be.stream()>>>(d_tasks, d_idx, d_rng, ngroups, d_groups, diag);
+  be.launches++;
+  be.note(cudaGetLastError(), "k_heff_diag");
+}
+
+// ---------------------------------------------------------------------------
+// FP64 vector kernels for the Davidson step (deterministic reductions)
+// ---------------------------------------------------------------------------
+constexpr int RED_BLOCKS = 304;  // 2 x 152 SMs
+constexpr int RED_NT = 256;
+constexpr int MAXK = 40;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial[i * gridDim.x + blk] = sum over this block's slice of V_i . w
+__global__ void __launch_bounds__(RED_NT) k_multidot(const double* __restrict__ V, long long ldv, int k,
+                                                     const double* __restrict__ w, long long n,
+                                                     double* __restrict__ partial) {
+  __shared__ double red[RED_NT / 32][MAXK];
+  double acc[MAXK];
+  for (int i = 0; i < k; ++i) acc[i] = 0.0;
+  for (long long j = blockIdx.x * (long long)RED_NT + threadIdx.x; j < n; j += (long long)gridDim.x * RED_NT) {
+    const double x = w[j];
+    for (int i = 0; i < k; ++i) acc[i] = fma(V[i * ldv + j], x, acc[i]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = 0; i < k; ++i) {
+    double s = warp_sum(acc[i]);
+    if (lane == 0) red[wid][i] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double s = 0.0;
+    for (int q = 0; q < RED_NT / 32; ++q) s += red[q][threadIdx.x];
+    partial[threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nb, int k, double* out) {
+  // one warp per output, fixed order
+  const int i = blockIdx.x;
+  if (i >= k) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 32) s += partial[i * nb + b];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) out[i] = s;
+}
+
+void launch_multidot(CudaBackend& be, const double* V, long long ldv, int k, const double* w, long long n,
+                     double* out) {
+  if (k <= 0) return;
+  if (k > MAXK) {
+    be.note(cudaErrorInvalidValue, "multidot: too many vectors");
+    return;
+  }
+  double* partial = (double*)be.scratch(sizeof(double) * MAXK * RED_BLOCKS, 0);
+  k_multidot<<<RED_BLOCKS, RED_NT, 0, be.stream()>>>(V, ldv, k, w, n, partial);
+  k_reduce_partials<<<k, 32, 0, be.stream()>>>(partial, RED_BLOCKS, k, out);
+  be.launches += 2;
+  be.note(cudaGetLastError(), "multidot");
+}
+
+// w += sign * sum_i coef[i] V_i
+__global__ void k_axpy_multi(const double* __restrict__ V, long long ldv, int k, const double* __restrict__ coef,
+                             double sign, double* w, long long n) {
+  __shared__ double c[MAXK];
+  if (threadIdx.x < k) c[threadIdx.x] = sign * coef[threadIdx.x];
+  __syncthreads();
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    double s = w[j];
+    for (int i = 0; i < k; ++i) s = fma(c[i], V[i * ldv + j], s);
+    w[j] = s;
+  }
+}
+
+void launch_axpy_multi(CudaBackend& be, const double* V, long long ldv, int k, const double* coef, double sign,
+                       double* w, long long n) {
+  if (k <= 0) return;
+  k_axpy_multi<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(V, ldv, k, coef, sign, w, n);
+  be.launches++;
+  be.note(cudaGetLastError(), "axpy_multi");
+}
+
+__global__ void k_combine(const double* __restrict__ V, long long ldv, int k, const double* __restrict__ coef,
+                          double* out, long long n) {
+  __shared__ double c[MAXK];
+  if (threadIdx.x < k) c[threadIdx.x] = coef[threadIdx.x];
+  __syncthreads();
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s = fma(c[i], V[i * ldv + j], s);
+    out[j] = s;
+  }
+}
+
+void launch_combine(CudaBackend& be, const double* V, long long ldv, int k, const double* coef, double* out,
+                    long long n) {
+  k_combine<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(V, ldv, k, coef, out, n);
+  be.launches++;
+  be.note(cudaGetLastError(), "combine");
+}
+
+// x *= f(num): inv_sqrt ? 1/sqrt(num) : num
+__global__ void k_scale(double* x, const double* num, int inv_sqrt, long long n) {
+  const double v = *num;
+  const double s = inv_sqrt ? (v > 0.0 ? 1.0 / sqrt(v) : 0.0) : v;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    x[j] *= s;
+}
+
+void launch_scale(CudaBackend& be, double* x, const double* num, int inv_sqrt, long long n) {
+  k_scale<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(x, num, inv_sqrt, n);
+  be.launches++;
+  be.note(cudaGetLastError(), "scale");
+}
+
+// Davidson correction t = r / (theta - d), denominator floored at 1e-12
+__global__ void k_precond(const double* r, const double* diag, const double* theta, double* t, long long n) {
+  const double th = *theta;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    double den = th - diag[j];
+    if (fabs(den) < 1e-12) den = den < 0 ? -1e-12 : 1e-12;
+    t[j] = r[j] / den;
+  }
+}
+
+void launch_precond(CudaBackend& be, const double* r, const double* diag, const double* theta, double* t,
+                    long long n) {
+  k_precond<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(r, diag, theta, t, n);
+  be.launches++;
+  be.note(cudaGetLastError(), "precond");
+}
+
+// r = AVs - theta x
+__global__ void k_residual(const double* AVs, const double* x, const double* theta, double* r, long long n) {
+  const double th = *theta;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    r[j] = fma(-th, x[j], AVs[j]);
+}
+
+void launch_residual(CudaBackend& be, const double* AVs, const double* x, const double* theta, double* r,
+                     long long n) {
+  k_residual<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(AVs, x, theta, r, n);
+  be.launches++;
+  be.note(cudaGetLastError(), "residual");
+}
+
+__global__ void k_argmin(const double* x, long long n, long long* idx) {
+  __shared__ double bv[1024];
+  __shared__ long long bi[1024];
+  double v = 1e300;
+  long long id = 0;
+  for (long long j = threadIdx.x; j < n; j += blockDim.x)
+    if (x[j] < v) {
+      v = x[j];
+      id = j;
+    }
+  bv[threadIdx.x] = v;
+  bi[threadIdx.x] = id;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      double v2 = bv[threadIdx.x + s];
+      long long i2 = bi[threadIdx.x + s];
+      if (v2 < bv[threadIdx.x] || (v2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
+        bv[threadIdx.x] = v2;
+        bi[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *idx = bi[0];
+}
+
+void launch_argmin(CudaBackend& be, const double* x, long long n, long long* idx) {
+  k_argmin<<<1, 1024, 0, be.stream()>>>(x, n, idx);
+  be.launches++;
+  be.note(cudaGetLastError(), "argmin");
+}
+
+__global__ void k_fill_unit(double* x, long long n, const long long* idx) {
+  const long long id = *idx;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    x[j] = (j == id) ? 1.0 : 0.0;
+}
+
+void launch_fill_unit(CudaBackend& be, double* x, long long n, const long long* idx) {
+  k_fill_unit<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(x, n, idx);
+  be.launches++;
+  be.note(cudaGetLastError(), "fill_unit");
+}
+
+// ---------------------------------------------------------------------------
+// batched symmetric eigensolver: parallel cyclic Jacobi (round-robin pairs),
+// one CTA per matrix, matrices in global memory; bounded number of sweeps
+// ---------------------------------------------------------------------------
+constexpr int JAC_NT = 256;
+constexpr int JAC_MAXSWEEP = 40;
+constexpr int JAC_MAXPAIR = 1024;  // n <= 2048
+
+__global__ void __launch_bounds__(JAC_NT) k_jacobi(double* A, double* V, double* w, const long long* off,
+                                                   const int* nn, const int* woff, int* sweeps_out) {
+  __shared__ double cs[JAC_MAXPAIR], sn[JAC_MAXPAIR];
+  __shared__ int pp[JAC_MAXPAIR], qq[JAC_MAXPAIR];
+  __shared__ double red[JAC_NT / 32];
+  __shared__ int done;
+  const int mi = blockIdx.x;
+  const int n = nn[mi];
+  double* a = A + off[mi];
+  double* v = V + off[mi];
+  for (long long e = threadIdx.x; e < (long long)n * n; e += JAC_NT) v[e] = ((e / n) == (e % n)) ? 1.0 : 0.0;
+  __syncthreads();
+  const int ne = n + (n & 1);
+  const int np = ne / 2;
+  int sweep = 0;
+  for (; sweep < JAC_MAXSWEEP && n > 1; ++sweep) {
+    // convergence test: off-diagonal vs diagonal Frobenius norm
+    double off2 = 0.0, dia2 = 0.0;
+    for (long long e = threadIdx.x; e < (long long)n * n; e += JAC_NT) {
+      double x = a[e];
+      if ((e / n) == (e % n)) dia2 += x * x;
+      else off2 += x * x;
+    }
+    off2 = warp_sum(off2);
+    dia2 = warp_sum(dia2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = off2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0;
+      for (int q = 0; q < JAC_NT / 32; ++q) s += red[q];
+      red[0] = s;
+    }
+    __syncthreads();
+    off2 = red[0];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dia2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0;
+      for (int q = 0; q < JAC_NT / 32; ++q) s += red[q];
+      done = (off2 <= 1e-30 * (s + off2)) || off2 < 1e-300;
+    }
+    __syncthreads();
+    if (done) break;
+    for (int round = 0; round < ne - 1; ++round) {
+      for (int k = threadIdx.x; k < np; k += JAC_NT) {
+        int p, q;
+        if (k == 0) {
+          p = round;
+          q = ne - 1;
+        } else {
+          p = (round + k) % (ne - 1);
+          q = (round - k + (ne - 1)) % (ne - 1);
+        }
+        if (p > q) {
+          int t = p;
+          p = q;
+          q = t;
+        }
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          double apq = a[(long long)p * n + q];
+          if (apq != 0.0) {
+            double app = a[(long long)p * n + p], aqq = a[(long long)q * n + q];
+            double tau = (aqq - app) / (2.0 * apq);
+            double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        cs[k] = c;
+        sn[k] = s;
+        pp[k] = p;
+        qq[k] = q;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (long long e = threadIdx.x; e < (long long)np * n; e += JAC_NT) {
+        int k = (int)(e / n), j = (int)(e % n);
+        int p = pp[k], q = qq[k];
+        if (q >= n || sn[k] == 0.0) continue;
+        double c = cs[k], s = sn[k];
+        double x = a[(long long)p * n + j], y = a[(long long)q * n + j];
+        a[(long long)p * n + j] = c * x - s * y;
+        a[(long long)q * n + j] = s * x + c * y;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (long long e = threadIdx.x; e < (long long)np * n; e += JAC_NT) {
+        int k = (int)(e / n), i = (int)(e % n);
+        int p = pp[k], q = qq[k];
+        if (q >= n || sn[k] == 0.0) continue;
+        double c = cs[k], s = sn[k];
+        double x = a[(long long)i * n + p], y = a[(long long)i * n + q];
+        a[(long long)i * n + p] = c * x - s * y;
+        a[(long long)i * n + q] = s * x + c * y;
+        x = v[(long long)i * n + p];
+        y = v[(long long)i * n + q];
+        v[(long long)i * n + p] = c * x - s * y;
+        v[(long long)i * n + q] = s * x + c * y;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += JAC_NT) w[woff[mi] + i] = a[(long long)i * n + i];
+  if (threadIdx.x == 0 && sweeps_out) sweeps_out[mi] = sweep;
+}
+
+void launch_jacobi(CudaBackend& be, double* A, double* V, double* w, const long long* off, const int* n,
+                   const int* woff, int nmat, int maxn, int* sweeps_out) {
+  if (nmat <= 0) return;
+  if (maxn > 2 * JAC_MAXPAIR) {
+    be.note(cudaErrorInvalidValue, "jacobi: matrix too large");
+    return;
+  }
+  k_jacobi<<<nmat, JAC_NT, 0, be.stream()>>>(A, V, w, off, n, woff, sweeps_out);
+  be.launches++;
+  be.note(cudaGetLastError(), "jacobi");
+}
+
+// ---------------------------------------------------------------------------
+// global truncation: keep the `keep_max` largest eigenvalues (> cut) over all
+// sectors; ties broken by (sector, index).  One CTA, bitonic sort in global
+// scratch.  keep_flag[i] = 1 for kept entries, disc = discarded weight.
+// ---------------------------------------------------------------------------
+__global__ void k_select(const double* w, const int* sec_of, int total, int P, int keep_max, double cut,
+                         double* kv, int* ki, int* keep_flag, double* disc) {
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    kv[i] = i < total ? w[i] : -1e300;
+    ki[i] = i < total ? i : 0x7fffffff;
+  }
+  __syncthreads();
+  // sort descending by value, ascending by index on ties (index order = (sector, in-sector))
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        int l = i ^ j;
+        if (l > i) {
+          bool desc = ((i & k) == 0);
+          double a = kv[i], b = kv[l];
+          int ia = ki[i], ib = ki[l];
+          bool a_first = (a > b) || (a == b && ia < ib);
+          if (desc ? !a_first : a_first) {
+            kv[i] = b;
+            kv[l] = a;
+            ki[i] = ib;
+            ki[l] = ia;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < total; i += blockDim.x) keep_flag[i] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < total; i += blockDim.x)
+    if (i < keep_max && kv[i] > cut) keep_flag[ki[i]] = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double d = 0.0;
+    for (int i = 0; i < total; ++i)
+      if (!(i < keep_max && kv[i] > cut)) d += fmax(kv[i], 0.0);
+    *disc = d;
+  }
+  (void)sec_of;
+}
+
+void launch_select(CudaBackend& be, const double* w, const int* sec_of, int total, int keep_max, double cut,
+                   int* keep_flag, double* disc) {
+  int P = 1;
+  while (P < total) P <<= 1;
+  double* kv = (double*)be.scratch(sizeof(double) * P + 64, 1);
+  int* ki = (int*)be.scratch(sizeof(int) * P + 64, 2);
+  k_select<<<1, 1024, 0, be.stream()>>>(w, sec_of, total, P, keep_max, cut, kv, ki, keep_flag, disc);
+  be.launches++;
+  be.note(cudaGetLastError(), "select");
+}
+
+// strided block copies: dst[i*dld + j] = trans ? src[j*sld + i] : src[i*sld + j]
+__global__ void k_gather(const double* src, const long long* so, const int* sld, double* dst, const long long* dof,
+                         const int* dld, const int* rows, const int* cols, const int* trans, int nblk) {
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const double* s = src + so[b];
+    double* d = dst + dof[b];
+    const int R = rows[b], Cn = cols[b], ls = sld[b], ld = dld[b], tr = trans[b];
+    for (int e = threadIdx.x; e < R * Cn; e += blockDim.x) {
+      int i = e / Cn, j = e % Cn;
+      d[(long long)i * ld + j] = tr ? s[(long long)j * ls + i] : s[(long long)i * ls + j];
+    }
+  }
+}
+
+void launch_gather(CudaBackend& be, const double* src, const long long* so, const int* sld, double* dst,
+                   const long long* dof, const int* dld, const int* rows, const int* cols, const int* trans,
+                   int nblk) {
+  if (nblk <= 0) return;
+  k_gather<<<std::min(nblk, 65535), 128, 0, be.stream()>>>(src, so, sld, dst, dof, dld, rows, cols, trans, nblk);
+  be.launches++;
+  be.note(cudaGetLastError(), "gather");
+}
+
+// ---------------------------------------------------------------------------
+// backend
+// ---------------------------------------------------------------------------
+CudaBackend::~CudaBackend() {
+  for (auto& kv : lists_) free_list(kv.second);
+  for (auto& s : scratch_)
+    if (s.first) cudaFree(s.first);
+  if (own_ && stream_) cudaStreamDestroy(stream_);
+}
+
+void CudaBackend::note(cudaError_t e, const char* what) {
+  if (e != cudaSuccess && err_.empty()) err_ = std::string(what) + ": " + cudaGetErrorString(e);
+}
+
+std::string CudaBackend::error() {
+  std::string e = err_;
+  err_.clear();
+  return e;
+}
+
+double* CudaBackend::alloc(long long n) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, (size_t)n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (double*)p;
+}
+
+void CudaBackend::release(double* p) {
+  if (p) {
+    cudaStreamSynchronize(stream_);
+    cudaFree(p);
+  }
+}
+
+void CudaBackend::upload(double* dst, const double* src, long long n) {
+  note(cudaMemcpyAsync(dst, src, (size_t)n * 8, cudaMemcpyHostToDevice, stream_), "upload");
+  note(cudaStreamSynchronize(stream_), "upload");
+}
+
+void CudaBackend::download(double* dst, const double* src, long long n) {
+  note(cudaMemcpyAsync(dst, src, (size_t)n * 8, cudaMemcpyDeviceToHost, stream_), "download");
+  note(cudaStreamSynchronize(stream_), "download");
+}
+
+void CudaBackend::zero(double* p, long long n) { note(cudaMemsetAsync(p, 0, (size_t)n * 8, stream_), "zero"); }
+
+void CudaBackend::sync() { note(cudaStreamSynchronize(stream_), "sync"); }
+
+void* CudaBackend::scratch(size_t bytes, int slot) {
+  auto& s = scratch_[slot];
+  if (s.second < bytes) {
+    if (s.first) {
+      cudaStreamSynchronize(stream_);
+      cudaFree(s.first);
+    }
+    s.first = nullptr;
+    s.second = 0;
+    if (cudaMalloc(&s.first, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      note(cudaErrorMemoryAllocation, "scratch");
+      return nullptr;
+    }
+    s.second = bytes;
+  }
+  return s.first;
+}
+
+template <typename T>
+static T* dev_copy(const std::vector<T>& v, CudaBackend& be) {
+  if (v.empty()) return nullptr;
+  void* p = nullptr;
+  if (cudaMalloc(&p, v.size() * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    be.note(cudaErrorMemoryAllocation, "work list upload");
+    return nullptr;
+  }
+  be.note(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, be.stream()), "work list upload");
+  return (T*)p;
+}
+
+void CudaBackend::free_list(DevList& d) {
+  cudaStreamSynchronize(stream_);
+  if (d.tasks) cudaFree(d.tasks);
+  if (d.groups) cudaFree(d.groups);
+  if (d.tiles) cudaFree(d.tiles);
+  if (d.tc) cudaFree(d.tc);
+  d = DevList();
+}
+
+void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
+  free_list(d);
+  // tiles of at most 64 x 64, split into size classes
+  std::vector<Tile> cls[3];
+  for (int g = 0; g < (int)tl.groups.size(); ++g) {
+    const Group& G = tl.groups[g];
+    for (int r0 = 0; r0 < G.q; r0 += 64)
+      for (int c0 = 0; c0 < G.r; c0 += 64) {
+        Tile t;
+        t.g = g;
+        t.row0 = r0;
+        t.col0 = c0;
+        t.nrows = std::min(64, G.q - r0);
+        t.ncols = std::min(64, G.r - c0);
+        int nout = t.nrows * t.ncols;
+        int c = nout <= C0_NT * C0_ACC ? 0 : nout <= C1_NT * C1_ACC ? 1 : 2;
+        cls[c].push_back(t);
+      }
+  }
+  std::vector<Tile> all;
+  for (int c = 0; c < 3; ++c) {
+    d.ncls[c] = (int)cls[c].size();
+    all.insert(all.end(), cls[c].begin(), cls[c].end());
+  }
+  d.ntiles = (int)all.size();
+  d.tasks = dev_copy(tl.tasks, *this);
+  d.groups = dev_copy(tl.groups, *this);
+  d.tiles = dev_copy(all, *this);
+  d.gen = tl.gen;
+  note(cudaStreamSynchronize(stream_), "work list upload");
+}
+
+DevList& CudaBackend::dev(const TaskList& tl) {
+  DevList& d = lists_[&tl];
+  if (d.gen != tl.gen) upload_list(tl, d);
+  return d;
+}
+
+void CudaBackend::drop(const TaskList& tl) {
+  auto it = lists_.find(&tl);
+  if (it != lists_.end()) {
+    free_list(it->second);
+    lists_.erase(it);
+  }
+}
+
+void launch_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, const double* xv, double* yv, int nvec,
+                     long long xs, long long ys, int precision);
+
+void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec, long long xs, long long ys,
+                      int precision) {
+  if (tl.groups.empty()) return;
+  DevList tmp;
+  DevList* d;
+  if (tl.persistent) {
+    d = &dev(tl);
+  } else {
+    upload_list(tl, tmp);
+    d = &tmp;
+  }
+  if (!d->tiles) return;
+  if (precision != 0) {
+    launch_tasks_tc(*this, tl, *d, xv, yv, nvec, xs, ys, precision);
+  } else {
+    int t0 = 0;
+    for (int c = 0; c < 3; ++c) {
+      int n = d->ncls[c];
+      if (n == 0) continue;
+      dim3 grid(n, nvec);
+      if (c == 0)
+        k_tasks_fp64<C0_NT, C0_ACC><<<grid, C0_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
+      else if (c == 1)
+        k_tasks_fp64<C1_NT, C1_ACC><<<grid, C1_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
+      else
+        k_tasks_fp64<C2_NT, C2_ACC><<<grid, C2_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
+      launches++;
+      note(cudaGetLastError(), "k_tasks_fp64");
+      t0 += n;
+    }
+  }
+  if (!tl.persistent) free_list(tmp);
+}
+
+void CudaBackend::lincomb(const LCList& l) {
+  if (l.blocks.empty()) return;
+  LCBlock* b = dev_copy(l.blocks, *this);
+  LCTerm* t = dev_copy(l.terms, *this);
+  if (!b) return;
+  int nb = (int)l.blocks.size();
+  k_lincomb<<<std::min(nb, 65535), 128, 0, stream_>>>(b, nb, t);
+  launches++;
+  note(cudaGetLastError(), "k_lincomb");
+  cudaStreamSynchronize(stream_);
+  cudaFree(b);
+  if (t) cudaFree(t);
+}
+
+}  // namespace tns

@@ -79,6 +79,11 @@ static int backend_davidson(tns::Engine&, double*, double, int, int, double*, in
   err = "not available in the host-logic check library";
   return -2;
 }
+static int backend_step(tns::Engine&, int, bool, const tns_sweep_opts*, const double*, double*, tns_step_stats*,
+                        std::string& err) {
+  err = "not available in the host-logic check library";
+  return -2;
+}
 static int backend_sweep(tns::Engine&, const tns_sweep_opts*, double*, tns_sweep_stats*, std::string& err) {
   err = "not available in the host-logic check library";
   return -2;
