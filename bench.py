@@ -1,0 +1,355 @@
+"""Benchmark: two-site DMRG steps of the H_eff*psi hot path on GB300.
+
+A step is one two-site DMRG step (one "iteration cycle" of a sweep) at the
+middle of the chain: partial sums and work lists, device Davidson with the
+H_eff*psi grouped products, SVD truncation to D and renormalisation.
+Workload: 24 orbitals, 24 electrons, S_z = 0, random integrals with decay
+length 5 (seed 1), D = 512, FP64 -- synthetic stand-ins for the paper's
+molecular integrals.  Untimed set-up runs the sweep from the first site up to
+the warm-up steps; W warm-up steps and K timed steps follow the sweep order.
+
+Output: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(oracle/dmrg.py) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H_eff*psi useful TFLOP/s per two-site step (FP64, 24 orbitals, D=512)"
+UNIT = "TFLOP/s"
+
+# DRAM traffic of one k_tasks_fp64 launch set per H_eff*psi at this workload,
+# from the ncu capture summarised in profiles/k_tasks_fp64_n24.md (None until
+# captured for the current kernel).
+TRAFFIC_BYTES_PER_HEFF = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="n24")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16x3"])
+    p.add_argument("--tol", type=float, default=1e-8)
+    p.add_argument("--case", default="step", choices=["step", "heff"],
+                   help="step: two-site DMRG steps (the benchmark); heff: H_eff*psi alone at the middle bond "
+                        "of a random MPS of the workload (kernel micro-benchmark, used for ncu captures)")
+    p.add_argument("--nvec", type=int, default=1)
+    return p.parse_args()
+
+
+def run_heff_case(args):
+    """H_eff*psi alone: K timed applications after W warm-up ones."""
+    import torch
+    import synth
+    from paper_2305_05581_gb300 import Context, TNS_FP64, TNS_TF32, TNS_BF16X3
+    prec = {"fp64": TNS_FP64, "tf32": TNS_TF32, "bf16x3": TNS_BF16X3}[args.precision]
+    c = synth.WORKLOADS[args.workload]
+    N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
+    k = N // 2 - 1
+    h, v = synth.integrals(N, c["lam"], c["seed"])
+    bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=c["seed"])
+    stream = torch.cuda.current_stream()
+    ctx = Context(device=0, stream=stream.cuda_stream)
+    ctx.load_integrals(h, v)
+    ctx.mps_import(N, n, s2, D, bonds, sites)
+    ctx.build_env(k)
+    desc, length = ctx.psi_layout(k)
+    flops, nprod = ctx.heff_flops(k)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(length * args.nvec, device="cuda", dtype=torch.float64, generator=g)
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        ctx.heff_apply_ptr(k, x.data_ptr(), y.data_ptr(), args.nvec, prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.heff_apply_ptr(k, x.data_ptr(), y.data_ptr(), args.nvec, prec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) * 1e-3 / args.steps
+    dims = [d for _, d in bonds[k]]
+    print(json.dumps({"case": "heff", "workload": args.workload, "precision": args.precision, "nvec": args.nvec,
+                      "psi_blocks": int(len(desc)), "psi_length": int(length), "products": int(nprod),
+                      "useful_flops": flops * args.nvec, "ms": dt * 1e3,
+                      "tflops": flops * args.nvec / dt / 1e12, "max_sector_dim": max(dims),
+                      "bond_dim": sum(dims)}), flush=True)
+    ctx.close()
+    return 0
+
+
+def sweep_plan(N):
+    plan = [(k, True) for k in range(0, N - 2)] + [(N - 2, False)] + [(k, False) for k in range(N - 3, 0, -1)]
+    return plan
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def fp64_gemm_peak(torch):
+    """cuBLAS DGEMM rate (TFLOP/s), the measured FP64 denominator."""
+    n = 4096
+    a = torch.randn(n, n, device="cuda", dtype=torch.float64)
+    b = torch.randn_like(a)
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 1e30
+    for _ in range(3):
+        e0.record()
+        a @ b
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference_full(args, rank, world)
+
+    import numpy as np
+    import torch
+    import synth
+    from paper_2305_05581_gb300 import Context, TNS_FP64, TNS_TF32, TNS_BF16X3
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the product path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    if args.case == "heff":
+        return run_heff_case(args)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = {"fp64": TNS_FP64, "tf32": TNS_TF32, "bf16x3": TNS_BF16X3}[args.precision]
+    c = synth.WORKLOADS[args.workload]
+    N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
+    peak = fp64_gemm_peak(torch)
+    h, v = synth.integrals(N, c["lam"], c["seed"])
+    stream = torch.cuda.current_stream()
+    ctx = Context(device=local, stream=stream.cuda_stream)
+    ctx.load_integrals(h, v)
+    ctx.mps_init(N, n, s2, D, seed=c["seed"])
+    plan = sweep_plan(N)
+    mid = N // 2 - 1
+    start = max(0, mid - args.warmup)
+    i = 0
+    # untimed set-up: sweep from the first site to the warm-up steps
+    for k, ltr in plan[:start]:
+        ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec)
+        i += 1
+    for _ in range(args.warmup):
+        k, ltr = plan[i % len(plan)]
+        ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec)
+        i += 1
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    flops = heff_s = 0.0
+    iters = 0
+    launches = 0
+    stats = []
+    for _ in range(args.steps):
+        k, ltr = plan[i % len(plan)]
+        st = ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec)
+        flops += st.heff_flops
+        heff_s += st.heff_seconds
+        iters += st.iters
+        launches += st.kernel_launches
+        stats.append((k, st.energy, st.iters, st.bond_dim, st.seconds, st.length))
+        i += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) * 1e-3
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t)
+        f = torch.tensor([flops], device="cuda", dtype=torch.float64)
+        dist.all_reduce(f)
+        flops_all = float(f)
+    else:
+        flops_all = flops
+    value = flops_all / elapsed / 1e12
+
+    # end to end through the public API with host buffers: each step uploads
+    # its start vector from pinned host memory and reads the converged psi back
+    e2e_steps = max(1, min(args.steps, 3))
+    lens = []
+    for _ in range(e2e_steps):
+        k, ltr = plan[i % len(plan)]
+        L = ctx.psi_guess(k)
+        xh = torch.empty(L, dtype=torch.float64, pin_memory=True)
+        ph = torch.empty(L, dtype=torch.float64, pin_memory=True)
+        ctx.psi_guess(k, xh.data_ptr())
+        t1 = time.perf_counter()
+        st = ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec, x0_host_ptr=xh.data_ptr(),
+                      psi_host_ptr=ph.data_ptr())
+        lens.append((time.perf_counter() - t1, st.heff_flops, L))
+        i += 1
+    e2e_time = sum(x[0] for x in lens)
+    e2e_flops = sum(x[1] for x in lens)
+    h2d = int(sum(x[2] for x in lens) * 8 / e2e_steps)
+    d2h = h2d
+    e2e = {"value": e2e_flops / e2e_time / 1e12 * (world if dist else 1), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+
+    achieved = flops / heff_s / 1e12 if heff_s > 0 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": TRAFFIC_BYTES_PER_HEFF,
+                "kernel": "k_tasks_fp64 (grouped triple product, FP64 DFMA)",
+                "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (FP64 has no entry in MEASURED_PEAKS.json)"}
+    if rank == 0:
+        cpu = None
+        try:
+            cpu = cpu_baseline(args)
+        except Exception as ex:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {ex}"}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == TNS_FP64 else args.precision,
+                "data": "synthetic",
+                "config": {"workload": f"{args.workload}: N={N} n_elec={n} 2Sz={s2} D={D} lambda={c['lam']} "
+                                       f"seed={c['seed']}, two-site steps around the middle bond",
+                           "precision": args.precision, "davidson_tol": args.tol,
+                           "l2": "inputs larger than L2 (operator arenas are GBs)",
+                           "steps_detail": [{"site": s[0], "energy": s[1], "matvecs": s[2], "bond": s[3],
+                                             "seconds": s[4], "psi_length": s[5]} for s in stats]},
+                "s_per_step": elapsed / args.steps,
+                "heff_matvecs_per_step": iters / args.steps,
+                "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def cpu_baseline(args):
+    """The oracle timed on this host's cores on a bounded sample (not the target)."""
+    import synth
+    from oracle import dmrg as O3
+    c = synth.WORKLOADS[args.workload]
+    N, n, s2 = c["N"], c["n_elec"], c["two_sz"]
+    Ds, k = 48, N // 2 - 1
+    h, v = synth.integrals(N, c["lam"], c["seed"])
+    bonds, sites = synth.random_mps(N, n, s2, Ds, center=k, seed=c["seed"])
+    keys = synth.psi_keys(bonds, N, n, s2, k)
+    X = synth.random_psi(keys, seed=7)[0]
+    heff = O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2)
+    flops = O3.useful_flops(heff)
+    heff.apply(X)
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < 10.0 and reps < 20:
+        heff.apply(X)
+        reps += 1
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": flops / dt / 1e12, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle dense-operator H_eff*psi, middle bond of the {N}-orbital workload at D={Ds} "
+                      f"(not {c['D']}), {reps} products of {flops:.3e} useful flops, env build excluded"}
+
+
+def run_reference_full(args, rank, world):
+    """--impl reference: the oracle as it stands on the host cores (rank 0 only)."""
+    if rank != 0:
+        return 0
+    import numpy as np
+    import synth
+    from oracle import dmrg as O3
+    c = synth.WORKLOADS[args.workload]
+    N, n, s2 = c["N"], c["n_elec"], c["two_sz"]
+    Ds, k = 48, N // 2 - 1
+    h, v = synth.integrals(N, c["lam"], c["seed"])
+    bonds, sites = synth.random_mps(N, n, s2, Ds, center=k, seed=c["seed"])
+    keys = synth.psi_keys(bonds, N, n, s2, k)
+    X = synth.random_psi(keys, seed=7)[0]
+    heff = O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2)
+    flops = O3.useful_flops(heff)
+    for _ in range(args.warmup):
+        heff.apply(X)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        heff.apply(X)
+    dt = time.perf_counter() - t0
+    val = flops * args.steps / dt / 1e12
+    sample = (f"oracle dense-operator H_eff*psi at the middle bond of the {N}-orbital workload with D={Ds} "
+              f"(not {c['D']}); env build excluded; useful flops {flops:.3e} per product")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload} sample: N={N} n_elec={n} 2Sz={s2} D={Ds}, middle bond"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -178,6 +178,7 @@ typedef struct tns_step_stats {
   double seconds;           /* wall time of the call */
   long long length;         /* two-site wavefunction length */
   int bond_dim;             /* new dimension of bond site+1 */
+  long long kernel_launches; /* launches of the engine's own CUDA kernels in the call */
 } tns_step_stats;
 
 /* One two-site step of a sweep at (site, site+1) (one "DMRG iteration cycle",
@@ -191,6 +192,12 @@ typedef struct tns_step_stats {
  * Returns TNS_OK also when Davidson stops at max_iter (stats->converged = 0). */
 int tns_step(tns_ctx* ctx, int site, int left_to_right, const tns_sweep_opts* opts, const double* x0_host,
              double* psi_host, tns_step_stats* stats);
+
+/* Two-site product of the current site tensors at (site, site+1) in the layout
+ * of tns_psi_layout(site) (the default Davidson start of tns_step), copied to
+ * the HOST array x_host; *length receives its length (x_host NULL: length
+ * only).  Works without tns_build_env. */
+int tns_psi_guess(tns_ctx* ctx, int site, double* x_host, long long* length);
 
 /* Useful FP64-equivalent flop count of one tns_heff_apply(site) for nvec = 1:
  * sum over products of p * min(2mr(n+q), 2qn(m+r)) (best chain order, the

@@ -546,3 +546,84 @@ def dmrg(h, v, n_elec, two_sz, D, nsweeps, seed=0, tol=1e-12, verbose=False):
                 if verbose:
                     print(sweep, direction, k, E, disc)
     return E, hist
+
+
+def useful_flops(heff: "DenseHeff") -> float:
+    """Useful flop count of one H_eff*psi in the block-sparse form: over every
+    term of formula (*), every dot block (s' <- s) of its left and right
+    enlarged operators and every symmetry block of psi, the cheaper chain of
+    the product L_blk X_blk R_blk^T: min(2mr(n+q), 2qn(m+r)).  Identity
+    factors cost one product.  Pure counting over the nonzero blocks of the
+    oracle's own dense operators (no arithmetic of the method)."""
+    LL, RR = heff.LL, heff.RR
+    DL, DR = heff.DL, heff.DR
+
+    def sectors(n, sz):
+        lab = list(zip(n.tolist(), sz.tolist()))
+        out = {}
+        for i, q in enumerate(lab):
+            out.setdefault(q, []).append(i)
+        return out
+
+    # D-basis sector index sets of the two blocks
+    secL = sectors(heff.L.n, heff.L.sz)
+    secR = sectors(heff.R.n, heff.R.sz)
+
+    def blocks(E, dim, left, sec):
+        """{(s', s): [(q_out, q_in, is_identity)]} of the nonzero D-basis blocks."""
+        out = {}
+        for so in range(4):
+            for si in range(4):
+                if left:
+                    M = E[so::4, si::4]
+                else:
+                    M = E[so * dim:(so + 1) * dim, si * dim:(si + 1) * dim]
+                if not M.any():
+                    continue
+                lst = []
+                ident = np.allclose(M, M[0, 0] * np.eye(dim)) if M[0, 0] != 0 else False
+                for qo, io in sec.items():
+                    for qi, ii in sec.items():
+                        if M[np.ix_(io, ii)].any():
+                            lst.append((qo, qi, ident and qo == qi))
+                out[(so, si)] = lst
+        return out
+
+    terms = [(LL.ops["H"], None), (None, RR.ops["H"])]
+    for k in _keys(LL, "c"):
+        terms += [(LL.ops[k], RR.ops[("S", k[1])]), (LL.ops[k].T, RR.ops[("S", k[1])].T)]
+    for k in _keys(RR, "c"):
+        terms += [(LL.ops[("T", k[1])], RR.ops[k].T), (LL.ops[("T", k[1])].T, RR.ops[k])]
+    for k in _keys(LL, "A"):
+        P = RR.ops[("P", k[1], k[2])]
+        terms += [(LL.ops[k], P), (LL.ops[k].T, P.T)]
+    for k in _keys(LL, "B"):
+        terms += [(LL.ops[k], RR.ops[("Q", k[1], k[2])])]
+    eyeL = np.eye(4 * DL)
+    eyeR = np.eye(4 * DR)
+    dimL = {q: len(i) for q, i in secL.items()}
+    dimR = {q: len(i) for q, i in secR.items()}
+    tot = 0.0
+    for El, Er in terms:
+        bl = blocks(eyeL if El is None else El, DL, True, secL)
+        br = blocks(eyeR if Er is None else Er, DR, False, secR)
+        for (s1o, s1i), lb in bl.items():
+            for (s2o, s2i), rb in br.items():
+                for (qlo, qli, li) in lb:
+                    for (qro, qri, ri) in rb:
+                        # psi block (qli, s1i, s2i, qri) must be in the target sector
+                        q, m = dimL[qlo], dimL[qli]
+                        n, r = dimR[qri], dimR[qro]
+                        nl = qli[0] + int(N_SITE[s1i]) + int(N_SITE[s2i]) + qri[0]
+                        sl = qli[1] + int(SZ2_SITE[s1i]) + int(SZ2_SITE[s2i]) + qri[1]
+                        if (nl, sl) != heff.target:
+                            continue
+                        if li and ri:
+                            tot += 2.0 * m * n
+                        elif li:
+                            tot += 2.0 * m * n * r
+                        elif ri:
+                            tot += 2.0 * q * m * n
+                        else:
+                            tot += min(2.0 * m * r * (n + q), 2.0 * q * n * (m + r))
+    return tot

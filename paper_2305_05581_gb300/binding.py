@@ -21,7 +21,7 @@ DEFAULT_LIB = os.path.join(HERE, "libtns.so")
 # every entry point of include/tns.h
 SYMBOLS = ["create", "destroy", "last_error", "load_integrals", "mps_init", "mps_define",
            "mps_set_bond", "mps_set_site", "mps_get_bond", "mps_get_site", "build_env",
-           "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops", "step"]
+           "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops", "step", "psi_guess"]
 
 
 class TnsError(RuntimeError):
@@ -46,7 +46,7 @@ class StepStats(C.Structure):
     _fields_ = [("energy", C.c_double), ("discarded", C.c_double), ("iters", C.c_int), ("converged", C.c_int),
                 ("heff_flops", C.c_double), ("heff_seconds", C.c_double), ("env_seconds", C.c_double),
                 ("svd_seconds", C.c_double), ("seconds", C.c_double), ("length", C.c_longlong),
-                ("bond_dim", C.c_int)]
+                ("bond_dim", C.c_int), ("kernel_launches", C.c_longlong)]
 
 
 _LIBS = {}
@@ -81,6 +81,7 @@ def load_library(path: str = DEFAULT_LIB, prefix: str = "tns_"):
         "sweep": (C.c_int, [vp, C.POINTER(SweepOpts), dp, C.POINTER(SweepStats)]),
         "heff_flops": (C.c_int, [vp, C.c_int, dp, llp]),
         "step": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(SweepOpts), vp, vp, C.POINTER(StepStats)]),
+        "psi_guess": (C.c_int, [vp, C.c_int, vp, llp]),
     }
     for name, (res, args) in sig.items():
         fn = f(name)
@@ -220,6 +221,14 @@ class Context:
                                      C.c_void_p(x0_host_ptr) if x0_host_ptr else None,
                                      C.c_void_p(psi_host_ptr) if psi_host_ptr else None, C.byref(st)))
         return st
+
+
+    def psi_guess(self, site, x_host_ptr: int = 0) -> int:
+        """Copy the two-site start vector to host memory at x_host_ptr (0: length only)."""
+        n = C.c_longlong()
+        self._check(self._fn("psi_guess")(self._h, site, C.c_void_p(x_host_ptr) if x_host_ptr else None,
+                                          C.byref(n)))
+        return n.value
 
 
 def blocks_to_vector(desc, length, blocks: dict) -> np.ndarray:

@@ -67,6 +67,11 @@ class CudaBackend : public Backend {
   void free_list(DevList& d);
 };
 
+// tensor-core form (tc.cu)
+void launch_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, const double* xv, double* yv, int nvec,
+                     long long xs, long long ys, int precision);
+void release_tc_plan(void* plan);
+
 // kernels used by the solver (defined in kernels.cu)
 void launch_heff_diag(CudaBackend& be, const Task* d_tasks, const int* d_idx, const int* d_rng, int ngroups,
                       const Group* d_groups, double* diag);

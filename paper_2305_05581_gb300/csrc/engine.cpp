@@ -1206,20 +1206,18 @@ int Engine::ensure_right(int k, std::string& err) {
   return 0;
 }
 
-void Engine::build_psi(int k) {
-  Step& st = step_;
-  st.psi.clear();
-  st.desc.clear();
-  const Basis& L = bonds_[k];
-  const Catalogue& R = Rcat_[k + 2];
-  int nqr = R.basis.size();
-  st.psi_index.assign((size_t)L.size() * 16 * nqr, -1);
+void psi_layout_of(const Basis& L, const Basis& R, QN target, std::vector<PsiBlock>& psi, std::vector<int>& index,
+                   std::vector<long long>& desc, long long& length) {
+  psi.clear();
+  desc.clear();
+  int nqr = R.size();
+  index.assign((size_t)L.size() * 16 * nqr, -1);
   long long off = 0;
   for (int ql = 0; ql < L.size(); ++ql)
     for (int s1 = 0; s1 < 4; ++s1)
       for (int s2 = 0; s2 < 4; ++s2) {
-        QN need = target_ - L.q[ql] - kSiteQN[s1] - kSiteQN[s2];
-        int qr = R.basis.find(need);
+        QN need = target - L.q[ql] - kSiteQN[s1] - kSiteQN[s2];
+        int qr = R.find(need);
         if (qr < 0) continue;
         PsiBlock pb;
         pb.ql = ql;
@@ -1227,15 +1225,26 @@ void Engine::build_psi(int k) {
         pb.s2 = s2;
         pb.qr = qr;
         pb.m = L.dim[ql];
-        pb.n = R.basis.dim[qr];
+        pb.n = R.dim[qr];
         pb.off = off;
         off += (long long)pb.m * pb.n;
-        st.psi_index[((size_t)(ql * 4 + s1) * 4 + s2) * nqr + qr] = (int)st.psi.size();
-        st.psi.push_back(pb);
-        long long d9[9] = {L.q[ql].n, L.q[ql].s, s1, s2, R.basis.q[qr].n, R.basis.q[qr].s, pb.m, pb.n, pb.off};
-        st.desc.insert(st.desc.end(), d9, d9 + 9);
+        index[((size_t)(ql * 4 + s1) * 4 + s2) * nqr + qr] = (int)psi.size();
+        psi.push_back(pb);
+        long long d9[9] = {L.q[ql].n, L.q[ql].s, s1, s2, R.q[qr].n, R.q[qr].s, pb.m, pb.n, pb.off};
+        desc.insert(desc.end(), d9, d9 + 9);
       }
-  st.length = off;
+  length = off;
+}
+
+Basis Engine::right_basis_of_bond(int b) const {
+  Basis R;
+  const Basis& bb = bonds_[b];
+  for (int i = 0; i < bb.size(); ++i) R.add(target_ - bb.q[i], bb.dim[i]);
+  return R;
+}
+
+void Engine::build_psi(int k) {
+  psi_layout_of(bonds_[k], Rcat_[k + 2].basis, target_, step_.psi, step_.psi_index, step_.desc, step_.length);
 }
 
 // operator-table x task-table: every pair of the LL|RR split, every dot

@@ -314,6 +314,10 @@ struct Step {
   bool valid = false;
 };
 
+// two-site wavefunction layout: blocks (ql, s1, s2, qr) ordered by (ql, s1, s2, qr)
+void psi_layout_of(const Basis& L, const Basis& R, QN target, std::vector<PsiBlock>& psi, std::vector<int>& index,
+                   std::vector<long long>& desc, long long& length);
+
 class Engine {
  public:
   explicit Engine(Backend* be) : be_(be) {}
@@ -352,6 +356,7 @@ class Engine {
   int site_from_host(int b, const std::vector<SiteBlock>& blocks, const std::vector<double>& data,
                      std::string& err);
   int alloc_site(int b, std::string& err);  // layout from bonds b, b+1; zeroed device storage
+  Basis right_basis_of_bond(int b) const;    // right-counted basis of bond b (bond order)
   void set_bond_basis(int b, const Basis& basis);
 
   // integrals

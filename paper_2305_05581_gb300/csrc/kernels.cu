@@ -38,15 +38,21 @@ __device__ __forceinline__ double opR(const Task& t, int j, int k) {
   return (t.flags & TF_RT) ? __ldg(t.R + (long long)k * t.r + j) : __ldg(t.R + (long long)j * t.n + k);
 }
 
-constexpr int CH = 32;          // chunk of the contracted middle dimension
-constexpr int SPITCH = 65;      // shared-memory pitch of the intermediate (64 cols + 1)
-constexpr int SMEM_D = 64 * SPITCH;
+constexpr int CH = 32;  // chunk of the contracted middle dimension
 
-template <int NT, int ACC>
+// tile classes: (threads, outputs per thread, max tile rows, max tile cols);
+// shared memory is sized per class so that small tiles keep many CTAs per SM
+constexpr int C0_NT = 32, C0_ACC = 8, C0_TR = 16, C0_TC = 16;
+constexpr int C1_NT = 128, C1_ACC = 8, C1_TR = 32, C1_TC = 32;
+constexpr int C2_NT = 256, C2_ACC = 16, C2_TR = 64, C2_TC = 64;
+
+template <int NT, int ACC, int TR, int TC>
 __global__ void __launch_bounds__(NT) k_tasks_fp64(const Task* __restrict__ tasks, const Group* __restrict__ groups,
                                                    const Tile* __restrict__ tiles, int tile0, const double* xv,
                                                    double* yv, long long xs, long long ys) {
-  __shared__ double S[SMEM_D];
+  constexpr int SA = CH * (TC + 1);  // L (X R^T): CH rows of X R^T, TC columns
+  constexpr int SB = TR * (CH + 1);  // (L X) R^T: TR rows of L X, CH columns
+  __shared__ double S[SA > SB ? SA : SB];
   const Tile T = tiles[tile0 + blockIdx.x];
   const Group G = groups[T.g];
   const int vec = blockIdx.y;
@@ -54,56 +60,86 @@ __global__ void __launch_bounds__(NT) k_tasks_fp64(const Task* __restrict__ task
   double* Y = yv + (long long)vec * ys + G.yoff;
   const int nc = T.ncols, nr = T.nrows;
   const int nout = nr * nc;
+  const int tid = threadIdx.x;
+  int ri[ACC], cj[ACC];
   double acc[ACC];
 #pragma unroll
-  for (int u = 0; u < ACC; ++u) acc[u] = 0.0;
+  for (int u = 0; u < ACC; ++u) {
+    const int e = tid + u * NT;
+    ri[u] = e < nout ? e / nc : -1;
+    cj[u] = e < nout ? e % nc : 0;
+    acc[u] = 0.0;
+  }
+  // phase-1 thread maps (no division inside the task loop)
+  const int a_j = tid % nc, a_i0 = tid / nc, a_st = NT / nc;
+  const bool a_ok = tid < a_st * nc;
+  const int b_j = tid % CH, b_i0 = tid / CH, b_st = NT / CH;
 
   for (int ti = G.t0; ti < G.t1; ++ti) {
     const Task tk = tasks[ti];
-    const double* Xp = (tk.flags & TF_XV) ? X0 + (long long)(size_t)tk.X : tk.X;
-    const double a = tk.alpha;
     const int f = tk.flags;
+    const double a = tk.alpha;
+    // element (i,k) of op(L) = pL[i*sLi + k*sLk]; op(X)(i,k) = pX[i*sXi + k*sXk]; op(R)(j,k) = pR[j*sRj + k*sRk]
+    const double* pL = tk.L;
+    const long long sLi = (f & TF_LT) ? 1 : tk.m, sLk = (f & TF_LT) ? tk.q : 1;
+    const double* pX = (f & TF_XV) ? X0 + (long long)(size_t)tk.X : tk.X;
+    const long long sXi = (f & TF_XT) ? 1 : tk.n, sXk = (f & TF_XT) ? tk.m : 1;
+    const double* pR = tk.R;
+    const long long sRj = (f & TF_RT) ? 1 : tk.n, sRk = (f & TF_RT) ? tk.r : 1;
     if ((f & TF_LI) && (f & TF_RI)) {
 #pragma unroll
-      for (int u = 0; u < ACC; ++u) {
-        int e = threadIdx.x + u * NT;
-        if (e < nout) acc[u] += a * opX(tk, Xp, T.row0 + e / nc, T.col0 + e % nc);
-      }
-    } else if (f & (TF_LI | TF_RI | TF_XI)) {
-      // two-factor products: contract directly
+      for (int u = 0; u < ACC; ++u)
+        if (ri[u] >= 0) acc[u] = fma(a, __ldg(pX + (T.row0 + ri[u]) * sXi + (T.col0 + cj[u]) * sXk), acc[u]);
+    } else if (f & TF_LI) {  // Y += X R^T
 #pragma unroll
       for (int u = 0; u < ACC; ++u) {
-        int e = threadIdx.x + u * NT;
-        if (e >= nout) continue;
-        int i = T.row0 + e / nc, j = T.col0 + e % nc;
+        if (ri[u] < 0) continue;
+        const double* xr = pX + (T.row0 + ri[u]) * sXi;
+        const double* rr = pR + (T.col0 + cj[u]) * sRj;
         double s = 0.0;
-        if (f & TF_LI) {
-          for (int k = 0; k < tk.n; ++k) s = fma(opX(tk, Xp, i, k), opR(tk, j, k), s);
-        } else if (f & TF_RI) {
-          for (int k = 0; k < tk.m; ++k) s = fma(opL(tk, i, k), opX(tk, Xp, k, j), s);
-        } else {
-          for (int k = 0; k < tk.m; ++k) s = fma(opL(tk, i, k), opR(tk, j, k), s);
-        }
+        for (int k = 0; k < tk.n; ++k) s = fma(__ldg(xr + k * sXk), __ldg(rr + k * sRk), s);
+        acc[u] = fma(a, s, acc[u]);
+      }
+    } else if (f & TF_RI) {  // Y += L X
+#pragma unroll
+      for (int u = 0; u < ACC; ++u) {
+        if (ri[u] < 0) continue;
+        const double* lr = pL + (T.row0 + ri[u]) * sLi;
+        const double* xc = pX + (T.col0 + cj[u]) * sXk;
+        double s = 0.0;
+        for (int k = 0; k < tk.m; ++k) s = fma(__ldg(lr + k * sLk), __ldg(xc + k * sXi), s);
+        acc[u] = fma(a, s, acc[u]);
+      }
+    } else if (f & TF_XI) {  // Y += L R^T
+#pragma unroll
+      for (int u = 0; u < ACC; ++u) {
+        if (ri[u] < 0) continue;
+        const double* lr = pL + (T.row0 + ri[u]) * sLi;
+        const double* rr = pR + (T.col0 + cj[u]) * sRj;
+        double s = 0.0;
+        for (int k = 0; k < tk.m; ++k) s = fma(__ldg(lr + k * sLk), __ldg(rr + k * sRk), s);
         acc[u] = fma(a, s, acc[u]);
       }
     } else if (!(f & TF_ORDB)) {
       // L (X R^T): chunks of CH rows of X
       for (int m0 = 0; m0 < tk.m; m0 += CH) {
         const int mc = min(CH, tk.m - m0);
-        for (int e = threadIdx.x; e < mc * nc; e += NT) {
-          int i = e / nc, j = e % nc;
-          double s = 0.0;
-          for (int k = 0; k < tk.n; ++k) s = fma(opX(tk, Xp, m0 + i, k), opR(tk, T.col0 + j, k), s);
-          S[i * SPITCH + j] = s;
+        if (a_ok) {
+          const double* rr = pR + (T.col0 + a_j) * sRj;
+          for (int i = a_i0; i < mc; i += a_st) {
+            const double* xr = pX + (m0 + i) * sXi;
+            double s = 0.0;
+            for (int k = 0; k < tk.n; ++k) s = fma(__ldg(xr + k * sXk), __ldg(rr + k * sRk), s);
+            S[i * (TC + 1) + a_j] = s;
+          }
         }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < ACC; ++u) {
-          int e = threadIdx.x + u * NT;
-          if (e >= nout) continue;
-          int i = e / nc, j = e % nc;
+          if (ri[u] < 0) continue;
+          const double* lr = pL + (T.row0 + ri[u]) * sLi + m0 * sLk;
           double s = 0.0;
-          for (int k = 0; k < mc; ++k) s = fma(opL(tk, T.row0 + i, m0 + k), S[k * SPITCH + j], s);
+          for (int k = 0; k < mc; ++k) s = fma(__ldg(lr + k * sLk), S[k * (TC + 1) + cj[u]], s);
           acc[u] = fma(a, s, acc[u]);
         }
         __syncthreads();
@@ -112,20 +148,22 @@ __global__ void __launch_bounds__(NT) k_tasks_fp64(const Task* __restrict__ task
       // (L X) R^T: chunks of CH columns of X
       for (int n0 = 0; n0 < tk.n; n0 += CH) {
         const int ncc = min(CH, tk.n - n0);
-        for (int e = threadIdx.x; e < nr * ncc; e += NT) {
-          int i = e / ncc, j = e % ncc;
-          double s = 0.0;
-          for (int k = 0; k < tk.m; ++k) s = fma(opL(tk, T.row0 + i, k), opX(tk, Xp, k, n0 + j), s);
-          S[i * (CH + 1) + j] = s;
+        if (b_j < ncc) {
+          const double* xc = pX + (n0 + b_j) * sXk;
+          for (int i = b_i0; i < nr; i += b_st) {
+            const double* lr = pL + (T.row0 + i) * sLi;
+            double s = 0.0;
+            for (int k = 0; k < tk.m; ++k) s = fma(__ldg(lr + k * sLk), __ldg(xc + k * sXi), s);
+            S[i * (CH + 1) + b_j] = s;
+          }
         }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < ACC; ++u) {
-          int e = threadIdx.x + u * NT;
-          if (e >= nout) continue;
-          int i = e / nc, j = e % nc;
+          if (ri[u] < 0) continue;
+          const double* rr = pR + (T.col0 + cj[u]) * sRj + n0 * sRk;
           double s = 0.0;
-          for (int k = 0; k < ncc; ++k) s = fma(S[i * (CH + 1) + k], opR(tk, T.col0 + j, n0 + k), s);
+          for (int k = 0; k < ncc; ++k) s = fma(S[ri[u] * (CH + 1) + k], __ldg(rr + k * sRk), s);
           acc[u] = fma(a, s, acc[u]);
         }
         __syncthreads();
@@ -133,16 +171,9 @@ __global__ void __launch_bounds__(NT) k_tasks_fp64(const Task* __restrict__ task
     }
   }
 #pragma unroll
-  for (int u = 0; u < ACC; ++u) {
-    int e = threadIdx.x + u * NT;
-    if (e < nout) Y[(long long)(T.row0 + e / nc) * G.r + T.col0 + e % nc] = acc[u];
-  }
+  for (int u = 0; u < ACC; ++u)
+    if (ri[u] >= 0) Y[(long long)(T.row0 + ri[u]) * G.r + T.col0 + cj[u]] = acc[u];
 }
-
-// size classes: (threads, outputs per thread)
-constexpr int C0_NT = 32, C0_ACC = 4;    // <= 128 outputs
-constexpr int C1_NT = 128, C1_ACC = 8;   // <= 1024 outputs
-constexpr int C2_NT = 256, C2_ACC = 16;  // <= 4096 outputs (64 x 64)
 
 // ---------------------------------------------------------------------------
 // partial sums (materialised linear combinations of operator blocks)
@@ -681,7 +712,7 @@ void CudaBackend::free_list(DevList& d) {
   if (d.tasks) cudaFree(d.tasks);
   if (d.groups) cudaFree(d.groups);
   if (d.tiles) cudaFree(d.tiles);
-  if (d.tc) cudaFree(d.tc);
+  if (d.tc) release_tc_plan(d.tc);
   d = DevList();
 }
 
@@ -699,8 +730,7 @@ void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
         t.col0 = c0;
         t.nrows = std::min(64, G.q - r0);
         t.ncols = std::min(64, G.r - c0);
-        int nout = t.nrows * t.ncols;
-        int c = nout <= C0_NT * C0_ACC ? 0 : nout <= C1_NT * C1_ACC ? 1 : 2;
+        int c = (t.nrows <= C0_TR && t.ncols <= C0_TC) ? 0 : (t.nrows <= C1_TR && t.ncols <= C1_TC) ? 1 : 2;
         cls[c].push_back(t);
       }
   }
@@ -755,11 +785,11 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
       if (n == 0) continue;
       dim3 grid(n, nvec);
       if (c == 0)
-        k_tasks_fp64<C0_NT, C0_ACC><<<grid, C0_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
+        k_tasks_fp64<C0_NT, C0_ACC, C0_TR, C0_TC><<<grid, C0_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
       else if (c == 1)
-        k_tasks_fp64<C1_NT, C1_ACC><<<grid, C1_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
+        k_tasks_fp64<C1_NT, C1_ACC, C1_TR, C1_TC><<<grid, C1_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
       else
-        k_tasks_fp64<C2_NT, C2_ACC><<<grid, C2_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
+        k_tasks_fp64<C2_NT, C2_ACC, C2_TR, C2_TC><<<grid, C2_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
       launches++;
       note(cudaGetLastError(), "k_tasks_fp64");
       t0 += n;

@@ -186,7 +186,7 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
   bool have_fp64 = false;
   while (true) {
     // expand
-    matvec(V.d() + (long long)k * n, AV.d() + (long long)k * n, (lowp && have_fp64 && k > 0) ? precision : 0);
+    matvec(V.d() + (long long)k * n, AV.d() + (long long)k * n, (lowp && k > 0) ? precision : 0);
     ++it;
     launch_multidot(be, V.d(), n, k + 1, AV.d() + (long long)k * n, n, dcoef);
     std::vector<double> hc;
@@ -223,10 +223,20 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
     rn = std::sqrt(std::max(0.0, dot1(r.d(), r.d())));
     if (check(be, err)) return -6;
     if (lowp) {
-      // the subspace products are reduced precision after the first; the
-      // residual of the Ritz vector is recomputed in FP64 before accepting
-      bool stalled = rn < std::max(tol, 1e-3 * fp64_res) || k == kmax || it >= max_iter;
-      if (stalled || !have_fp64) {
+      // FP64 residual correction: V_0 always carries an exact FP64 product,
+      // the other basis vectors reduced-precision ones; the Ritz pair is
+      // accepted only on an FP64 residual, and every refresh restarts the
+      // subspace from the exact pair (x, H x)
+      if (k == 1) {
+        fp64_res = rn;  // x = V_0 and A V_0 is exact
+        have_fp64 = true;
+        if (rn < tol || it >= max_iter) {
+          conv = rn < tol;
+          break;
+        }
+      }
+      bool stalled = k > 1 && (rn < std::max(0.5 * tol, 1e-3 * fp64_res) || k == kmax || it >= max_iter);
+      if (stalled) {
         matvec(x.d(), avs.d(), 0);
         ++it;
         double xx = dot1(x.d(), x.d());
@@ -312,15 +322,13 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
 // ---------------------------------------------------------------------------
 // two-site guess: psi(ql,s1,s2,qr) = site_k(ql,s1) * site_{k+1}(qm,s2)
 // ---------------------------------------------------------------------------
-void two_site_guess(Engine& E, CudaBackend& be, double* X) {
-  Step& st = E.step();
-  const int k = st.k;
+void two_site_guess(Engine& E, CudaBackend& be, double* X, int k, const std::vector<PsiBlock>& psi) {
   const Site& a = E.sites()[k];
   const Site& b = E.sites()[k + 1];
   const Basis& bm = E.bonds()[k + 1];
   const Basis& bl = E.bonds()[k];
   TaskList tl;
-  for (const PsiBlock& p : st.psi) {
+  for (const PsiBlock& p : psi) {
     Group g;
     g.yoff = p.off;
     g.q = p.m;
@@ -796,7 +804,7 @@ int one_step(Engine& E, CudaBackend& be, int k, bool ltr, const tns_sweep_opts* 
   if (x0_host) {
     be.note(cudaMemcpyAsync(X.d(), x0_host, sizeof(double) * st.length, cudaMemcpyHostToDevice, be.stream()), "x0");
   } else {
-    two_site_guess(E, be, X.d());
+    two_site_guess(E, be, X.d(), k, st.psi);
   }
   int rc = davidson(E, be, X.d(), o->tol, o->max_iter, o->precision, e, its, &acc, err);
   *conv = rc == 0;
@@ -825,6 +833,29 @@ int one_step(Engine& E, CudaBackend& be, int k, bool ltr, const tns_sweep_opts* 
 }  // namespace
 }  // namespace tns
 
+static int backend_psi_guess(tns::Engine& E, int k, double* xh, long long* len, std::string& err) {
+  using namespace tns;
+  CudaBackend& be = *static_cast<CudaBackend*>(E.be());
+  cudaSetDevice(be.device());
+  std::vector<PsiBlock> psi;
+  std::vector<int> index;
+  std::vector<long long> desc;
+  long long length = 0;
+  psi_layout_of(E.bonds()[k], E.right_basis_of_bond(k + 2), E.target(), psi, index, desc, length);
+  if (len) *len = length;
+  if (!xh) return 0;
+  for (int b : {k, k + 1})
+    if (!E.sites()[b].d) {
+      err = "psi_guess: site tensor not set";
+      return -2;
+    }
+  DBuf X(be, 8 * std::max(length, 1LL));
+  two_site_guess(E, be, X.d(), k, psi);
+  be.note(cudaMemcpyAsync(xh, X.d(), 8 * length, cudaMemcpyDeviceToHost, be.stream()), "psi_guess");
+  be.sync();
+  return check(be, err);
+}
+
 static int backend_step(tns::Engine& E, int k, bool ltr, const tns_sweep_opts* o, const double* x0, double* psi,
                         tns_step_stats* stats, std::string& err) {
   using namespace tns;
@@ -837,6 +868,7 @@ static int backend_step(tns::Engine& E, int k, bool ltr, const tns_sweep_opts* o
   int its = 0;
   bool conv = false;
   long long length = 0;
+  const long long launches0 = be.launches;
   if (E.step().valid && E.step().k == k) length = E.step().length;
   int rc = one_step(E, be, k, ltr, o, x0, psi, X, acc, &e, &its, &disc, &conv, err);
   if (rc) return rc;
@@ -852,6 +884,7 @@ static int backend_step(tns::Engine& E, int k, bool ltr, const tns_sweep_opts* o
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     stats->length = length ? length : (long long)(X.bytes / 8);
     stats->bond_dim = (int)E.bonds()[k + 1].total;
+    stats->kernel_launches = be.launches - launches0;
   }
   return 0;
 }

@@ -84,6 +84,10 @@ static int backend_step(tns::Engine&, int, bool, const tns_sweep_opts*, const do
   err = "not available in the host-logic check library";
   return -2;
 }
+static int backend_psi_guess(tns::Engine&, int, double*, long long*, std::string& err) {
+  err = "not available in the host-logic check library";
+  return -2;
+}
 static int backend_sweep(tns::Engine&, const tns_sweep_opts*, double*, tns_sweep_stats*, std::string& err) {
   err = "not available in the host-logic check library";
   return -2;

@@ -1,0 +1,114 @@
+"""Reduced-precision form (tcgen05 TF32 and split-BF16) against the FP64 path
+and the oracle: H_eff*psi error bounds, and FP64-corrected Davidson energies
+within 1e-8 Ha of the FP64 results."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dmrg as O3
+from oracle.fci import fci_energy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2305_05581_gb300 import (Context, TNS_FP64, TNS_TF32, TNS_BF16X3,  # noqa: E402
+                                    blocks_to_vector, vector_to_blocks, DEFAULT_LIB)
+
+# error bounds of one H_eff*psi relative to its 2-norm: split-BF16 keeps ~16
+# significant bits per operand (hi + lo), TF32 11; both accumulate in FP32
+TOL = {TNS_BF16X3: 2e-4, TNS_TF32: 1e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(DEFAULT_LIB):
+        from paper_2305_05581_gb300 import build as b
+        b.build()
+
+
+def _ctx():
+    return Context(device=0, stream=torch.cuda.current_stream().cuda_stream)
+
+
+def _setup(N, n, s2, D, k, seed):
+    h, v = synth.integrals(N, 3.0, seed)
+    bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=seed + 1)
+    ctx = _ctx()
+    ctx.load_integrals(h, v)
+    ctx.mps_import(N, n, s2, D, bonds, sites)
+    ctx.build_env(k)
+    return ctx, h, v, bonds, sites
+
+
+@pytest.mark.parametrize("prec", [TNS_BF16X3, TNS_TF32])
+@pytest.mark.parametrize("N,n,s2,D,k", [(6, 6, 0, 12, 2), (8, 8, 0, 60, 3), (8, 7, 1, 256, 2), (10, 10, 0, 140, 4)])
+def test_heff_reduced_precision_vs_oracle(prec, N, n, s2, D, k):
+    ctx, h, v, bonds, sites = _setup(N, n, s2, D, k, 300 + N + k)
+    keys = synth.psi_keys(bonds, N, n, s2, k)
+    X = synth.random_psi(keys, seed=5)[0]
+    ref = O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2).apply(X)
+    desc, length = ctx.psi_layout(k)
+    x = torch.tensor(blocks_to_vector(desc, length, X), device="cuda", dtype=torch.float64)
+    y = torch.empty_like(x)
+    ctx.heff_apply_ptr(k, x.data_ptr(), y.data_ptr(), 1, prec)
+    torch.cuda.synchronize()
+    r = blocks_to_vector(desc, length, ref)
+    err = float(np.linalg.norm(y.cpu().numpy() - r) / np.linalg.norm(r))
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [TNS_BF16X3, TNS_TF32])
+def test_heff_reduced_precision_full_size(prec):
+    """24 orbitals, D=512, middle bond: error against the FP64 GPU path."""
+    c = synth.WORKLOADS["n24"]
+    N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
+    k = N // 2 - 1
+    h, v = synth.integrals(N, c["lam"], c["seed"])
+    bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=c["seed"])
+    ctx = _ctx()
+    ctx.load_integrals(h, v)
+    ctx.mps_import(N, n, s2, D, bonds, sites)
+    ctx.build_env(k)
+    desc, length = ctx.psi_layout(k)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn(length, device="cuda", dtype=torch.float64, generator=g)
+    y64 = torch.empty_like(x)
+    ylo = torch.empty_like(x)
+    ctx.heff_apply_ptr(k, x.data_ptr(), y64.data_ptr(), 1, TNS_FP64)
+    ctx.heff_apply_ptr(k, x.data_ptr(), ylo.data_ptr(), 1, prec)
+    torch.cuda.synchronize()
+    err = float(torch.linalg.norm(ylo - y64) / torch.linalg.norm(y64))
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [TNS_BF16X3, TNS_TF32])
+def test_davidson_fp64_corrected_energy(prec):
+    """Reduced-precision products with FP64 residual correction reach the FP64
+    eigenvalue within 1e-8 Ha (exact middle-bond space: = FCI)."""
+    N, n, s2 = 8, 8, 0
+    h, v = synth.integrals(N, 3.0, 0)
+    k = 3
+    bonds, sites = synth.random_mps(N, n, s2, 10 ** 6, center=k, seed=1)
+    ctx = _ctx()
+    ctx.load_integrals(h, v)
+    ctx.mps_import(N, n, s2, 10 ** 6, bonds, sites)
+    ctx.build_env(k)
+    desc, length = ctx.psi_layout(k)
+    x = torch.zeros(length, device="cuda", dtype=torch.float64)
+    e, its, ok = ctx.davidson_ptr(k, x.data_ptr(), tol=1e-7, max_iter=600, precision=prec)
+    assert ok
+    assert abs(e - fci_energy(h, v, n, s2)) < 1e-8
+
+
+def test_sweep_bf16x3_reaches_fci_n8():
+    c = synth.WORKLOADS["n8"]
+    h, v = synth.integrals(c["N"], c["lam"], c["seed"])
+    ctx = _ctx()
+    ctx.load_integrals(h, v)
+    ctx.mps_init(c["N"], c["n_elec"], c["two_sz"], c["D"], seed=1)
+    e, st = ctx.sweep(4, c["D"], tol=1e-7, max_iter=300, precision=TNS_BF16X3)
+    assert abs(e - fci_energy(h, v, c["n_elec"], c["two_sz"])) < 1e-8
