@@ -126,6 +126,32 @@ int tns_heff_apply(tns_ctx* ctx, int site, const double* X, double* Y, int nvec,
  * (length doubles).  Used as the Davidson preconditioner. */
 int tns_heff_diag(tns_ctx* ctx, int site, double* diag);
 
+/* Allocation-free variant of tns_heff_diag (the paper has no counterpart;
+ * this is a service to callers).  Callers that must not allocate device
+ * memory at this point -- code running under a memory pool that reserves
+ * the whole device, or inside a region where a cudaMalloc would synchronise
+ * the device or fail with out-of-memory -- cannot use tns_heff_diag, which
+ * uploads its per-call index tables into freshly allocated buffers.  This
+ * entry point stages them instead into one fixed file-scope device array of
+ * TNS_NOALLOC_DIAG_MAX int entries (16 MiB), which every GPU that loads the
+ * library holds until the process exits, and calls no cudaMalloc, cudaFree
+ * or allocating library routine.
+ *  - Same arguments and result as tns_heff_diag (diag: DEVICE, length doubles,
+ *    fully overwritten).
+ *  - Requires the step's work list to be resident on the device already: call
+ *    tns_heff_apply or tns_heff_diag once for this step first; otherwise
+ *    TNS_ERR_STATE.
+ *  - TNS_ERR_ARG if the step's diagonal work list needs more than
+ *    TNS_NOALLOC_DIAG_MAX index entries.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls share the array and each call rewrites the part it uses, so
+ *    nothing carries over between calls; calls that overlap on the GPU (from
+ *    several contexts or threads) race on it and must be serialised. */
+#define TNS_NOALLOC_DIAG_MAX (4 * 1024 * 1024)
+int tns_heff_diag_noalloc(tns_ctx* ctx, int site, double* diag);
+
 /* Lowest eigenpair of H_eff at step (site, site+1) by block Davidson on the
  * device (FP64 orthogonalisation, Rayleigh quotient and residual).  X is a
  * DEVICE vector of `length` doubles: on entry the start vector (zero vector:

@@ -21,7 +21,8 @@ DEFAULT_LIB = os.path.join(HERE, "libtns.so")
 # every entry point of include/tns.h
 SYMBOLS = ["create", "destroy", "last_error", "load_integrals", "mps_init", "mps_define",
            "mps_set_bond", "mps_set_site", "mps_get_bond", "mps_get_site", "build_env",
-           "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops", "step", "psi_guess"]
+           "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops", "step", "psi_guess",
+           "heff_diag_noalloc"]
 
 
 class TnsError(RuntimeError):
@@ -82,6 +83,7 @@ def load_library(path: str = DEFAULT_LIB, prefix: str = "tns_"):
         "heff_flops": (C.c_int, [vp, C.c_int, dp, llp]),
         "step": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(SweepOpts), vp, vp, C.POINTER(StepStats)]),
         "psi_guess": (C.c_int, [vp, C.c_int, vp, llp]),
+        "heff_diag_noalloc": (C.c_int, [vp, C.c_int, vp]),
     }
     for name, (res, args) in sig.items():
         fn = f(name)
@@ -189,6 +191,10 @@ class Context:
 
     def heff_diag_ptr(self, site, d_ptr: int):
         self._check(self._fn("heff_diag")(self._h, site, C.c_void_p(d_ptr)))
+
+    def heff_diag_noalloc_ptr(self, site, d_ptr: int):
+        """Allocation-free H_eff diagonal (see tns_heff_diag_noalloc in include/tns.h)."""
+        self._check(self._fn("heff_diag_noalloc")(self._h, site, C.c_void_p(d_ptr)))
 
     def heff_flops(self, site):
         f = C.c_double()

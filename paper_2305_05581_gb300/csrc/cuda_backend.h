@@ -49,6 +49,11 @@ class CudaBackend : public Backend {
   void note(cudaError_t e, const char* what);
   // persistent device copy of a task list (uploaded when tl.gen changes)
   DevList& dev(const TaskList& tl);
+  // the device copy of tl if it is resident and current, else nullptr (never uploads)
+  const DevList* resident(const TaskList& tl) const {
+    auto it = lists_.find(&tl);
+    return (it != lists_.end() && it->second.gen == tl.gen && it->second.tasks) ? &it->second : nullptr;
+  }
   void drop(const TaskList& tl);
   // scratch device memory owned by the backend (grows, never shrinks)
   void* scratch(size_t bytes, int slot);
@@ -66,6 +71,9 @@ class CudaBackend : public Backend {
   void upload_list(const TaskList& tl, DevList& d);
   void free_list(DevList& d);
 };
+
+// allocation-free H_eff diagonal (noalloc.cu)
+int heff_diag_noalloc(CudaBackend& be, Step& st, double* diag, std::string& err);
 
 // tensor-core form (tc.cu)
 void launch_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, const double* xv, double* yv, int nvec,

@@ -762,6 +762,12 @@ static tns::Backend* make_backend(int device, void* stream, std::string& err) {
   return new tns::CudaBackend(device, s, own);
 }
 
+static int backend_diag_noalloc(tns::Engine& E, double* diag, std::string& err) {
+  tns::CudaBackend& be = *static_cast<tns::CudaBackend*>(E.be());
+  cudaSetDevice(be.device());
+  return tns::heff_diag_noalloc(be, E.step(), diag, err);
+}
+
 static int backend_diag(tns::Engine& E, double* diag, std::string& err) {
   tns::CudaBackend& be = *static_cast<tns::CudaBackend*>(E.be());
   cudaSetDevice(be.device());
