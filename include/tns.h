@@ -126,6 +126,27 @@ int tns_heff_apply(tns_ctx* ctx, int site, const double* X, double* Y, int nvec,
  * (length doubles).  Used as the Davidson preconditioner. */
 int tns_heff_diag(tns_ctx* ctx, int site, double* diag);
 
+/* Differentiation form (not in the paper; adjoint of Eq. 2).  The operator
+ * catalogues of the left block (orbitals 0..site-1, side 0) and of the right
+ * block (orbitals site+2..N-1, side 1) used by step (site, site+1) live in one
+ * DEVICE arena each; tns_env_arena returns its pointer and length (doubles).
+ * The arena may be modified by the caller (e.g. to perturb an operator); call
+ * tns_build_env(site) afterwards so the partial sums are recomputed.
+ * Layout: operators in catalogue order, each operator its symmetry blocks
+ * (out <- in) row-major. */
+int tns_env_arena(tns_ctx* ctx, int site, int side, double** data, long long* size);
+
+/* Adjoint of Y = H_eff X at step (site, site+1) for the cotangent Ybar:
+ * Xbar = H_eff^T Ybar (= H_eff Ybar, H_eff being symmetric), and the gradients
+ * of <Ybar, H_eff X> with respect to every element of the left and right
+ * arenas of tns_env_arena: per product alpha L X R^T the contributions
+ * alpha Ybar R X^T (to L) and alpha Ybar^T L X (to R), carried through the
+ * partial sums to the catalogue operators.  All pointers are DEVICE; X, Ybar,
+ * Xbar have the layout of tns_psi_layout, Lbar/Rbar the arena lengths; any of
+ * Xbar, Lbar, Rbar may be NULL.  Outputs are overwritten.  FP64. */
+int tns_heff_adjoint(tns_ctx* ctx, int site, const double* X, const double* Ybar, double* Xbar, double* Lbar,
+                     double* Rbar);
+
 /* Allocation-free variant of tns_heff_diag (the paper has no counterpart;
  * this is a service to callers).  Callers that must not allocate device
  * memory at this point -- code running under a memory pool that reserves

@@ -22,7 +22,7 @@ DEFAULT_LIB = os.path.join(HERE, "libtns.so")
 SYMBOLS = ["create", "destroy", "last_error", "load_integrals", "mps_init", "mps_define",
            "mps_set_bond", "mps_set_site", "mps_get_bond", "mps_get_site", "build_env",
            "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops", "step", "psi_guess",
-           "heff_diag_noalloc"]
+           "heff_diag_noalloc", "env_arena", "heff_adjoint"]
 
 
 class TnsError(RuntimeError):
@@ -84,6 +84,8 @@ def load_library(path: str = DEFAULT_LIB, prefix: str = "tns_"):
         "step": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(SweepOpts), vp, vp, C.POINTER(StepStats)]),
         "psi_guess": (C.c_int, [vp, C.c_int, vp, llp]),
         "heff_diag_noalloc": (C.c_int, [vp, C.c_int, vp]),
+        "env_arena": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(vp), llp]),
+        "heff_adjoint": (C.c_int, [vp, C.c_int, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = f(name)
@@ -195,6 +197,17 @@ class Context:
     def heff_diag_noalloc_ptr(self, site, d_ptr: int):
         """Allocation-free H_eff diagonal (see tns_heff_diag_noalloc in include/tns.h)."""
         self._check(self._fn("heff_diag_noalloc")(self._h, site, C.c_void_p(d_ptr)))
+
+    def env_arena(self, site, side):
+        """(pointer, length) of the left (side 0) or right (side 1) operator arena."""
+        p = C.c_void_p()
+        n = C.c_longlong()
+        self._check(self._fn("env_arena")(self._h, site, side, C.byref(p), C.byref(n)))
+        return p.value or 0, n.value
+
+    def heff_adjoint_ptr(self, site, x_ptr, yb_ptr, xb_ptr=0, lb_ptr=0, rb_ptr=0):
+        v = lambda p: C.c_void_p(p) if p else None
+        self._check(self._fn("heff_adjoint")(self._h, site, v(x_ptr), v(yb_ptr), v(xb_ptr), v(lb_ptr), v(rb_ptr)))
 
     def heff_flops(self, site):
         f = C.c_double()

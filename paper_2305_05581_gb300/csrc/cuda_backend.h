@@ -14,6 +14,15 @@ namespace tns {
 struct Tile {  // an output tile of a group: rows [row0, row0+nrows), cols [col0, col0+ncols)
   int g;
   int row0, col0, nrows, ncols;
+  int t0, t1;      // task range of this piece (a split tile has several pieces)
+  long long poff;  // -1: write the output block; else element offset of this piece's partial tile
+};
+
+struct SplitRed {  // a split tile: sum of nsplit partial tiles (fixed order) -> output
+  int g;
+  int row0, col0, nrows, ncols;
+  int nsplit;
+  long long poff;
 };
 
 // device copy of a work list; tiles split into size classes
@@ -24,6 +33,13 @@ struct DevList {
   Tile* tiles = nullptr;
   int ncls[3] = {0, 0, 0};   // tiles per size class (contiguous, class 0 first)
   int ntiles = 0;
+  Tile* wtiles = nullptr;    // 32 x 16 warp tiles of the FP64 tensor (DMMA) kernel
+  int nwtiles = 0;
+  SplitRed* reds = nullptr;  // split tiles to reduce after the product kernels
+  int nreds = 0;
+  long long psize = 0;       // partial-tile elements per vector
+  double* part = nullptr;    // partial tiles (psize * part_nvec)
+  int part_nvec = 0;
   // tensor-core form (precision != FP64)
   void* tc = nullptr;
   long long tc_gen = -1;
@@ -31,7 +47,11 @@ struct DevList {
 
 class CudaBackend : public Backend {
  public:
-  CudaBackend(int device, cudaStream_t s, bool own) : device_(device), stream_(s), own_(own) {}
+  CudaBackend(int device, cudaStream_t s, bool own);
+  // FP64 product kernel: 0 DFMA tile classes (default: on GB300 DFMA and DMMA
+  // peak at ~1.0 TFLOP/s alike and the DFMA kernel measured faster), 1 DMMA
+  // (mma.sync m8n8k4 f64); environment TNS_FP64_KERNEL=dfma|dmma
+  int fp64_kernel = 0;
   ~CudaBackend() override;
   double* alloc(long long n) override;
   void release(double* p) override;

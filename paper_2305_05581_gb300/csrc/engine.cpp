@@ -1470,4 +1470,201 @@ int Engine::heff(const double* X, double* Y, int nvec, int precision, std::strin
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// adjoint of the grouped triple product
+//
+// E = <Yb, Y>, Y_blk = sum alpha op(L) op(X) op(R)^T.  For one product
+//   Xb_blk        += alpha op(L)^T Yb op(R)
+//   d/d op(L)      = alpha Yb op(R) op(X)^T       d/d op(R) = alpha Yb^T op(L) op(X)
+// and the gradient of a stored block is the (transposed) gradient of its
+// op().  Each is again a triple product, grouped by its target block, so the
+// same kernels run it.  Gradients reaching a materialised partial sum flow on
+// to the catalogue operators of its terms (adjoint of the linear combination).
+// ---------------------------------------------------------------------------
+namespace {
+struct AdjTarget {
+  std::vector<Task> tasks;
+};
+Task adj_task(double a, const double* P, int pf, const double* M, int mf, const double* S, int sf, int q, int m, int n,
+              int r) {
+  Task t;
+  t.alpha = a;
+  t.L = P;
+  t.X = M;
+  t.R = S;
+  t.q = q;
+  t.m = m;
+  t.n = n;
+  t.r = r;
+  t.flags = pf | mf | sf;
+  t.pad = 0;
+  return t;
+}
+// flags of a stored operand used as op(.)^T given its flags as op(.)
+int lflags_T(int f) { return (f & TF_LI) ? TF_LI : ((f & TF_LT) ? 0 : TF_LT); }
+int rflags_T(int f) { return (f & TF_RI) ? TF_RI : ((f & TF_RT) ? 0 : TF_RT); }
+}  // namespace
+
+int Engine::heff_adjoint(const double* X, const double* Yb, double* Xb, double* Lb, double* Rb, std::string& err) {
+  if (!step_.valid) {
+    err = "heff_adjoint: call build_env first";
+    return -2;
+  }
+  Step& st = step_;
+  const int k = st.k;
+  Catalogue& Lc = Lcat_[k];
+  Catalogue& Rc = Rcat_[k + 2];
+  const TaskList& fw = st.heff;
+  const long long nL = Lc.size, nR = Rc.size, nML = st.L.size, nMR = st.R.size;
+  // temporaries: direct gradients of catalogue blocks and of materialised blocks
+  double* GL = Lb ? be_->alloc(std::max(nL, 1LL)) : nullptr;
+  double* GR = Rb ? be_->alloc(std::max(nR, 1LL)) : nullptr;
+  double* ML = (Lb && nML) ? be_->alloc(nML) : nullptr;
+  double* MR = (Rb && nMR) ? be_->alloc(nMR) : nullptr;
+  if ((Lb && !GL) || (Rb && !GR) || (Lb && nML && !ML) || (Rb && nMR && !MR)) {
+    err = "heff_adjoint: device allocation failed";
+    for (double* p : {GL, GR, ML, MR})
+      if (p) be_->release(p);
+    return -3;
+  }
+  // target maps: block pointer -> list of tasks
+  std::map<const double*, std::vector<Task>> tx, tl_, tr_;
+  for (size_t g = 0; g < fw.groups.size(); ++g) {
+    const Group& G = fw.groups[g];
+    const double* yb = Yb + G.yoff;
+    for (int i = G.t0; i < G.t1; ++i) {
+      const Task& t = fw.tasks[i];
+      const PsiBlock& xbk = st.psi[t.pad];
+      const double* xblk = X + xbk.off;
+      const int lf = t.flags & (TF_LI | TF_LT), rf = t.flags & (TF_RI | TF_RT);
+      const int q = t.q, m = t.m, n = t.n, r = t.r;
+      if (Xb) {  // Xb (m x n) += a op(L)^T Yb op(R)
+        tx[Xb + xbk.off].push_back(adj_task(t.alpha, t.L, lflags_T(lf), yb, 0, t.R, rflags_T(rf), m, q, r, n));
+      }
+      if (Lb && !(t.flags & TF_LI)) {
+        const int mfR = (t.flags & TF_RI) ? TF_XI : ((t.flags & TF_RT) ? TF_XT : 0);
+        if (!(t.flags & TF_LT))  // L (q x m) += a Yb op(R) op(X)^T
+          tl_[t.L].push_back(adj_task(t.alpha, yb, 0, t.R, mfR, xblk, 0, q, r, n, m));
+        else  // L stored (m x q) += a op(X) op(R)^T Yb^T
+          tl_[t.L].push_back(adj_task(t.alpha, xblk, 0, t.R, (t.flags & TF_RI) ? TF_XI : ((t.flags & TF_RT) ? 0 : TF_XT),
+                                      yb, 0, m, n, r, q));
+      }
+      if (Rb && !(t.flags & TF_RI)) {
+        if (!(t.flags & TF_RT))  // R (r x n) += a Yb^T op(L) op(X)
+          tr_[t.R].push_back(adj_task(t.alpha, yb, TF_LT, t.L,
+                                      (t.flags & TF_LI) ? TF_XI : ((t.flags & TF_LT) ? TF_XT : 0), xblk, TF_RT, r, q,
+                                      m, n));
+        else  // R stored (n x r) += a op(X)^T op(L)^T Yb
+          tr_[t.R].push_back(adj_task(t.alpha, xblk, TF_LT, t.L,
+                                      (t.flags & TF_LI) ? TF_XI : ((t.flags & TF_LT) ? 0 : TF_XT), yb, TF_RT, n, m, q,
+                                      r));
+      }
+    }
+  }
+  auto run_map = [&](std::map<const double*, std::vector<Task>>& mp, double* outbase, const double* srcbase,
+                     long long srcsize, const std::vector<std::pair<long long, std::pair<int, int>>>& blocks) {
+    // groups: every block of [srcbase, srcbase+srcsize) listed in `blocks` (offset, (rows, cols))
+    TaskList tl;
+    for (auto& b : blocks) {
+      Group g;
+      g.yoff = b.first;
+      g.q = b.second.first;
+      g.r = b.second.second;
+      g.row0 = g.col0 = 0;
+      g.nrows = g.q;
+      g.ncols = g.r;
+      g.t0 = (int)tl.tasks.size();
+      auto it = mp.find(srcbase + b.first);
+      if (it != mp.end())
+        for (auto& t : it->second) tl.tasks.push_back(t);
+      g.t1 = (int)tl.tasks.size();
+      tl.groups.push_back(g);
+    }
+    (void)srcsize;
+    be_->run(tl, nullptr, outbase, 1, 0, 0, 0);
+  };
+  auto cat_blocks = [&](const Catalogue& c) {
+    std::vector<std::pair<long long, std::pair<int, int>>> v;
+    for (auto& o : c.ops) {
+      const Layout& L = c.layouts[o.layout];
+      for (size_t b = 0; b < L.in.size(); ++b)
+        v.push_back({o.off + L.off[b], {c.basis.dim[L.out[b]], c.basis.dim[L.in[b]]}});
+    }
+    return v;
+  };
+  auto mat_blocks = [&](const Side& s, const Catalogue& c) {
+    std::vector<std::pair<long long, std::pair<int, int>>> v;
+    for (auto& mt : s.mats) {
+      const Layout& L = c.layouts[mt.layout];
+      for (size_t b = 0; b < L.in.size(); ++b)
+        v.push_back({mt.off + L.off[b], {c.basis.dim[L.out[b]], c.basis.dim[L.in[b]]}});
+    }
+    return v;
+  };
+  if (Xb) {
+    std::vector<std::pair<long long, std::pair<int, int>>> v;
+    for (auto& p : st.psi) v.push_back({p.off, {p.m, p.n}});
+    run_map(tx, Xb, Xb, st.length, v);
+  }
+  // second phase: catalogue gradient = direct part + adjoint of the partial sums
+  auto finish = [&](Side& S, Catalogue& C, double* G, double* M, double* out, std::map<const double*, std::vector<Task>>& mp) {
+    const auto cb = cat_blocks(C);
+    run_map(mp, G, C.d, C.size, cb);
+    if (M) run_map(mp, M, S.d, S.size, mat_blocks(S, C));
+    be_->sync();
+    std::map<long long, std::vector<Task>> add;  // target offset -> tasks
+    for (auto& b : cb)
+      add[b.first].push_back(adj_task(1.0, nullptr, TF_LI, G + b.first, 0, nullptr, TF_RI, b.second.first,
+                                      b.second.first, b.second.second, b.second.second));
+    const Basis& bs = C.basis;
+    for (auto& mt : S.mats) {
+      const Expr& x = S.exprs[mt.expr];
+      const Layout& L = C.layouts[mt.layout];
+      for (size_t b = 0; b < L.in.size(); ++b) {
+        const int in = L.in[b], out = L.out[b];
+        const double* mb = M + mt.off + L.off[b];
+        for (auto& tm : x.t) {
+          if (tm.op < 0) continue;
+          const double sign = tm.par == 1 ? sgn_n(bs.q[in].n) : tm.par == 2 ? sgn_n(bs.q[out].n) : 1.0;
+          const CatOp& o = C.ops[tm.op];
+          const Layout& OL = C.layouts[o.layout];
+          int ob = tm.tr ? OL.blk_of_in[out] : OL.blk_of_in[in];
+          if (ob < 0) continue;
+          if (tm.tr && OL.out[ob] != in) continue;
+          if (!tm.tr && OL.out[ob] != out) continue;
+          const long long toff = o.off + OL.off[ob];
+          const int tr = bs.dim[OL.out[ob]], tc = bs.dim[OL.in[ob]];
+          add[toff].push_back(adj_task(tm.c * sign, nullptr, TF_LI, mb, tm.tr ? TF_XT : 0, nullptr, TF_RI, tr, tr, tc, tc));
+        }
+      }
+    }
+    TaskList tl;
+    for (auto& b : cb) {
+      Group g;
+      g.yoff = b.first;
+      g.q = b.second.first;
+      g.r = b.second.second;
+      g.row0 = g.col0 = 0;
+      g.nrows = g.q;
+      g.ncols = g.r;
+      g.t0 = (int)tl.tasks.size();
+      for (auto& t : add[b.first]) tl.tasks.push_back(t);
+      g.t1 = (int)tl.tasks.size();
+      tl.groups.push_back(g);
+    }
+    be_->run(tl, nullptr, out, 1, 0, 0, 0);
+  };
+  if (Lb) finish(st.L, Lc, GL, ML, Lb, tl_);
+  if (Rb) finish(st.R, Rc, GR, MR, Rb, tr_);
+  be_->sync();
+  for (double* p : {GL, GR, ML, MR})
+    if (p) be_->release(p);
+  std::string e = be_->error();
+  if (!e.empty()) {
+    err = e;
+    return -6;
+  }
+  return 0;
+}
+
 }  // namespace tns

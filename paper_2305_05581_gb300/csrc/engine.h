@@ -332,6 +332,12 @@ class Engine {
 
   int build_env(int k, std::string& err);        // L_k, R_{k+2}, step k tables
   int heff(const double* X, double* Y, int nvec, int precision, std::string& err);
+  // adjoint of Y = H_eff X for the cotangent Yb: Xb = H_eff^T Yb and the
+  // gradients of <Yb, H_eff X> w.r.t. the arenas of L_k (Lb) and R_{k+2} (Rb);
+  // any output may be null.  All pointers in the backend's memory space.
+  int heff_adjoint(const double* X, const double* Yb, double* Xb, double* Lb, double* Rb, std::string& err);
+  // refresh the step's partial sums after the catalogue arenas were changed
+  int refresh_step(std::string& err) { return step_.valid ? prepare_step(step_.k, err) : -2; }
   double e_core() const { return e_core_; }
 
   // accessors for the API layer

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 
 #include "cuda_backend.h"
 
@@ -49,7 +50,8 @@ constexpr int C2_NT = 256, C2_ACC = 16, C2_TR = 64, C2_TC = 64;
 template <int NT, int ACC, int TR, int TC>
 __global__ void __launch_bounds__(NT) k_tasks_fp64(const Task* __restrict__ tasks, const Group* __restrict__ groups,
                                                    const Tile* __restrict__ tiles, int tile0, const double* xv,
-                                                   double* yv, long long xs, long long ys) {
+                                                   double* yv, long long xs, long long ys, double* part,
+                                                   long long psize) {
   constexpr int SA = CH * (TC + 1);  // L (X R^T): CH rows of X R^T, TC columns
   constexpr int SB = TR * (CH + 1);  // (L X) R^T: TR rows of L X, CH columns
   __shared__ double S[SA > SB ? SA : SB];
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(NT) k_tasks_fp64(const Task* __restrict__ task
   const int nc = T.ncols, nr = T.nrows;
   const int nout = nr * nc;
   const int tid = threadIdx.x;
+  double* P = T.poff >= 0 ? part + (long long)vec * psize + T.poff : nullptr;  // split piece
   int ri[ACC], cj[ACC];
   double acc[ACC];
 #pragma unroll
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(NT) k_tasks_fp64(const Task* __restrict__ task
   const bool a_ok = tid < a_st * nc;
   const int b_j = tid % CH, b_i0 = tid / CH, b_st = NT / CH;
 
-  for (int ti = G.t0; ti < G.t1; ++ti) {
+  for (int ti = T.t0; ti < T.t1; ++ti) {
     const Task tk = tasks[ti];
     const int f = tk.flags;
     const double a = tk.alpha;
@@ -172,7 +175,211 @@ __global__ void __launch_bounds__(NT) k_tasks_fp64(const Task* __restrict__ task
   }
 #pragma unroll
   for (int u = 0; u < ACC; ++u)
-    if (ri[u] >= 0) Y[(long long)(T.row0 + ri[u]) * G.r + T.col0 + cj[u]] = acc[u];
+    if (ri[u] >= 0) {
+      if (P) P[ri[u] * nc + cj[u]] = acc[u];
+      else Y[(long long)(T.row0 + ri[u]) * G.r + T.col0 + cj[u]] = acc[u];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 tensor path: the same grouped triple product on DMMA
+// (mma.sync m8n8k4 f64).  One warp owns a 32 x 16 output tile; per product it
+// streams the contracted dimension in chunks of 8 through a warp-private
+// shared-memory slab: L (X R^T) (T chunk 8 x 16) or (L X) R^T (U chunk
+// 32 x 8), whichever is cheaper for the tile.  Ragged edges are predicated
+// loads returning zero.  Fragment layout of m8n8k4 f64 (g = lane/4,
+// t = lane%4): A(g, t), B(t, g), C(g, 2t), C(g, 2t+1).
+// ---------------------------------------------------------------------------
+constexpr int DM_WR = 32, DM_WC = 16, DM_WARPS = 4;
+constexpr int DM_SLAB = 32 * 9;  // max(8 x 17, 32 x 9)
+
+__device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+               : "+d"(c[0]), "+d"(c[1])
+               : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(32 * DM_WARPS) k_tasks_dmma(const Task* __restrict__ tasks,
+                                                              const Group* __restrict__ groups,
+                                                              const Tile* __restrict__ tiles, int ntiles,
+                                                              const double* xv, double* yv, long long xs,
+                                                              long long ys) {
+  __shared__ double slab[DM_WARPS][DM_SLAB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ti_ = blockIdx.x * DM_WARPS + warp;
+  if (ti_ >= ntiles) return;  // whole warp
+  double* S = slab[warp];
+  const int g = lane >> 2, t = lane & 3;
+  const Tile T = tiles[ti_];
+  const Group G = groups[T.g];
+  const int vec = blockIdx.y;
+  const double* X0 = xv ? xv + (long long)vec * xs : nullptr;
+  double* Y = yv + (long long)vec * ys + G.yoff;
+  const int nr = T.nrows, nc = T.ncols;
+  const int nrt = (nr + 7) >> 3, nct = (nc + 7) >> 3;  // used 8x8 tiles
+  double acc[4][2][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+
+  for (int k = T.t0; k < T.t1; ++k) {
+    const Task tk = tasks[k];
+    const int f = tk.flags;
+    const double al = tk.alpha;
+    const int m = tk.m, n = tk.n;
+    const double* pL = tk.L;
+    const long long sLi = (f & TF_LT) ? 1 : m, sLk = (f & TF_LT) ? tk.q : 1;
+    const double* pX = (f & TF_XV) ? X0 + (long long)(size_t)tk.X : tk.X;
+    const long long sXi = (f & TF_XT) ? 1 : n, sXk = (f & TF_XT) ? m : 1;
+    const double* pR = tk.R;
+    const long long sRj = (f & TF_RT) ? 1 : n, sRk = (f & TF_RT) ? tk.r : 1;
+    // predicated operand loads (tile-local row/col)
+    auto Lv = [&](int i, int kk) -> double {
+      if (i >= nr || kk >= m) return 0.0;
+      if (f & TF_LI) return (T.row0 + i == kk) ? 1.0 : 0.0;
+      return __ldg(pL + (T.row0 + i) * sLi + kk * sLk);
+    };
+    auto Rv = [&](int j, int kk) -> double {  // op(R)(col, kk)
+      if (j >= nc || kk >= n) return 0.0;
+      if (f & TF_RI) return (T.col0 + j == kk) ? 1.0 : 0.0;
+      return __ldg(pR + (T.col0 + j) * sRj + kk * sRk);
+    };
+    auto Xv = [&](int i, int kk) -> double {  // op(X)(i, kk), absolute indices
+      if (i >= m || kk >= n) return 0.0;
+      if (f & TF_XI) return (i == kk) ? 1.0 : 0.0;
+      return __ldg(pX + i * sXi + kk * sXk);
+    };
+    if ((f & TF_LI) && (f & TF_RI)) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int i = 8 * a + g, j = 8 * b + 2 * t + e;
+            if (i < nr && j < nc) acc[a][b][e] = fma(al, Xv(T.row0 + i, T.col0 + j), acc[a][b][e]);
+          }
+      continue;
+    }
+    if (f & (TF_LI | TF_RI | TF_XI)) {
+      // two-factor product P Q^T with P rows = tile rows, Q rows = tile cols
+      const int K = (f & TF_LI) ? n : m;
+      for (int k0 = 0; k0 < K; k0 += 4) {
+        double bq[2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const int j = 8 * b + g, kk = k0 + t;
+          bq[b] = (f & TF_RI) ? Xv(kk, (j < nc) ? T.col0 + j : n) : Rv(j, kk);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (a >= nrt) break;
+          const int i = 8 * a + g, kk = k0 + t;
+          const double av = al * ((f & TF_LI) ? ((i < nr) ? Xv(T.row0 + i, kk) : 0.0) : Lv(i, kk));
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+            if (b < nct) dmma(acc[a][b], av, bq[b]);
+        }
+      }
+      continue;
+    }
+    // three-factor product: choose the chain order for this tile
+    const double ca = (double)m * n * nc + (double)nr * m * nc;
+    const double cb = (double)nr * m * n + (double)nr * n * nc;
+    if (ca <= cb) {
+      // L (X R^T): T chunk (8 x 16) = X[k0..k0+8, :] R[cols, :]^T
+      for (int k0 = 0; k0 < m; k0 += 8) {
+        double tc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+        for (int b0 = 0; b0 < n; b0 += 4) {
+          const double av = Xv(k0 + g, b0 + t);
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+            if (b < nct) dmma(tc[b], av, Rv(8 * b + g, b0 + t));
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          S[g * 17 + 8 * b + 2 * t] = tc[b][0];
+          S[g * 17 + 8 * b + 2 * t + 1] = tc[b][1];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          double bq[2];
+#pragma unroll
+          for (int b = 0; b < 2; ++b) bq[b] = S[(4 * s + t) * 17 + 8 * b + g];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            if (a >= nrt) break;
+            const double av = al * Lv(8 * a + g, k0 + 4 * s + t);
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+              if (b < nct) dmma(acc[a][b], av, bq[b]);
+          }
+        }
+        __syncwarp();
+      }
+    } else {
+      // (L X) R^T: U chunk (32 x 8) = L[rows, :] X[:, n0..n0+8]
+      for (int n0 = 0; n0 < n; n0 += 8) {
+        double uc[4][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+        for (int k0 = 0; k0 < m; k0 += 4) {
+          const double bx = Xv(k0 + t, n0 + g);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+            if (a < nrt) dmma(uc[a], Lv(8 * a + g, k0 + t), bx);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          S[(8 * a + g) * 9 + 2 * t] = uc[a][0];
+          S[(8 * a + g) * 9 + 2 * t + 1] = uc[a][1];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          double bq[2];
+#pragma unroll
+          for (int b = 0; b < 2; ++b) bq[b] = Rv(8 * b + g, n0 + 4 * s + t);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            if (a >= nrt) break;
+            const double av = al * S[(8 * a + g) * 9 + 4 * s + t];
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+              if (b < nct) dmma(acc[a][b], av, bq[b]);
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int i = 8 * a + g, j = 8 * b + 2 * t + e;
+        if (i < nr && j < nc) Y[(long long)(T.row0 + i) * G.r + T.col0 + j] = acc[a][b][e];
+      }
+}
+
+// split tiles: output = sum of the pieces' partial tiles in piece order
+__global__ void k_reduce_splits(const SplitRed* __restrict__ reds, int nreds, const Group* __restrict__ groups,
+                                const double* __restrict__ part, long long psize, double* yv, long long ys) {
+  const int vec = blockIdx.y;
+  for (int b = blockIdx.x; b < nreds; b += gridDim.x) {
+    const SplitRed R = reds[b];
+    const Group G = groups[R.g];
+    const int nel = R.nrows * R.ncols;
+    const double* p = part + (long long)vec * psize + R.poff;
+    double* Y = yv + (long long)vec * ys + G.yoff;
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+      double s = 0.0;
+      for (int q = 0; q < R.nsplit; ++q) s += p[(long long)q * nel + e];
+      Y[(long long)(R.row0 + e / R.ncols) * G.r + R.col0 + e % R.ncols] = s;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -216,6 +423,15 @@ __global__ void k_heff_diag(const Task* __restrict__ tasks, const int* __restric
       diag[G.yoff + e] = s;
     }
   }
+}
+
+void launch_reduce_splits(CudaBackend& be, const SplitRed* reds, int nreds, const Group* groups, const double* part,
+                          long long psize, double* yv, long long ys, int nvec) {
+  if (nreds <= 0) return;
+  dim3 grid(std::min(nreds, 65535), nvec);
+  k_reduce_splits<<<grid, 128, 0, be.stream()>>>(reds, nreds, groups, part, psize, yv, ys);
+  be.launches++;
+  be.note(cudaGetLastError(), "k_reduce_splits");
 }
 
 void launch_heff_diag(CudaBackend& be, const Task* d_tasks, const int* d_idx, const int* d_rng, int ngroups,
@@ -628,6 +844,12 @@ void launch_gather(CudaBackend& be, const double* src, const long long* so, cons
 // ---------------------------------------------------------------------------
 // backend
 // ---------------------------------------------------------------------------
+CudaBackend::CudaBackend(int device, cudaStream_t s, bool own) : device_(device), stream_(s), own_(own) {
+  const char* k = std::getenv("TNS_FP64_KERNEL");
+  if (k && std::strcmp(k, "dfma") == 0) fp64_kernel = 0;
+  if (k && std::strcmp(k, "dmma") == 0) fp64_kernel = 1;
+}
+
 CudaBackend::~CudaBackend() {
   for (auto& kv : lists_) free_list(kv.second);
   for (auto& s : scratch_)
@@ -712,14 +934,33 @@ void CudaBackend::free_list(DevList& d) {
   if (d.tasks) cudaFree(d.tasks);
   if (d.groups) cudaFree(d.groups);
   if (d.tiles) cudaFree(d.tiles);
+  if (d.wtiles) cudaFree(d.wtiles);
+  if (d.reds) cudaFree(d.reds);
+  if (d.part) cudaFree(d.part);
   if (d.tc) release_tc_plan(d.tc);
   d = DevList();
 }
 
+// estimated cost of one product (flops of the cheaper chain)
+static double task_cost(const Task& t) {
+  const double q = t.q, m = t.m, n = t.n, r = t.r;
+  if ((t.flags & TF_LI) && (t.flags & TF_RI)) return m * n;
+  if (t.flags & (TF_LI | TF_RI | TF_XI)) return 2.0 * std::max(q * m * n, std::max(m * n * r, q * m * r));
+  return std::min(2.0 * m * r * (n + q), 2.0 * q * n * (m + r));
+}
+
 void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
   free_list(d);
-  // tiles of at most 64 x 64, split into size classes
+  // tiles of at most 64 x 64, split into size classes; a tile whose task
+  // list is long is cut into pieces of similar cost (split-K), each written
+  // to a partial tile and summed afterwards in piece order, so that every
+  // class fills the GPU and no CTA walks a much longer list than the rest
   std::vector<Tile> cls[3];
+  std::vector<double> cost[3];
+  double ctot[3] = {0, 0, 0};
+  std::vector<double> gcost(tl.groups.size(), 0.0);
+  for (int g = 0; g < (int)tl.groups.size(); ++g)
+    for (int i = tl.groups[g].t0; i < tl.groups[g].t1; ++i) gcost[g] += task_cost(tl.tasks[i]);
   for (int g = 0; g < (int)tl.groups.size(); ++g) {
     const Group& G = tl.groups[g];
     for (int r0 = 0; r0 < G.q; r0 += 64)
@@ -730,19 +971,100 @@ void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
         t.col0 = c0;
         t.nrows = std::min(64, G.q - r0);
         t.ncols = std::min(64, G.r - c0);
+        t.t0 = G.t0;
+        t.t1 = G.t1;
+        t.poff = -1;
         int c = (t.nrows <= C0_TR && t.ncols <= C0_TC) ? 0 : (t.nrows <= C1_TR && t.ncols <= C1_TC) ? 1 : 2;
+        const double w = gcost[g] * (double)t.nrows * t.ncols / std::max(1.0, (double)G.q * G.r);
         cls[c].push_back(t);
+        cost[c].push_back(w);
+        ctot[c] += w;
       }
   }
+  // resident CTAs per SM of each class (registers) x SMs x 2 rounds
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device_);
+  const double slots[3] = {16.0 * sms * 2, 4.0 * sms * 2, 2.0 * sms * 2};
   std::vector<Tile> all;
+  std::vector<SplitRed> reds;
+  long long poff = 0;
   for (int c = 0; c < 3; ++c) {
-    d.ncls[c] = (int)cls[c].size();
-    all.insert(all.end(), cls[c].begin(), cls[c].end());
+    const double target = std::max(ctot[c] / slots[c], 1.0);
+    int count = 0;
+    for (size_t i = 0; i < cls[c].size(); ++i) {
+      Tile t = cls[c][i];
+      const int ntask = t.t1 - t.t0;
+      int ns = (int)std::min<double>(ntask, std::ceil(cost[c][i] / target));
+      ns = std::max(1, std::min(ns, 64));
+      if (ns == 1) {
+        all.push_back(t);
+        ++count;
+        continue;
+      }
+      // cut the task range at equal shares of its cost
+      double tot = 0;
+      for (int k = t.t0; k < t.t1; ++k) tot += task_cost(tl.tasks[k]);
+      SplitRed R;
+      R.g = t.g;
+      R.row0 = t.row0;
+      R.col0 = t.col0;
+      R.nrows = t.nrows;
+      R.ncols = t.ncols;
+      R.poff = poff;
+      int start = t.t0, made = 0;
+      double acc = 0;
+      for (int k = t.t0; k < t.t1 && made < ns - 1; ++k) {
+        acc += task_cost(tl.tasks[k]);
+        if (acc >= tot * (made + 1) / ns) {
+          Tile p = t;
+          p.t0 = start;
+          p.t1 = k + 1;
+          p.poff = poff;
+          poff += (long long)t.nrows * t.ncols;
+          all.push_back(p);
+          ++made;
+          ++count;
+          start = k + 1;
+        }
+      }
+      Tile p = t;
+      p.t0 = start;
+      p.t1 = t.t1;
+      p.poff = poff;
+      poff += (long long)t.nrows * t.ncols;
+      all.push_back(p);
+      ++count;
+      R.nsplit = made + 1;
+      reds.push_back(R);
+    }
+    d.ncls[c] = count;
   }
+  d.psize = poff;
+  d.nreds = (int)reds.size();
+  d.reds = dev_copy(reds, *this);
   d.ntiles = (int)all.size();
   d.tasks = dev_copy(tl.tasks, *this);
   d.groups = dev_copy(tl.groups, *this);
   d.tiles = dev_copy(all, *this);
+  std::vector<Tile> wt;
+  for (int g = 0; g < (int)tl.groups.size(); ++g) {
+    const Group& G = tl.groups[g];
+    for (int r0 = 0; r0 < G.q; r0 += DM_WR)
+      for (int c0 = 0; c0 < G.r; c0 += DM_WC) {
+        Tile t;
+        t.g = g;
+        t.row0 = r0;
+        t.col0 = c0;
+        t.nrows = std::min(DM_WR, G.q - r0);
+        t.ncols = std::min(DM_WC, G.r - c0);
+        t.t0 = G.t0;
+        t.t1 = G.t1;
+        t.poff = -1;
+        wt.push_back(t);
+      }
+  }
+  d.nwtiles = (int)wt.size();
+  d.wtiles = dev_copy(wt, *this);
   d.gen = tl.gen;
   note(cudaStreamSynchronize(stream_), "work list upload");
 }
@@ -778,21 +1100,56 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
   if (!d->tiles) return;
   if (precision != 0) {
     launch_tasks_tc(*this, tl, *d, xv, yv, nvec, xs, ys, precision);
+  } else if (fp64_kernel == 1) {
+    if (d->nwtiles > 0) {
+      dim3 grid((d->nwtiles + DM_WARPS - 1) / DM_WARPS, nvec);
+      k_tasks_dmma<<<grid, 32 * DM_WARPS, 0, stream_>>>(d->tasks, d->groups, d->wtiles, d->nwtiles, xv, yv, xs, ys);
+      launches++;
+      note(cudaGetLastError(), "k_tasks_dmma");
+    }
   } else {
+    if (d->psize > 0 && d->part_nvec < nvec) {
+      if (d->part) {
+        cudaStreamSynchronize(stream_);
+        cudaFree(d->part);
+      }
+      d->part = nullptr;
+      d->part_nvec = 0;
+      if (cudaMalloc(&d->part, sizeof(double) * d->psize * nvec) != cudaSuccess) {
+        cudaGetLastError();
+        note(cudaErrorMemoryAllocation, "split partial tiles");
+        d->part = nullptr;
+      } else {
+        d->part_nvec = nvec;
+      }
+    }
+    if (d->psize > 0 && !d->part) {
+      if (!tl.persistent) free_list(tmp);
+      return;
+    }
     int t0 = 0;
     for (int c = 0; c < 3; ++c) {
       int n = d->ncls[c];
       if (n == 0) continue;
       dim3 grid(n, nvec);
       if (c == 0)
-        k_tasks_fp64<C0_NT, C0_ACC, C0_TR, C0_TC><<<grid, C0_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
+        k_tasks_fp64<C0_NT, C0_ACC, C0_TR, C0_TC><<<grid, C0_NT, 0, stream_>>>(
+            d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys, d->part, d->psize);
       else if (c == 1)
-        k_tasks_fp64<C1_NT, C1_ACC, C1_TR, C1_TC><<<grid, C1_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
+        k_tasks_fp64<C1_NT, C1_ACC, C1_TR, C1_TC><<<grid, C1_NT, 0, stream_>>>(
+            d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys, d->part, d->psize);
       else
-        k_tasks_fp64<C2_NT, C2_ACC, C2_TR, C2_TC><<<grid, C2_NT, 0, stream_>>>(d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys);
+        k_tasks_fp64<C2_NT, C2_ACC, C2_TR, C2_TC><<<grid, C2_NT, 0, stream_>>>(
+            d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys, d->part, d->psize);
       launches++;
       note(cudaGetLastError(), "k_tasks_fp64");
       t0 += n;
+    }
+    if (d->nreds > 0) {
+      dim3 grid(std::min(d->nreds, 65535), nvec);
+      k_reduce_splits<<<grid, 128, 0, stream_>>>(d->reds, d->nreds, d->groups, d->part, d->psize, yv, ys);
+      launches++;
+      note(cudaGetLastError(), "k_reduce_splits");
     }
   }
   if (!tl.persistent) free_list(tmp);

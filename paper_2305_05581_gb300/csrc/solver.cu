@@ -191,6 +191,12 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
     launch_multidot(be, V.d(), n, k + 1, AV.d() + (long long)k * n, n, dcoef);
     std::vector<double> hc;
     get(be, hc, dcoef, k + 1);
+    if (lowp && k > 0) {
+      // couplings to V_0 from its exact FP64 product: <V_k, H V_0> instead of
+      // <V_0, H~ V_k>; near convergence the reduced-precision error of the
+      // latter exceeds the coupling itself and would stall the refinement
+      hc[0] = dot1(V.d() + (long long)k * n, AV.d());
+    }
     for (int i = 0; i <= k; ++i) H[(size_t)i * kmax + k] = H[(size_t)k * kmax + i] = hc[i];
     ++k;
     // Rayleigh-Ritz on the device

@@ -31,18 +31,20 @@ namespace tns {
 
 namespace {
 
-constexpr int TC_NT = 128;
+// two CTAs of 8 warps per SM: ~105 KB shared memory and 256 TMEM columns each
+constexpr int TC_NT = 256;
 constexpr int TC_M = 128;    // MMA M (rows of a tile / of an X chunk)
 constexpr int TC_RMAX = 64;  // tile columns
-constexpr int TC_N1 = 256;   // GEMM1 N limit (p * r_pad)
+constexpr int TC_N1 = 128;   // GEMM1 N limit (p * r_pad) = TMEM columns of D1
 constexpr int TC_K1 = 32;    // GEMM1 K chunk (elements)
-constexpr int TC_K2 = 128;   // GEMM2 K limit per chunk (p * mc16)
+constexpr int TC_K2 = 96;    // GEMM2 K limit per chunk (p * mc16)
 constexpr long long TC_SPIN = 20000000;
 
 struct TcTile {
   int g;
   int row0, col0, nrows, ncols;
-  int c0, c1;  // chunk range
+  int c0, c1;      // chunk range of this piece
+  long long poff;  // -1: write the output block; else offset of this piece's partial tile
 };
 struct TcChunk {
   int t0, t1;  // tasks (indices into the permuted task array)
@@ -56,6 +58,11 @@ struct TcPlan {
   TcChunk* chunks = nullptr;
   int ntiles = 0;
   int* flag = nullptr;
+  SplitRed* reds = nullptr;  // split tiles (pieces summed in order afterwards)
+  int nreds = 0;
+  long long psize = 0;
+  double* part = nullptr;
+  int part_nvec = 0;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -135,10 +142,11 @@ __device__ __forceinline__ double g_opR(const Task& t, int j, int k) {
 }
 
 template <int TF32>
-__global__ void __launch_bounds__(TC_NT, 1) k_tasks_tc(const Task* __restrict__ tasks, const Group* __restrict__ groups,
+__global__ void __launch_bounds__(TC_NT, 2) k_tasks_tc(const Task* __restrict__ tasks, const Group* __restrict__ groups,
                                                         const TcTile* __restrict__ tiles,
                                                         const TcChunk* __restrict__ chunks, const double* xv,
-                                                        double* yv, long long xs, long long ys, int* flag) {
+                                                        double* yv, long long xs, long long ys, int* flag,
+                                                        double* part_all, long long psize) {
   constexpr int ES = TF32 ? 4 : 2;
   constexpr int NPROD = TF32 ? 1 : 3;
   constexpr int KSTEP = 16 / ES * 2;  // elements per MMA k-step (32 bytes)
@@ -162,6 +170,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_tasks_tc(const Task* __restrict__ 
   const int vec = blockIdx.y;
   const double* X0 = xv + (long long)vec * xs;
   const int rpad = (TL.ncols + 15) & ~15;
+  double* part = TL.poff >= 0 ? part_all : nullptr;  // split piece: write the partial tile
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
@@ -169,12 +178,12 @@ __global__ void __launch_bounds__(TC_NT, 1) k_tasks_tc(const Task* __restrict__ 
     bad = 0;
   }
   if (tid < 32) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tbase)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tbase)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tD1 = tbase, tD2 = tbase + 256;
+  const uint32_t tD1 = tbase, tD2 = tbase + TC_N1;
   uint32_t phase = 0;
   bool d2 = false;
 
@@ -240,12 +249,14 @@ __global__ void __launch_bounds__(TC_NT, 1) k_tasks_tc(const Task* __restrict__ 
         put<TF32>(A2h, A2l, coff<ES>(i, kk, TC_K2), x);
       }
       if (C.kind == 0) {
-        // from TMEM: warp w holds rows 32w..32w+31 of D1 (row = k index inside a task's slot)
-        const int warp = tid >> 5, row = tid;
+        // from TMEM: warp w reads lane quarter w%4 (rows 32(w%4)..+31 of D1,
+        // row = k index inside a task's slot); the two warpgroups split the
+        // column chunks
+        const int warp = tid >> 5, row = ((warp & 3) << 5) | (tid & 31), wg = warp >> 2;
         for (int t = 0; t < pc; ++t)
-          for (int j0 = 0; j0 < rpad; j0 += 8) {
+          for (int j0 = 8 * wg; j0 < rpad; j0 += 16) {
             uint32_t r[8];
-            const uint32_t addr = tD1 + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * rpad + j0);
+            const uint32_t addr = tD1 + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(t * rpad + j0);
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
                            "=r"(r[7])
@@ -293,11 +304,11 @@ __global__ void __launch_bounds__(TC_NT, 1) k_tasks_tc(const Task* __restrict__ 
   }
   // epilogue: D2 -> Y (FP64)
   double* Y = yv + (long long)vec * ys + G.yoff;
-  const int warp = tid >> 5, row = tid;
-  for (int j0 = 0; j0 < rpad; j0 += 8) {
+  const int warp = tid >> 5, row = ((warp & 3) << 5) | (tid & 31), wg = warp >> 2;
+  for (int j0 = 8 * wg; j0 < rpad; j0 += 16) {
     uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (d2 && !bad) {
-      const uint32_t addr = tD2 + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0;
+      const uint32_t addr = tD2 + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)j0;
       asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                    : "r"(addr));
@@ -305,8 +316,12 @@ __global__ void __launch_bounds__(TC_NT, 1) k_tasks_tc(const Task* __restrict__ 
     }
     if (row < TL.nrows)
       for (int q = 0; q < 8; ++q)
-        if (j0 + q < TL.ncols)
-          Y[(long long)(TL.row0 + row) * G.r + TL.col0 + j0 + q] = (double)__uint_as_float(r[q]);
+        if (j0 + q < TL.ncols) {
+          if (part)
+            part[(long long)vec * psize + TL.poff + row * TL.ncols + j0 + q] = (double)__uint_as_float(r[q]);
+          else
+            Y[(long long)(TL.row0 + row) * G.r + TL.col0 + j0 + q] = (double)__uint_as_float(r[q]);
+        }
   }
   if (bad && tid == 0) {
     // let any MMA still in flight finish (bounded) before the TMEM is released
@@ -315,7 +330,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_tasks_tc(const Task* __restrict__ 
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
+  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tbase));
 }
 
 template <int TF32>
@@ -377,12 +392,85 @@ void build_plan(const TaskList& tl, std::vector<Task>& perm, std::vector<TcTile>
           i = j;
         }
         T.c1 = (int)chunks.size();
+        T.poff = -1;
         tiles.push_back(T);
       }
   }
 }
 
+// cut tiles whose chunk lists are long into pieces of similar cost (each piece
+// accumulates its own TMEM tile and writes a partial tile; the pieces are
+// summed in order afterwards), so the CTAs of one launch finish together
+void split_plan(const TaskList& tl, const std::vector<Task>& perm, std::vector<TcTile>& tiles,
+                const std::vector<TcChunk>& chunks, std::vector<SplitRed>& reds, long long& psize, int sms) {
+  auto ccost = [&](const TcChunk& C) {
+    double s = 4.0e4;  // fixed cost of one chunk (staging passes and two MMA round trips)
+    for (int t = C.t0; t < C.t1; ++t) {
+      const Task& k = perm[t];
+      s += 2.0 * k.m * k.n * std::min(k.r, TC_RMAX) + 2.0 * std::min(k.q, TC_M) * k.m * std::min(k.r, TC_RMAX);
+    }
+    return s;
+  };
+  std::vector<double> tcost(tiles.size(), 0.0);
+  double tot = 0;
+  for (size_t i = 0; i < tiles.size(); ++i) {
+    for (int c = tiles[i].c0; c < tiles[i].c1; ++c) tcost[i] += ccost(chunks[c]);
+    tot += tcost[i];
+  }
+  const double target = std::max(tot / (2.0 * sms * 2.0), 1.0);
+  std::vector<TcTile> out;
+  psize = 0;
+  reds.clear();
+  for (size_t i = 0; i < tiles.size(); ++i) {
+    const TcTile& T = tiles[i];
+    const int nch = T.c1 - T.c0;
+    int ns = (int)std::min<double>(nch, std::ceil(tcost[i] / target));
+    ns = std::max(1, std::min(ns, 64));
+    if (ns == 1) {
+      out.push_back(T);
+      continue;
+    }
+    SplitRed R;
+    R.g = T.g;
+    R.row0 = T.row0;
+    R.col0 = T.col0;
+    R.nrows = T.nrows;
+    R.ncols = T.ncols;
+    R.poff = psize;
+    int start = T.c0, made = 0;
+    double acc = 0;
+    for (int c = T.c0; c < T.c1 && made < ns - 1; ++c) {
+      acc += ccost(chunks[c]);
+      if (acc >= tcost[i] * (made + 1) / ns) {
+        TcTile p = T;
+        p.c0 = start;
+        p.c1 = c + 1;
+        p.poff = psize;
+        psize += (long long)T.nrows * T.ncols;
+        out.push_back(p);
+        ++made;
+        start = c + 1;
+      }
+    }
+    TcTile p = T;
+    p.c0 = start;
+    p.c1 = T.c1;
+    p.poff = psize;
+    psize += (long long)T.nrows * T.ncols;
+    out.push_back(p);
+    R.nsplit = made + 1;
+    reds.push_back(R);
+  }
+  tiles.swap(out);
+  (void)tl;
+}
+
 }  // namespace
+
+void launch_reduce_splits(CudaBackend& be, const SplitRed* reds, int nreds, const Group* groups, const double* part,
+                          long long psize, double* yv, long long ys, int nvec);
+
+void release_tc_plan(void* p);
 
 void launch_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, const double* xv, double* yv, int nvec,
                      long long xs, long long ys, int precision) {
@@ -390,36 +478,57 @@ void launch_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, const doub
   if (!plan || d.tc_gen != tl.gen) {
     if (plan) {
       cudaStreamSynchronize(be.stream());
-      cudaFree(plan->tasks);
-      cudaFree(plan->tiles);
-      cudaFree(plan->chunks);
-      cudaFree(plan->flag);
-      delete plan;
+      release_tc_plan(plan);
     }
     std::vector<Task> perm;
     std::vector<TcTile> tiles;
     std::vector<TcChunk> chunks;
+    std::vector<SplitRed> reds;
+    long long psize = 0;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, be.device());
     build_plan(tl, perm, tiles, chunks);
+    split_plan(tl, perm, tiles, chunks, reds, psize, sms);
     plan = new TcPlan();
     bool ok = cudaMalloc(&plan->tasks, sizeof(Task) * std::max<size_t>(perm.size(), 1)) == cudaSuccess &&
               cudaMalloc(&plan->tiles, sizeof(TcTile) * std::max<size_t>(tiles.size(), 1)) == cudaSuccess &&
               cudaMalloc(&plan->chunks, sizeof(TcChunk) * std::max<size_t>(chunks.size(), 1)) == cudaSuccess &&
-              cudaMalloc(&plan->flag, sizeof(int)) == cudaSuccess;
+              cudaMalloc(&plan->flag, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&plan->reds, sizeof(SplitRed) * std::max<size_t>(reds.size(), 1)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       be.note(cudaErrorMemoryAllocation, "tensor-core plan");
-      delete plan;
+      release_tc_plan(plan);
       d.tc = nullptr;
       return;
     }
     if (!perm.empty()) cudaMemcpyAsync(plan->tasks, perm.data(), sizeof(Task) * perm.size(), cudaMemcpyHostToDevice, be.stream());
     if (!tiles.empty()) cudaMemcpyAsync(plan->tiles, tiles.data(), sizeof(TcTile) * tiles.size(), cudaMemcpyHostToDevice, be.stream());
     if (!chunks.empty()) cudaMemcpyAsync(plan->chunks, chunks.data(), sizeof(TcChunk) * chunks.size(), cudaMemcpyHostToDevice, be.stream());
+    if (!reds.empty()) cudaMemcpyAsync(plan->reds, reds.data(), sizeof(SplitRed) * reds.size(), cudaMemcpyHostToDevice, be.stream());
     plan->ntiles = (int)tiles.size();
+    plan->nreds = (int)reds.size();
+    plan->psize = psize;
     d.tc = plan;
     d.tc_gen = tl.gen;
+    be.note(cudaStreamSynchronize(be.stream()), "tensor-core plan upload");
   }
   if (plan->ntiles == 0) return;
+  if (plan->psize > 0 && plan->part_nvec < nvec) {
+    if (plan->part) {
+      cudaStreamSynchronize(be.stream());
+      cudaFree(plan->part);
+    }
+    plan->part = nullptr;
+    plan->part_nvec = 0;
+    if (cudaMalloc(&plan->part, sizeof(double) * plan->psize * nvec) != cudaSuccess) {
+      cudaGetLastError();
+      be.note(cudaErrorMemoryAllocation, "tensor-core partial tiles");
+      plan->part = nullptr;
+      return;
+    }
+    plan->part_nvec = nvec;
+  }
   cudaMemsetAsync(plan->flag, 0, sizeof(int), be.stream());
   dim3 grid(plan->ntiles, nvec);
   if (precision == 1) {
@@ -429,7 +538,7 @@ void launch_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, const doub
       attr = true;
     }
     k_tasks_tc<1><<<grid, TC_NT, tc_smem<1>(), be.stream()>>>(plan->tasks, d.groups, plan->tiles, plan->chunks, xv,
-                                                             yv, xs, ys, plan->flag);
+                                                             yv, xs, ys, plan->flag, plan->part, plan->psize);
   } else {
     static bool attr = false;
     if (!attr) {
@@ -437,10 +546,12 @@ void launch_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, const doub
       attr = true;
     }
     k_tasks_tc<0><<<grid, TC_NT, tc_smem<0>(), be.stream()>>>(plan->tasks, d.groups, plan->tiles, plan->chunks, xv,
-                                                             yv, xs, ys, plan->flag);
+                                                             yv, xs, ys, plan->flag, plan->part, plan->psize);
   }
   be.launches++;
   be.note(cudaGetLastError(), "k_tasks_tc");
+  if (plan->nreds > 0)
+    launch_reduce_splits(be, plan->reds, plan->nreds, d.groups, plan->part, plan->psize, yv, ys, nvec);
   int h = 0;
   cudaMemcpyAsync(&h, plan->flag, sizeof(int), cudaMemcpyDeviceToHost, be.stream());
   be.note(cudaStreamSynchronize(be.stream()), "k_tasks_tc");
@@ -450,6 +561,8 @@ void launch_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, const doub
 void release_tc_plan(void* p) {
   TcPlan* plan = (TcPlan*)p;
   if (!plan) return;
+  if (plan->reds) cudaFree(plan->reds);
+  if (plan->part) cudaFree(plan->part);
   cudaFree(plan->tasks);
   cudaFree(plan->tiles);
   cudaFree(plan->chunks);

@@ -112,3 +112,20 @@ def test_sweep_bf16x3_reaches_fci_n8():
     ctx.mps_init(c["N"], c["n_elec"], c["two_sz"], c["D"], seed=1)
     e, st = ctx.sweep(4, c["D"], tol=1e-7, max_iter=300, precision=TNS_BF16X3)
     assert abs(e - fci_energy(h, v, c["n_elec"], c["two_sz"])) < 1e-8
+
+
+@pytest.mark.parametrize("prec", [TNS_FP64, TNS_BF16X3])
+def test_four_vectors_in_one_launch(prec):
+    """A block of four Davidson vectors in one call equals four single calls."""
+    N, n, s2, D, k = 8, 8, 0, 60, 3
+    ctx, h, v, bonds, sites = _setup(N, n, s2, D, k, 77)
+    desc, length = ctx.psi_layout(k)
+    g = torch.Generator(device="cuda").manual_seed(9)
+    x = torch.randn(4 * length, device="cuda", dtype=torch.float64, generator=g)
+    y4 = torch.empty_like(x)
+    ctx.heff_apply_ptr(k, x.data_ptr(), y4.data_ptr(), 4, prec)
+    y1 = torch.empty_like(x)
+    for j in range(4):
+        ctx.heff_apply_ptr(k, x[j * length:].data_ptr(), y1[j * length:].data_ptr(), 1, prec)
+    torch.cuda.synchronize()
+    assert torch.equal(y4, y1)
