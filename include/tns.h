@@ -184,8 +184,20 @@ int tns_heff_diag_noalloc(tns_ctx* ctx, int site, double* diag);
 int tns_davidson(tns_ctx* ctx, int site, double* X, double tol, int max_iter, int precision,
                  double* energy, int* iters);
 
+/* Batched dense symmetric eigen-decomposition, the solver the truncation uses
+ * on each middle-bond sector's reduced density matrix (the SVD hand-off of the
+ * two-site step, Sec. III.A; Householder tridiagonalisation then implicit QR
+ * with the Wilkinson shift, one CTA per matrix).  nmat matrices of sizes n[i]
+ * (HOST array, each n[i] <= 4096) packed one after another, row-major, in the
+ * DEVICE array A (sum n[i]^2 doubles; overwritten).  Z (DEVICE, same size)
+ * receives eigenvector p of matrix i as row p of its n[i] x n[i] block; w
+ * (DEVICE, sum n[i] doubles) the eigenvalues, unsorted, in the same order.
+ * Synchronous.  TNS_ERR_ARG for a size above the limit, TNS_ERR_NOCONV if a
+ * matrix hits the QR step limit. */
+int tns_sym_eig(tns_ctx* ctx, int nmat, const int* n, double* A, double* Z, double* w);
+
 typedef struct tns_sweep_opts {
-  int nsweeps;          /* full sweeps (left->right then right->left) */
+  int nsweeps;         /* full sweeps (left->right then right->left) */
   int D;                /* bond dimension cap (<= the D of the MPS) */
   double tol;           /* Davidson residual tolerance (2-norm, normalised vector) */
   int max_iter;         /* Davidson matrix-vector products per step */

@@ -22,7 +22,7 @@ DEFAULT_LIB = os.path.join(HERE, "libtns.so")
 SYMBOLS = ["create", "destroy", "last_error", "load_integrals", "mps_init", "mps_define",
            "mps_set_bond", "mps_set_site", "mps_get_bond", "mps_get_site", "build_env",
            "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops", "step", "psi_guess",
-           "heff_diag_noalloc", "env_arena", "heff_adjoint"]
+           "heff_diag_noalloc", "env_arena", "heff_adjoint", "sym_eig"]
 
 
 class TnsError(RuntimeError):
@@ -86,6 +86,7 @@ def load_library(path: str = DEFAULT_LIB, prefix: str = "tns_"):
         "heff_diag_noalloc": (C.c_int, [vp, C.c_int, vp]),
         "env_arena": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(vp), llp]),
         "heff_adjoint": (C.c_int, [vp, C.c_int, vp, vp, vp, vp, vp]),
+        "sym_eig": (C.c_int, [vp, C.c_int, ip, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = f(name)
@@ -208,6 +209,12 @@ class Context:
     def heff_adjoint_ptr(self, site, x_ptr, yb_ptr, xb_ptr=0, lb_ptr=0, rb_ptr=0):
         v = lambda p: C.c_void_p(p) if p else None
         self._check(self._fn("heff_adjoint")(self._h, site, v(x_ptr), v(yb_ptr), v(xb_ptr), v(lb_ptr), v(rb_ptr)))
+
+    def sym_eig_ptr(self, sizes, a_ptr: int, z_ptr: int, w_ptr: int):
+        """Batched symmetric eigen-decomposition of packed DEVICE matrices (tns_sym_eig)."""
+        n = (C.c_int * max(1, len(sizes)))(*sizes)
+        self._check(self._fn("sym_eig")(self._h, len(sizes), n, C.c_void_p(a_ptr), C.c_void_p(z_ptr),
+                                        C.c_void_p(w_ptr)))
 
     def heff_flops(self, site):
         f = C.c_double()

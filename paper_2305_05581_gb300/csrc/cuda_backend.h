@@ -118,6 +118,12 @@ void launch_residual(CudaBackend& be, const double* AVs, const double* x, const 
 // A: nmat matrices at A + off[i] with size n[i]; V: eigenvectors (columns) at V + off[i]; w: eigenvalues at w + woff[i]
 void launch_jacobi(CudaBackend& be, double* A, double* V, double* w, const long long* off, const int* n,
                    const int* woff, int nmat, int maxn, int* sweeps_out);
+// batched symmetric eigensolver (Householder tridiagonalisation + implicit QR),
+// one CTA per matrix; eigenvector p is ROW p of Z (Z + off[i], n x n); A is
+// overwritten; *status (nullable) is set to 1 if a matrix hit the QR step limit
+constexpr int SYEV_MAXN = 4096;
+void launch_syev(CudaBackend& be, double* A, double* Z, double* w, const long long* off, const int* n,
+                 const int* woff, int nmat, int maxn, int* status);
 void launch_select(CudaBackend& be, const double* w, const int* sec_of, int total, int keep_max, double cut,
                    int* keep_flag, double* disc);
 void launch_gather(CudaBackend& be, const double* src, const long long* so, const int* sld, double* dst,

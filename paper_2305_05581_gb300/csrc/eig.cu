@@ -1,0 +1,239 @@
+// Batched symmetric eigen-decomposition for the truncation (reduced density
+// matrix of each sector of the new bond).  One CTA per matrix:
+//   1. Householder tridiagonalisation T = Q^T A Q (Golub & Van Loan,
+//      "Matrix Computations", Sec. 8.3.1), reflectors kept in the rows of A;
+//   2. explicit Z = Q^T by backward accumulation of the reflectors;
+//   3. implicit symmetric QR steps with the Wilkinson shift and deflation
+//      (Golub & Van Loan Sec. 8.3.3-8.3.5) on (d, e); thread 0 computes the
+//      Givens rotations of a bulge chase, then every thread applies them to its
+//      own columns of Z (rows i, i+1 of Z rotate), so no barrier is needed
+//      inside a chase and the accesses are coalesced.
+// Output: eigenvalues w[woff + p] and eigenvector p as ROW p of Z
+// (Z[p * n + i], n x n row-major at off).  A is overwritten.
+#include <cuda_runtime.h>
+
+#include "cuda_backend.h"
+
+namespace tns {
+namespace {
+
+constexpr int SY_NT = 256;
+constexpr int SY_WARPS = SY_NT / 32;
+
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum; every thread gets the result
+__device__ double bsum(double v, double* red) {
+  v = wsum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int q = 0; q < SY_WARPS; ++q) s += red[q];
+  __syncthreads();
+  return s;
+}
+
+__global__ void __launch_bounds__(SY_NT) k_syev(double* A, double* Zall, double* w, const long long* off,
+                                                const int* nn, const int* woff, int maxn, int* status) {
+  extern __shared__ double sm[];
+  double* v = sm;              // Householder vector / rotation cosines
+  double* p = sm + maxn;       // work vector / rotation sines
+  double* d = sm + 2 * maxn;   // diagonal of T
+  double* e = sm + 3 * maxn;   // sub-diagonal of T (e[i] couples i, i+1)
+  __shared__ double red[SY_WARPS];
+  __shared__ int ctl[3];       // lo, hi, done
+  const int mi = blockIdx.x;
+  const int n = nn[mi];
+  if (n <= 0) return;
+  double* a = A + off[mi];
+  double* Z = Zall + off[mi];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const double eps = 2.220446049250313e-16;
+
+  // ---- 1. tridiagonalisation ------------------------------------------------
+  for (int k = 0; k + 2 < n; ++k) {
+    const long long rk = (long long)k * n;
+    // x = a[k][k+1 .. n-1] (row k = column k by symmetry)
+    double sg = 0.0;
+    for (int j = k + 2 + tid; j < n; j += SY_NT) sg += a[rk + j] * a[rk + j];
+    sg = bsum(sg, red);
+    const double alpha = a[rk + k + 1];
+    double beta = 0.0, mu = alpha, v0 = 1.0;
+    if (sg > 0.0) {
+      mu = sqrt(alpha * alpha + sg);
+      v0 = alpha <= 0.0 ? alpha - mu : -sg / (alpha + mu);
+      beta = 2.0 * v0 * v0 / (sg + v0 * v0);
+    }
+    if (tid == 0) {
+      d[k] = a[rk + k];
+      e[k] = sg > 0.0 ? mu : alpha;
+    }
+    for (int j = k + 1 + tid; j < n; j += SY_NT) v[j] = j == k + 1 ? 1.0 : a[rk + j] / v0;
+    __syncthreads();
+    if (beta != 0.0) {
+      // p = beta * A_sub v (one warp per row, coalesced)
+      for (int i = k + 1 + wid; i < n; i += SY_WARPS) {
+        const long long ri = (long long)i * n;
+        double s = 0.0;
+        for (int j = k + 1 + lane; j < n; j += 32) s += a[ri + j] * v[j];
+        s = wsum(s);
+        if (lane == 0) p[i] = beta * s;
+      }
+      __syncthreads();
+      double pv = 0.0;
+      for (int j = k + 1 + tid; j < n; j += SY_NT) pv += p[j] * v[j];
+      pv = bsum(pv, red);
+      const double K = 0.5 * beta * pv;
+      for (int j = k + 1 + tid; j < n; j += SY_NT) p[j] -= K * v[j];
+      __syncthreads();
+      // A_sub -= v p^T + p v^T
+      const int m = n - k - 1;
+      for (long long t = tid; t < (long long)m * m; t += SY_NT) {
+        const int i = k + 1 + (int)(t / m), j = k + 1 + (int)(t % m);
+        a[(long long)i * n + j] -= v[i] * p[j] + p[i] * v[j];
+      }
+    }
+    // keep the reflector: v (without its leading 1) in row k, beta on the diagonal
+    for (int j = k + 2 + tid; j < n; j += SY_NT) a[rk + j] = v[j];
+    __syncthreads();
+    if (tid == 0) a[rk + k] = beta;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = a[(long long)(n - 2) * n + n - 2];
+      e[n - 2] = a[(long long)(n - 2) * n + n - 1];
+    }
+    d[n - 1] = a[(long long)(n - 1) * n + n - 1];
+  }
+  // ---- 2. Z = Q^T = H_{n-3} ... H_0 ----------------------------------------
+  for (long long t = tid; t < (long long)n * n; t += SY_NT) Z[t] = (t / n) == (t % n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = n - 3; k >= 0; --k) {
+    const long long rk = (long long)k * n;
+    const double beta = a[rk + k];
+    if (beta == 0.0) continue;  // uniform across the block
+    for (int j = k + 1 + tid; j < n; j += SY_NT) v[j] = j == k + 1 ? 1.0 : a[rk + j];
+    __syncthreads();
+    // rows r >= k+1 of Z: Z[r][k+1:] -= beta (Z[r][k+1:] . v) v
+    for (int r = k + 1 + wid; r < n; r += SY_WARPS) {
+      const long long rr = (long long)r * n;
+      double s = 0.0;
+      for (int j = k + 1 + lane; j < n; j += 32) s += Z[rr + j] * v[j];
+      s = wsum(s) * beta;
+      for (int j = k + 1 + lane; j < n; j += 32) Z[rr + j] -= s * v[j];
+    }
+    __syncthreads();
+  }
+  // ---- 3. implicit symmetric QR with Wilkinson shift -------------------------
+  if (tid == 0) {
+    ctl[1] = n - 1;
+    ctl[2] = 0;
+  }
+  __syncthreads();
+  const int max_steps = 40 * n + 40;
+  int steps = 0;
+  for (;;) {
+    if (tid == 0) {
+      int hi = ctl[1], lo = 0, done = 0;
+      // deflate from the bottom
+      while (hi > 0) {
+        double b = fabs(e[hi - 1]);
+        if (b <= eps * (fabs(d[hi - 1]) + fabs(d[hi])) || b < 1e-300) {
+          e[hi - 1] = 0.0;
+          --hi;
+        } else {
+          break;
+        }
+      }
+      if (hi == 0) {
+        done = 1;
+      } else {
+        lo = hi - 1;
+        while (lo > 0) {
+          double b = fabs(e[lo - 1]);
+          if (b <= eps * (fabs(d[lo - 1]) + fabs(d[lo])) || b < 1e-300) {
+            e[lo - 1] = 0.0;
+            break;
+          }
+          --lo;
+        }
+        // Wilkinson shift from the trailing 2x2 of the block
+        const double dl = 0.5 * (d[hi - 1] - d[hi]);
+        const double bb = e[hi - 1] * e[hi - 1];
+        const double den = dl + (dl >= 0.0 ? 1.0 : -1.0) * sqrt(dl * dl + bb);
+        const double mu = den != 0.0 ? d[hi] - bb / den : d[hi];
+        double x = d[lo] - mu, z = e[lo];
+        for (int i = lo; i < hi; ++i) {
+          double r = hypot(x, z);
+          double c = 1.0, s = 0.0;
+          if (r != 0.0) {
+            c = x / r;
+            s = z / r;
+          }
+          if (i > lo) e[i - 1] = r;
+          const double ai = d[i], aj = d[i + 1], b = e[i];
+          d[i] = c * c * ai + 2.0 * c * s * b + s * s * aj;
+          d[i + 1] = s * s * ai - 2.0 * c * s * b + c * c * aj;
+          e[i] = c * s * (aj - ai) + (c * c - s * s) * b;
+          if (i + 1 < hi) {
+            z = s * e[i + 1];  // bulge at (i, i+2)
+            e[i + 1] *= c;
+          }
+          x = e[i];
+          v[i] = c;
+          p[i] = s;
+        }
+      }
+      ctl[0] = lo;
+      ctl[1] = hi;
+      ctl[2] = done;
+    }
+    __syncthreads();
+    if (ctl[2]) break;
+    const int lo = ctl[0], hi = ctl[1];
+    for (int j = tid; j < n; j += SY_NT) {
+      double carry = Z[(long long)lo * n + j];
+      for (int i = lo; i < hi; ++i) {
+        const double y = Z[(long long)(i + 1) * n + j];
+        const double c = v[i], s = p[i];
+        Z[(long long)i * n + j] = c * carry + s * y;
+        carry = -s * carry + c * y;
+      }
+      Z[(long long)hi * n + j] = carry;
+    }
+    __syncthreads();
+    if (++steps > max_steps) {
+      if (tid == 0 && status) atomicExch(status, 1);
+      break;
+    }
+  }
+  for (int i = tid; i < n; i += SY_NT) w[woff[mi] + i] = d[i];
+}
+
+}  // namespace
+
+void launch_syev(CudaBackend& be, double* A, double* Z, double* w, const long long* off, const int* n,
+                 const int* woff, int nmat, int maxn, int* status) {
+  if (nmat <= 0 || maxn <= 0) return;
+  if (maxn > SYEV_MAXN) {
+    be.note(cudaErrorInvalidValue, "syev: matrix too large");
+    return;
+  }
+  const size_t smem = sizeof(double) * 4 * (size_t)maxn;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+      be.note(e, "syev: shared memory attribute");
+      return;
+    }
+  }
+  k_syev<<<nmat, SY_NT, smem, be.stream()>>>(A, Z, w, off, n, woff, maxn, status);
+  be.launches++;
+  be.note(cudaGetLastError(), "syev");
+}
+
+}  // namespace tns

@@ -427,8 +427,8 @@ int truncate(Engine& E, CudaBackend& be, const double* psi, bool ltr, int Dmax, 
     err = "truncate: no middle-bond sector";
     return -1;
   }
-  if (maxn > 2048) {
-    err = "truncate: sector matrix larger than 2048";
+  if (maxn > SYEV_MAXN) {
+    err = "truncate: sector matrix larger than " + std::to_string(SYEV_MAXN);
     return -1;
   }
   DBuf M(be, sizeof(double) * mtot), RHO(be, sizeof(double) * rtot), EV(be, sizeof(double) * rtot),
@@ -516,7 +516,15 @@ int truncate(Engine& E, CudaBackend& be, const double* psi, bool ltr, int Dmax, 
     put(be, a.as<long long>(), off);
     put(be, b.as<int>(), nn);
     put(be, c.as<int>(), wo);
-    launch_jacobi(be, RHO.d(), EV.d(), W.d(), a.as<long long>(), b.as<int>(), c.as<int>(), nmat, maxn, nullptr);
+    DBuf stat(be, 8);
+    be.note(cudaMemsetAsync(stat.p, 0, 8, be.stream()), "syev status");
+    launch_syev(be, RHO.d(), EV.d(), W.d(), a.as<long long>(), b.as<int>(), c.as<int>(), nmat, maxn, stat.as<int>());
+    std::vector<int> sv;
+    get(be, sv, stat.as<int>(), 1);
+    if (sv[0]) {
+      err = "truncate: eigensolver did not converge";
+      return -4;
+    }
   }
   // global selection of the kept states
   DBuf keep(be, 4 * (size_t)wtot), dd(be, 8);
@@ -557,8 +565,8 @@ int truncate(Engine& E, CudaBackend& be, const double* psi, bool ltr, int Dmax, 
       int nn = ltr ? list[i]->R : list[i]->C;
       int kc = (int)kept[i].size();
       for (int c = 0; c < kc; ++c) {
-        so.push_back(list[i]->roff + kept[i][c]);
-        sld.push_back(nn);
+        so.push_back(list[i]->roff + (long long)kept[i][c] * nn);  // eigenvector = row of EV
+        sld.push_back(1);
         dof.push_back(soff[i] + c);
         dld.push_back(kc);
         rows.push_back(nn);
@@ -766,6 +774,43 @@ static tns::Backend* make_backend(int device, void* stream, std::string& err) {
     own = true;
   }
   return new tns::CudaBackend(device, s, own);
+}
+
+static int backend_sym_eig(tns::Engine& E, int nmat, const int* n, double* A, double* Z, double* w,
+                           std::string& err) {
+  using namespace tns;
+  CudaBackend& be = *static_cast<CudaBackend*>(E.be());
+  cudaSetDevice(be.device());
+  if (nmat == 0) return 0;
+  std::vector<long long> off(nmat);
+  std::vector<int> nn(n, n + nmat), wo(nmat);
+  long long o = 0;
+  int wt = 0, maxn = 0;
+  for (int i = 0; i < nmat; ++i) {
+    off[i] = o;
+    o += (long long)n[i] * n[i];
+    wo[i] = wt;
+    wt += n[i];
+    maxn = std::max(maxn, n[i]);
+  }
+  if (maxn > SYEV_MAXN) {
+    err = "sym_eig: matrix larger than " + std::to_string(SYEV_MAXN);
+    return -1;
+  }
+  DBuf a(be, 8 * (size_t)nmat), b(be, 4 * (size_t)nmat), c(be, 4 * (size_t)nmat), stat(be, 8);
+  put(be, a.as<long long>(), off);
+  put(be, b.as<int>(), nn);
+  put(be, c.as<int>(), wo);
+  be.note(cudaMemsetAsync(stat.p, 0, 8, be.stream()), "sym_eig status");
+  launch_syev(be, A, Z, w, a.as<long long>(), b.as<int>(), c.as<int>(), nmat, maxn, stat.as<int>());
+  std::vector<int> sv;
+  get(be, sv, stat.as<int>(), 1);
+  if (check(be, err)) return -6;
+  if (sv[0]) {
+    err = "sym_eig: QR iteration limit reached";
+    return -4;
+  }
+  return 0;
 }
 
 static int backend_diag_noalloc(tns::Engine& E, double* diag, std::string& err) {

@@ -84,6 +84,10 @@ static int backend_step(tns::Engine&, int, bool, const tns_sweep_opts*, const do
   err = "not available in the host-logic check library";
   return -2;
 }
+static int backend_sym_eig(tns::Engine&, int, const int*, double*, double*, double*, std::string& err) {
+  err = "not available in the host-logic check library";
+  return -2;
+}
 static int backend_diag_noalloc(tns::Engine&, double*, std::string& err) {
   err = "not available in the host-logic check library";
   return -2;
