@@ -4,9 +4,12 @@ A step is one two-site DMRG step (one "iteration cycle" of a sweep) at the
 middle of the chain: partial sums and work lists, device Davidson with the
 H_eff*psi grouped products, SVD truncation to D and renormalisation.
 Workload: 24 orbitals, 24 electrons, S_z = 0, random integrals with decay
-length 5 (seed 1), D = 512, FP64 -- synthetic stand-ins for the paper's
-molecular integrals.  Untimed set-up runs the sweep from the first site up to
-the warm-up steps; W warm-up steps and K timed steps follow the sweep order.
+length 5 (seed 1), D = 512 -- synthetic stand-ins for the paper's molecular
+integrals.  Sector products in split-BF16 on the tensor cores by default
+(--precision), Davidson/truncation in FP64; the energy of the next step's
+H_eff is checked against an FP64 Davidson (energy_check).  Untimed set-up: one
+full sweep (bond dimension D on both sides of the middle), then the second
+sweep up to the warm-up steps; W warm-up and K timed steps follow.
 
 Output: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 (oracle/dmrg.py) on a bounded sample of the same workload instead.
@@ -24,13 +27,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "H_eff*psi useful TFLOP/s per two-site step (FP64, 24 orbitals, D=512)"
+METRIC = "H_eff\u00b7\u03c8 useful TFLOP/s and s per two-site step at \u0394E\u22641e-8 Ha vs FP64 GPU path"
 UNIT = "TFLOP/s"
 
-# DRAM traffic of one k_tasks_fp64 launch set per H_eff*psi at this workload,
-# from the ncu capture summarised in profiles/k_tasks_fp64_n24.md (None until
-# captured for the current kernel).
-TRAFFIC_BYTES_PER_HEFF = None
+# DRAM bytes (read + write) of the dominant kernel per H_eff*psi at this
+# workload, from the ncu captures summarised under profiles/ (None until
+# captured for the current kernel of that precision).
+TRAFFIC_BYTES_PER_HEFF = {"fp64": None, "tf32": None, "bf16x3": None}
 
 
 def parse():
@@ -40,7 +43,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="n24")
-    p.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16x3"])
+    p.add_argument("--precision", default="bf16x3", choices=["fp64", "tf32", "bf16x3"],
+                   help="sector products: bf16x3 (split-BF16, FP32 accumulation; the precision form, default), "
+                        "tf32, or fp64; Davidson, residuals and truncation are FP64 in every case")
     p.add_argument("--tol", type=float, default=1e-8)
     p.add_argument("--case", default="step", choices=["step", "heff"],
                    help="step: two-site DMRG steps (the benchmark); heff: H_eff*psi alone at the middle bond "
@@ -154,6 +159,28 @@ def fp64_gemm_peak(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
+def workload_config(args, c):
+    N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
+    return {"workload": f"{args.workload}: N={N} n_elec={n} 2Sz={s2} D={D} lambda={c['lam']} seed={c['seed']}; "
+                        f"one warm-up sweep, then two-site steps around the middle bond",
+            "precision": args.precision, "davidson_tol": args.tol,
+            "l2": "inputs larger than L2 (operator arenas are GBs)"}
+
+
+def peak_for(args, torch):
+    """(peak TFLOP/s, bound, source) for the dominant kernel of the chosen precision."""
+    if args.precision == "fp64":
+        return (fp64_gemm_peak(torch), "alu",
+                "cuBLAS DGEMM 4096^3 measured in this run (MEASURED_PEAKS.json has no FP64 entry)")
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        mp = json.load(f)
+    bf16 = mp["bf16_tflops_sustained"]
+    if args.precision == "bf16x3":
+        return bf16, "tensor", "MEASURED_PEAKS.json bf16_tflops_sustained (dense bf16, timed inside a long step)"
+    return (bf16 * 1.1 / 2.25, "tensor",
+            "MEASURED_PEAKS.json bf16_tflops_sustained x nominal TF32/BF16 ratio 1.1/2.25")
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -176,10 +203,11 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    prec = {"fp64": TNS_FP64, "tf32": TNS_TF32, "bf16x3": TNS_BF16X3}[args.precision]
+    P = {"fp64": TNS_FP64, "tf32": TNS_TF32, "bf16x3": TNS_BF16X3}
+    prec = P[args.precision]
     c = synth.WORKLOADS[args.workload]
     N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
-    peak = fp64_gemm_peak(torch)
+    peak, bound, peak_source = peak_for(args, torch)
     h, v = synth.integrals(N, c["lam"], c["seed"])
     stream = torch.cuda.current_stream()
     ctx = Context(device=local, stream=stream.cuda_stream)
@@ -187,14 +215,16 @@ def main():
     ctx.mps_init(N, n, s2, D, seed=c["seed"])
     plan = sweep_plan(N)
     mid = N // 2 - 1
-    start = max(0, mid - args.warmup)
-    i = 0
-    # untimed set-up: sweep from the first site to the warm-up steps
-    for k, ltr in plan[:start]:
+    # untimed set-up: one full sweep to reach bond dimension D on both sides,
+    # then the second sweep up to the warm-up steps
+    start = max(0, mid - args.warmup - args.steps // 2)
+    setup = plan + [(k, True) for k in range(0, start)]
+    for k, ltr in setup:
         ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec)
-        i += 1
+    second = [(k, True) for k in range(start, N - 2)] + plan[N - 2:]
+    i = 0
     for _ in range(args.warmup):
-        k, ltr = plan[i % len(plan)]
+        k, ltr = second[i % len(second)]
         ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec)
         i += 1
     torch.cuda.synchronize()
@@ -209,13 +239,14 @@ def main():
     launches = 0
     stats = []
     for _ in range(args.steps):
-        k, ltr = plan[i % len(plan)]
+        k, ltr = second[i % len(second)]
         st = ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec)
         flops += st.heff_flops
         heff_s += st.heff_seconds
         iters += st.iters
         launches += st.kernel_launches
-        stats.append((k, st.energy, st.iters, st.bond_dim, st.seconds, st.length))
+        stats.append((k, st.energy, st.iters, st.bond_dim, st.seconds, st.length, st.heff_seconds,
+                      st.env_seconds, st.svd_seconds))
         i += 1
     e1.record(stream)
     torch.cuda.synchronize()
@@ -232,12 +263,25 @@ def main():
         flops_all = flops
     value = flops_all / elapsed / 1e12
 
+    # energy check at the next step's H_eff: Davidson in this precision (FP64
+    # residual correction) against Davidson in FP64, from the same start vector
+    k, ltr = second[i % len(second)]
+    ctx.build_env(k)
+    L = ctx.psi_guess(k)
+    x0 = torch.empty(L, dtype=torch.float64, pin_memory=True)
+    ctx.psi_guess(k, x0.data_ptr())
+    xa = x0.to("cuda")
+    xb = x0.to("cuda")
+    e64, _, _ = ctx.davidson_ptr(k, xa.data_ptr(), tol=args.tol, max_iter=200, precision=TNS_FP64)
+    ep, _, _ = ctx.davidson_ptr(k, xb.data_ptr(), tol=args.tol, max_iter=200, precision=prec)
+    echeck = {"site": k, "E_fp64_Ha": e64, "E_precision_Ha": ep, "delta_E_Ha": abs(ep - e64)}
+
     # end to end through the public API with host buffers: each step uploads
     # its start vector from pinned host memory and reads the converged psi back
     e2e_steps = max(1, min(args.steps, 3))
     lens = []
     for _ in range(e2e_steps):
-        k, ltr = plan[i % len(plan)]
+        k, ltr = second[i % len(second)]
         L = ctx.psi_guess(k)
         xh = torch.empty(L, dtype=torch.float64, pin_memory=True)
         ph = torch.empty(L, dtype=torch.float64, pin_memory=True)
@@ -255,11 +299,14 @@ def main():
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
     achieved = flops / heff_s / 1e12 if heff_s > 0 else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    kernel = ("k_tasks_fp64 (grouped triple product, FP64 DFMA) + split reduction" if prec == TNS_FP64 else
+              f"k_tasks_tc<{'TF32' if prec == TNS_TF32 else 'BF16x3'}> (tcgen05 grouped triple product) "
+              f"+ split reduction")
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None,
-                "traffic": TRAFFIC_BYTES_PER_HEFF,
-                "kernel": "k_tasks_fp64 (grouped triple product, FP64 DFMA)",
-                "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (FP64 has no entry in MEASURED_PEAKS.json)"}
+                "traffic": TRAFFIC_BYTES_PER_HEFF.get(args.precision),
+                "kernel": kernel, "peak_source": peak_source,
+                "achieved_is": "useful FP64-equivalent flops of the H_eff*psi products / their CUDA-event time"}
     if rank == 0:
         cpu = None
         try:
@@ -267,16 +314,14 @@ def main():
         except Exception as ex:  # the baseline is reported, never required
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {ex}"}
+        cfg = workload_config(args, c)
+        cfg["steps_detail"] = [{"site": s[0], "energy": s[1], "matvecs": s[2], "bond": s[3], "seconds": s[4],
+                                "psi_length": s[5], "heff_s": s[6], "env_s": s[7], "svd_s": s[8]} for s in stats]
+        cfg["energy_check"] = echeck
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == TNS_FP64 else args.precision,
-                "data": "synthetic",
-                "config": {"workload": f"{args.workload}: N={N} n_elec={n} 2Sz={s2} D={D} lambda={c['lam']} "
-                                       f"seed={c['seed']}, two-site steps around the middle bond",
-                           "precision": args.precision, "davidson_tol": args.tol,
-                           "l2": "inputs larger than L2 (operator arenas are GBs)",
-                           "steps_detail": [{"site": s[0], "energy": s[1], "matvecs": s[2], "bond": s[3],
-                                             "seconds": s[4], "psi_length": s[5]} for s in stats]},
+                "data": "synthetic", "config": cfg,
                 "s_per_step": elapsed / args.steps,
                 "heff_matvecs_per_step": iters / args.steps,
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
@@ -343,7 +388,7 @@ def run_reference_full(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload} sample: N={N} n_elec={n} 2Sz={s2} D={Ds}, middle bond"},
+            "config": workload_config(args, c),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
