@@ -204,6 +204,9 @@ typedef struct tns_sweep_opts {
   int precision;        /* TNS_FP64 / TNS_TF32 / TNS_BF16X3 */
   double cutoff;        /* singular values <= cutoff are dropped (e.g. 1e-14) */
   int verbose;          /* print one line per step on stdout */
+  int block;            /* Davidson block size: corrections from the lowest `block`
+                           Ritz pairs per iteration, their products in one
+                           batched H_eff*psi launch; 0 or 1 = single vector, max 4 */
 } tns_sweep_opts;
 
 typedef struct tns_sweep_stats {

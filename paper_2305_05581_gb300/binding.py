@@ -33,7 +33,7 @@ class TnsError(RuntimeError):
 
 class SweepOpts(C.Structure):
     _fields_ = [("nsweeps", C.c_int), ("D", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
-                ("precision", C.c_int), ("cutoff", C.c_double), ("verbose", C.c_int)]
+                ("precision", C.c_int), ("cutoff", C.c_double), ("verbose", C.c_int), ("block", C.c_int)]
 
 
 class SweepStats(C.Structure):
@@ -230,8 +230,8 @@ class Context:
             self._check(rc)
         return e.value, it.value, rc == 0
 
-    def sweep(self, nsweeps, D, tol=1e-8, max_iter=100, precision=TNS_FP64, cutoff=1e-14, verbose=False):
-        o = SweepOpts(nsweeps, D, tol, max_iter, precision, cutoff, int(verbose))
+    def sweep(self, nsweeps, D, tol=1e-8, max_iter=100, precision=TNS_FP64, cutoff=1e-14, verbose=False, block=1):
+        o = SweepOpts(nsweeps, D, tol, max_iter, precision, cutoff, int(verbose), block)
         e = C.c_double()
         st = SweepStats()
         self._check(self._fn("sweep")(self._h, C.byref(o), C.byref(e), C.byref(st)))
@@ -239,9 +239,9 @@ class Context:
 
 
     def step(self, site, left_to_right, D, tol=1e-8, max_iter=100, precision=TNS_FP64, cutoff=1e-14,
-             x0_host_ptr: int = 0, psi_host_ptr: int = 0):
+             x0_host_ptr: int = 0, psi_host_ptr: int = 0, block: int = 1):
         """One two-site step; host pointers (0 = none) for the start vector / result."""
-        o = SweepOpts(1, D, tol, max_iter, precision, cutoff, 0)
+        o = SweepOpts(1, D, tol, max_iter, precision, cutoff, 0, block)
         st = StepStats()
         self._check(self._fn("step")(self._h, site, int(left_to_right), C.byref(o),
                                      C.c_void_p(x0_host_ptr) if x0_host_ptr else None,

@@ -25,24 +25,59 @@ struct SplitRed {  // a split tile: sum of nsplit partial tiles (fixed order) ->
   long long poff;
 };
 
-// device copy of a work list; tiles split into size classes
-struct DevList {
-  long long gen = -1;
-  Task* tasks = nullptr;
-  Group* groups = nullptr;
+// schedule variants tried by the online autotuner: the split-K target is
+// (total cost) / (resident CTAs x SMs x rounds) with rounds = kRounds[v]
+constexpr int kNumVariants = 3;
+constexpr double kRounds[kNumVariants] = {1.0, 2.0, 4.0};
+
+// one schedule of a work list for the FP64 kernels: tiles split into size
+// classes, long task lists cut into partial tiles summed in fixed order
+struct FpVariant {
+  bool planned = false;
   Tile* tiles = nullptr;
   int ncls[3] = {0, 0, 0};   // tiles per size class (contiguous, class 0 first)
   int ntiles = 0;
-  Tile* wtiles = nullptr;    // 32 x 16 warp tiles of the FP64 tensor (DMMA) kernel
-  int nwtiles = 0;
   SplitRed* reds = nullptr;  // split tiles to reduce after the product kernels
   int nreds = 0;
   long long psize = 0;       // partial-tile elements per vector
   double* part = nullptr;    // partial tiles (psize * part_nvec)
   int part_nvec = 0;
+};
+
+// online autotuner state of one (precision, nvec) use of a work list: the
+// first kNumVariants products run one variant each and are timed; the
+// fastest is kept for the rest of the list's life
+struct Tune {
+  int next = 0;
+  int best = -1;
+  float ms[kNumVariants] = {0.f, 0.f, 0.f};
+};
+
+// captured launch sequence of one (precision, nvec) use: replayed with the
+// input copied into xbuf and the output copied out of ybuf
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  double* xbuf = nullptr;
+  double* ybuf = nullptr;
+  long long elems = 0;  // doubles per buffer (nvec * stride)
+  long long stride = 0;
+  int kernels = 0;      // kernel launches inside the graph
+  bool failed = false;  // capture not possible: launch directly
+};
+
+// device copy of a work list
+struct DevList {
+  long long gen = -1;
+  Task* tasks = nullptr;
+  Group* groups = nullptr;
+  Tile* wtiles = nullptr;    // 32 x 16 warp tiles of the FP64 tensor (DMMA) kernel
+  int nwtiles = 0;
+  FpVariant fv[kNumVariants];
   // tensor-core form (precision != FP64)
   void* tc = nullptr;
   long long tc_gen = -1;
+  std::map<int, Tune> tune;         // key: precision * 64 + nvec
+  std::map<int, GraphSlot> graphs;  // same key
 };
 
 class CudaBackend : public Backend {
@@ -75,6 +110,15 @@ class CudaBackend : public Backend {
     return (it != lists_.end() && it->second.gen == tl.gen && it->second.tasks) ? &it->second : nullptr;
   }
   void drop(const TaskList& tl);
+  // CUDA graphs for persistent work lists (on by default; TNS_GRAPHS=0 turns
+  // them off)
+  bool use_graphs = true;
+  // online schedule autotuning (on by default; TNS_AUTOTUNE=0 keeps the
+  // default variant, which makes repeated runs bitwise reproducible)
+  bool autotune = true;
+  // launches of the FP64 product kernels of variant v (no allocation, no
+  // synchronisation: capturable)
+  void enqueue_fp64(const DevList& d, int v, const double* xv, double* yv, int nvec, long long xs, long long ys);
   // scratch device memory owned by the backend (grows, never shrinks)
   void* scratch(size_t bytes, int slot);
   // counted launches of the engine's own kernels
@@ -88,16 +132,28 @@ class CudaBackend : public Backend {
   std::string err_;
   std::map<const TaskList*, DevList> lists_;
   std::vector<std::pair<void*, size_t>> scratch_ = std::vector<std::pair<void*, size_t>>(8, {nullptr, 0});
+  cudaStream_t gstream_ = nullptr;  // side stream for graph capture and replay
+  cudaEvent_t gev_[2] = {nullptr, nullptr};
   void upload_list(const TaskList& tl, DevList& d);
+  void plan_variant(const TaskList& tl, DevList& d, int v);
+  bool ensure_part(FpVariant& f, int nvec);
   void free_list(DevList& d);
+  void free_graphs(DevList& d);
+  template <class F>
+  void launch_graphed(DevList& d, int key, const double* xv, double* yv, int nvec, long long xs, long long ys,
+                      F&& enqueue);
 };
 
 // allocation-free H_eff diagonal (noalloc.cu)
 int heff_diag_noalloc(CudaBackend& be, Step& st, double* diag, std::string& err);
 
-// tensor-core form (tc.cu)
-void launch_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, const double* xv, double* yv, int nvec,
-                     long long xs, long long ys, int precision);
+// tensor-core form (tc.cu): prepare (plan, allocations; not capturable),
+// enqueue (kernel launches only; capturable), check (reads the timeout flag,
+// synchronises)
+bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec, int variant, int precision);
+void enqueue_tasks_tc(CudaBackend& be, DevList& d, const double* xv, double* yv, int nvec, long long xs,
+                      long long ys, int precision, int variant);
+void check_tasks_tc(CudaBackend& be, DevList& d);
 void release_tc_plan(void* plan);
 
 // kernels used by the solver (defined in kernels.cu)

@@ -180,6 +180,77 @@ double Engine::W(int p, int q, int r, int s) const {
   return v_[(((long long)(p >> 1) * N + (s >> 1)) * N + (q >> 1)) * N + (r >> 1)];
 }
 
+template <>
+double Engine::tc<double>(int p, int q) const {
+  return t(p, q);
+}
+template <>
+Lin Engine::tc<Lin>(int p, int q) const {
+  if ((p & 1) != (q & 1)) return Lin(0.0);
+  const long long idx = (long long)(p >> 1) * N_ + (q >> 1);
+  return Lin::var(h_[idx], idx);
+}
+template <>
+double Engine::Wc<double>(int p, int q, int r, int s) const {
+  return W(p, q, r, s);
+}
+template <>
+Lin Engine::Wc<Lin>(int p, int q, int r, int s) const {
+  if ((p & 1) != (s & 1) || (q & 1) != (r & 1)) return Lin(0.0);
+  const long long N = N_;
+  const long long idx = (((long long)(p >> 1) * N + (s >> 1)) * N + (q >> 1)) * N + (r >> 1);
+  return Lin::var(v_[idx], N * N + idx);
+}
+
+// ---------------------------------------------------------------------------
+// tracked scalars
+// ---------------------------------------------------------------------------
+void Lin::compact() {
+  if (c.size() < 2) return;
+  std::sort(c.begin(), c.end(), [](const std::pair<long long, double>& a, const std::pair<long long, double>& b) {
+    return a.first < b.first;
+  });
+  size_t w = 0;
+  for (size_t i = 0; i < c.size(); ++i) {
+    if (w > 0 && c[w - 1].first == c[i].first)
+      c[w - 1].second += c[i].second;
+    else
+      c[w++] = c[i];
+  }
+  c.resize(w);
+}
+
+Lin operator+(const Lin& a, const Lin& b) {
+  Lin r;
+  r.v = a.v + b.v;
+  r.c.reserve(a.c.size() + b.c.size());
+  r.c = a.c;
+  r.c.insert(r.c.end(), b.c.begin(), b.c.end());
+  if (r.c.size() > 64) r.compact();
+  return r;
+}
+Lin operator-(const Lin& a) {
+  Lin r = a;
+  r.v = -r.v;
+  for (auto& x : r.c) x.second = -x.second;
+  return r;
+}
+Lin operator-(const Lin& a, const Lin& b) { return a + (-b); }
+Lin operator*(double s, const Lin& a) {
+  Lin r = a;
+  r.v *= s;
+  for (auto& x : r.c) x.second *= s;
+  return r;
+}
+Lin operator*(const Lin& a, const Lin& b) {
+  if (a.is_const()) return a.v * b;
+  if (b.is_const()) return b.v * a;
+  // a product of two integral-dependent coefficients cannot occur in a
+  // Hamiltonian linear in the integrals; flag it with a NaN value
+  Lin r(std::nan(""));
+  return r;
+}
+
 int Engine::load_integrals(int N, const double* h, const double* v, double e_core, std::string& err) {
   if (N < 2 || N > 128 || !h || !v) {
     err = "load_integrals: need 2 <= N <= 128 and non-null h, v";
@@ -521,13 +592,14 @@ void Engine::empty_right(Catalogue& c) {
 // expressions and enlarged operators
 // ---------------------------------------------------------------------------
 namespace {
+template <class Sc>
 struct Builder {
-  Side& S;
+  SideT<Sc>& S;
   const Catalogue& cat;
   std::map<std::tuple<int, int, int>, int> refs;  // (op, tr, par) -> expr
-  Builder(Side& s, const Catalogue& c) : S(s), cat(c) {}
+  Builder(SideT<Sc>& s, const Catalogue& c) : S(s), cat(c) {}
 
-  QN term_dq(const Term& t) const {
+  QN term_dq(const TermT<Sc>& t) const {
     if (t.op < 0) return {0, 0};
     QN d = cat.ops[t.op].dq;
     return t.tr ? -d : d;
@@ -536,8 +608,8 @@ struct Builder {
     auto key = std::make_tuple(op, (int)tr, par);
     auto it = refs.find(key);
     if (it != refs.end()) return it->second;
-    Expr e;
-    e.t.push_back({1.0, op, tr, par});
+    ExprT<Sc> e;
+    e.t.push_back({Sc(1.0), op, tr, par});
     e.dq = term_dq(e.t[0]);
     S.exprs.push_back(e);
     int id = (int)S.exprs.size() - 1;
@@ -546,8 +618,8 @@ struct Builder {
   }
   int ident(int par = 0) { return ref(-1, false, par); }
   // linear combination; returns -1 if all coefficients vanish
-  int comb(const std::vector<Term>& ts) {
-    Expr e;
+  int comb(const std::vector<TermT<Sc>>& ts) {
+    ExprT<Sc> e;
     for (auto& t : ts)
       if (t.c != 0.0) e.t.push_back(t);
     if (e.t.empty()) return -1;
@@ -564,14 +636,17 @@ QN dot_shift(const M4& y) {
   return {0, 0};
 }
 
-void add_part(EOp& E, const M4& y, int expr) {
-  if (expr < 0 || y.zero()) return;
-  E.parts.push_back({y, expr});
+template <class Sc, class Y>
+void add_part(EOpT<Sc>& E, const Y& y, int expr) {
+  M4T<Sc> yy(y);
+  if (expr < 0 || yy.zero()) return;
+  E.parts.push_back({yy, expr});
 }
 }  // namespace
 
-static EOp& new_eop(Side& S, int kind, int i, int j) {
-  EOp E;
+template <class Sc>
+static EOpT<Sc>& new_eop(SideT<Sc>& S, int kind, int i, int j) {
+  EOpT<Sc> E;
   E.kind = kind;
   E.i = i;
   E.j = j;
@@ -582,9 +657,10 @@ static EOp& new_eop(Side& S, int kind, int i, int j) {
 
 // LL = L (x) dot `site`; L holds orbitals 0..site-1.  Operators of LL are the
 // catalogue of the left block of orbitals 0..site.
-void Engine::build_left_eops(const Catalogue& L, int site, Side& S) {
+template <class Sc>
+void Engine::build_left_eops(const Catalogue& L, int site, SideT<Sc>& S) {
   const DotOps& d = dot();
-  Builder B(S, L);
+  Builder<Sc> B(S, L);
   const int m0 = 2 * site, m1 = 2 * site + 1;
   const int ms[2] = {m0, m1};
   const int M = 2 * N_;
@@ -593,28 +669,28 @@ void Engine::build_left_eops(const Catalogue& L, int site, Side& S) {
   auto op = [&](int kind, int i, int j) { return L.find(kind, i, j); };
 
   // site Hamiltonian (one- and two-body terms on the dot)
-  M4 hs;
+  M4T<Sc> hs;
   for (int p : ms)
-    for (int q : ms) hs = hs + (d.cd[p & 1] * d.c[q & 1]).scale(t(p, q));
+    for (int q : ms) hs = hs + (d.cd[p & 1] * d.c[q & 1]).scale(tc<Sc>(p, q));
   for (int p : ms)
     for (int q : ms)
       for (int r : ms)
         for (int s : ms) {
-          double w = W(p, q, r, s);
+          Sc w = Wc<Sc>(p, q, r, s);
           if (w != 0.0) hs = hs + (d.cd[p & 1] * d.cd[q & 1] * d.c[r & 1] * d.c[s & 1]).scale(0.5 * w);
         }
 
   {  // H
-    EOp& E = new_eop(S, K_H, -1, -1);
+    EOpT<Sc>& E = new_eop(S, K_H, -1, -1);
     add_part(E, d.I, B.ref(op(K_H, -1, -1)));
     add_part(E, hs, B.ident());
     for (int a : inL) {
-      M4 Sa;
+      M4T<Sc> Sa;
       for (int q : ms) {
-        Sa = Sa + d.c[q & 1].scale(t(a, q));
+        Sa = Sa + d.c[q & 1].scale(tc<Sc>(a, q));
         for (int r : ms)
           for (int u : ms) {
-            double w = W(a, q, r, u);
+            Sc w = Wc<Sc>(a, q, r, u);
             if (w != 0.0) Sa = Sa + (d.cd[q & 1] * d.c[r & 1] * d.c[u & 1]).scale(w);
           }
       }
@@ -630,10 +706,10 @@ void Engine::build_left_eops(const Catalogue& L, int site, Side& S) {
     for (size_t ai = 0; ai < inL.size(); ++ai)
       for (size_t bi = ai + 1; bi < inL.size(); ++bi) {
         int a = inL[ai], b = inL[bi];
-        M4 Pp;
+        M4T<Sc> Pp;
         for (int r : ms)
           for (int u : ms) {
-            double w = W(a, b, r, u);
+            Sc w = Wc<Sc>(a, b, r, u);
             if (w != 0.0) Pp = Pp + (d.c[r & 1] * d.c[u & 1]).scale(w);
           }
         int Aab = op(K_A, a, b);
@@ -642,10 +718,10 @@ void Engine::build_left_eops(const Catalogue& L, int site, Side& S) {
       }
     for (int a : inL)
       for (int b : inL) {
-        M4 Q;
+        M4T<Sc> Q;
         for (int q : ms)
           for (int r : ms) {
-            double w = W(a, q, r, b) - W(a, q, b, r);
+            Sc w = Wc<Sc>(a, q, r, b) - Wc<Sc>(a, q, b, r);
             if (w != 0.0) Q = Q + (d.cd[q & 1] * d.c[r & 1]).scale(w);
           }
         add_part(E, Q, B.ref(op(K_B, a, b)));
@@ -673,42 +749,42 @@ void Engine::build_left_eops(const Catalogue& L, int site, Side& S) {
     for (int n : ms) add_part(new_eop(S, K_B, m, n), d.cd[m & 1] * d.c[n & 1], B.ident());
   // T_x for x right of LL
   for (int x = 2 * site + 2; x < M; ++x) {
-    EOp& E = new_eop(S, K_T, x, -1);
+    EOpT<Sc>& E = new_eop(S, K_T, x, -1);
     add_part(E, d.I, B.ref(op(K_T, x, -1)));
     for (int m : ms) {
-      std::vector<Term> bs, as;
+      std::vector<TermT<Sc>> bs, as;
       for (int q : inL)
         for (int r : inL) {
-          double w = W(m, q, r, x) - W(q, m, r, x);
+          Sc w = Wc<Sc>(m, q, r, x) - Wc<Sc>(q, m, r, x);
           if (w != 0.0) bs.push_back({w, op(K_B, q, r), false, 1});
         }
       for (size_t pi = 0; pi < inL.size(); ++pi)
         for (size_t qi = pi + 1; qi < inL.size(); ++qi) {
           int p = inL[pi], q = inL[qi];
-          double w = W(p, q, m, x) - W(q, p, m, x);
+          Sc w = Wc<Sc>(p, q, m, x) - Wc<Sc>(q, p, m, x);
           if (w != 0.0) as.push_back({w, op(K_A, p, q), false, 1});
         }
       add_part(E, d.cd[m & 1], B.comb(bs));
       add_part(E, d.c[m & 1], B.comb(as));
     }
     for (int a : inL) {
-      M4 y1, y2;
+      M4T<Sc> y1, y2;
       for (int p : ms)
         for (int q : ms) {
-          double w1 = W(p, q, a, x);
+          Sc w1 = Wc<Sc>(p, q, a, x);
           if (w1 != 0.0) y1 = y1 + (d.cd[p & 1] * d.cd[q & 1]).scale(w1);
-          double w2 = W(a, p, q, x) - W(p, a, q, x);
+          Sc w2 = Wc<Sc>(a, p, q, x) - Wc<Sc>(p, a, q, x);
           if (w2 != 0.0) y2 = y2 + (d.cd[p & 1] * d.c[q & 1]).scale(w2);
         }
       int ca = op(K_C, a, -1);
       add_part(E, y1, B.ref(ca, true));
       add_part(E, y2, B.ref(ca));
     }
-    M4 y3;
+    M4T<Sc> y3;
     for (int p : ms)
       for (int q : ms)
         for (int r : ms) {
-          double w = W(p, q, r, x);
+          Sc w = Wc<Sc>(p, q, r, x);
           if (w != 0.0) y3 = y3 + (d.cd[p & 1] * d.cd[q & 1] * d.c[r & 1]).scale(w);
         }
     add_part(E, y3, B.ident(1));
@@ -717,9 +793,10 @@ void Engine::build_left_eops(const Catalogue& L, int site, Side& S) {
 
 // RR = dot `site` (x) R; R holds orbitals site+1..N-1.  Operators of RR are
 // the catalogue of the right block of orbitals site..N-1.
-void Engine::build_right_eops(const Catalogue& R, int site, Side& S) {
+template <class Sc>
+void Engine::build_right_eops(const Catalogue& R, int site, SideT<Sc>& S) {
   const DotOps& d = dot();
-  Builder B(S, R);
+  Builder<Sc> B(S, R);
   const int m0 = 2 * site, m1 = 2 * site + 1;
   const int ms[2] = {m0, m1};
   const int M = 2 * N_;
@@ -728,18 +805,18 @@ void Engine::build_right_eops(const Catalogue& R, int site, Side& S) {
   auto op = [&](int kind, int i, int j) { return R.find(kind, i, j); };
   const M4& P4 = d.P;
 
-  M4 hs;
+  M4T<Sc> hs;
   for (int p : ms)
-    for (int q : ms) hs = hs + (d.cd[p & 1] * d.c[q & 1]).scale(t(p, q));
+    for (int q : ms) hs = hs + (d.cd[p & 1] * d.c[q & 1]).scale(tc<Sc>(p, q));
   for (int p : ms)
     for (int q : ms)
       for (int r : ms)
         for (int s : ms) {
-          double w = W(p, q, r, s);
+          Sc w = Wc<Sc>(p, q, r, s);
           if (w != 0.0) hs = hs + (d.cd[p & 1] * d.cd[q & 1] * d.c[r & 1] * d.c[s & 1]).scale(0.5 * w);
         }
   {  // H
-    EOp& E = new_eop(S, K_H, -1, -1);
+    EOpT<Sc>& E = new_eop(S, K_H, -1, -1);
     add_part(E, hs, B.ident());
     add_part(E, d.I, B.ref(op(K_H, -1, -1)));
     for (int m : ms) {
@@ -748,11 +825,11 @@ void Engine::build_right_eops(const Catalogue& R, int site, Side& S) {
       add_part(E, (d.c[m & 1] * P4).scale(-1.0), B.ref(Sm, true));
     }
     for (int x : inR) {
-      M4 Ts;
+      M4T<Sc> Ts;
       for (int p : ms)
         for (int q : ms)
           for (int r : ms) {
-            double w = W(p, q, r, x);
+            Sc w = Wc<Sc>(p, q, r, x);
             if (w != 0.0) Ts = Ts + (d.cd[p & 1] * d.cd[q & 1] * d.c[r & 1]).scale(w);
           }
       int cx = op(K_C, x, -1);
@@ -770,31 +847,31 @@ void Engine::build_right_eops(const Catalogue& R, int site, Side& S) {
   for (int x : inR) add_part(new_eop(S, K_C, x, -1), P4, B.ref(op(K_C, x, -1)));
   // S_a
   for (int a = 0; a < 2 * site; ++a) {
-    EOp& E = new_eop(S, K_S, a, -1);
+    EOpT<Sc>& E = new_eop(S, K_S, a, -1);
     add_part(E, P4, B.ref(op(K_S, a, -1)));
     for (int m : ms) {
       add_part(E, d.cd[m & 1], B.ref(op(K_P, a, m)));
       add_part(E, d.c[m & 1], B.ref(op(K_Q, a, m)));
-      if (t(a, m) != 0.0) add_part(E, d.c[m & 1].scale(t(a, m)), B.ident());
+      if (tc<Sc>(a, m) != 0.0) add_part(E, d.c[m & 1].scale(tc<Sc>(a, m)), B.ident());
     }
     for (int x : inR) {
-      M4 y1, y3;
+      M4T<Sc> y1, y3;
       for (int q : ms)
         for (int r : ms) {
-          double w1 = W(a, q, r, x) - W(a, q, x, r);
+          Sc w1 = Wc<Sc>(a, q, r, x) - Wc<Sc>(a, q, x, r);
           if (w1 != 0.0) y1 = y1 + (d.cd[q & 1] * d.c[r & 1]).scale(w1);
-          double w3 = W(a, x, q, r);
+          Sc w3 = Wc<Sc>(a, x, q, r);
           if (w3 != 0.0) y3 = y3 + (d.c[q & 1] * d.c[r & 1]).scale(w3);
         }
       int cx = op(K_C, x, -1);
       add_part(E, y1 * P4, B.ref(cx, true));
       add_part(E, y3 * P4, B.ref(cx));
     }
-    M4 y;
+    M4T<Sc> y;
     for (int q : ms)
       for (int r : ms)
         for (int u : ms) {
-          double w = W(a, q, r, u);
+          Sc w = Wc<Sc>(a, q, r, u);
           if (w != 0.0) y = y + (d.cd[q & 1] * d.c[r & 1] * d.c[u & 1]).scale(w);
         }
     add_part(E, y, B.ident());
@@ -803,13 +880,13 @@ void Engine::build_right_eops(const Catalogue& R, int site, Side& S) {
   for (int a = 0; a < 2 * site; ++a)
     for (int b = 0; b < 2 * site; ++b) {
       {
-        EOp& E = new_eop(S, K_Q, a, b);
+        EOpT<Sc>& E = new_eop(S, K_Q, a, b);
         add_part(E, d.I, B.ref(op(K_Q, a, b)));
         for (int m : ms) {
-          std::vector<Term> cqr, crq;
+          std::vector<TermT<Sc>> cqr, crq;
           for (int x : inR) {
-            double w1 = W(a, m, x, b) - W(a, m, b, x);  // c+_m c_x
-            double w2 = W(a, x, m, b) - W(a, x, b, m);  // c+_x c_m
+            Sc w1 = Wc<Sc>(a, m, x, b) - Wc<Sc>(a, m, b, x);  // c+_m c_x
+            Sc w2 = Wc<Sc>(a, x, m, b) - Wc<Sc>(a, x, b, m);  // c+_x c_m
             int cx = op(K_C, x, -1);
             if (w1 != 0.0) cqr.push_back({w1, cx, true, 0});
             if (w2 != 0.0) crq.push_back({w2, cx, false, 0});
@@ -817,29 +894,29 @@ void Engine::build_right_eops(const Catalogue& R, int site, Side& S) {
           add_part(E, d.cd[m & 1] * P4, B.comb(cqr));
           add_part(E, (d.c[m & 1] * P4).scale(-1.0), B.comb(crq));
         }
-        M4 y;
+        M4T<Sc> y;
         for (int q : ms)
           for (int r : ms) {
-            double w = W(a, q, r, b) - W(a, q, b, r);
+            Sc w = Wc<Sc>(a, q, r, b) - Wc<Sc>(a, q, b, r);
             if (w != 0.0) y = y + (d.cd[q & 1] * d.c[r & 1]).scale(w);
           }
         add_part(E, y, B.ident());
       }
       if (a < b) {
-        EOp& E = new_eop(S, K_P, a, b);
+        EOpT<Sc>& E = new_eop(S, K_P, a, b);
         add_part(E, d.I, B.ref(op(K_P, a, b)));
         for (int m : ms) {
-          std::vector<Term> cf;
+          std::vector<TermT<Sc>> cf;
           for (int x : inR) {
-            double w = W(a, b, m, x) - W(a, b, x, m);
+            Sc w = Wc<Sc>(a, b, m, x) - Wc<Sc>(a, b, x, m);
             if (w != 0.0) cf.push_back({w, op(K_C, x, -1), true, 0});
           }
           add_part(E, d.c[m & 1] * P4, B.comb(cf));
         }
-        M4 y;
+        M4T<Sc> y;
         for (int r : ms)
           for (int u : ms) {
-            double w = W(a, b, r, u);
+            Sc w = Wc<Sc>(a, b, r, u);
             if (w != 0.0) y = y + (d.c[r & 1] * d.c[u & 1]).scale(w);
           }
         add_part(E, y, B.ident());
@@ -849,20 +926,21 @@ void Engine::build_right_eops(const Catalogue& R, int site, Side& S) {
 
 // dot blocks of every enlarged operator; dot blocks with more than two
 // expressions become one materialised expression (partial summation)
-void Engine::compile_side(Side& S, const Catalogue& cat, bool left) {
+template <class Sc>
+void Engine::compile_side(SideT<Sc>& S, const Catalogue& cat, bool left) {
   (void)left;
-  Builder B(S, cat);
+  Builder<Sc> B(S, cat);
   for (auto& E : S.eops) {
     E.dots.clear();
     E.dq = {0, 0};
     bool have_dq = false;
     for (int so = 0; so < 4; ++so)
       for (int si = 0; si < 4; ++si) {
-        DotBlock db;
+        DotBlockT<Sc> db;
         db.so = so;
         db.si = si;
         for (auto& pr : E.parts) {
-          double y = pr.first.a[so][si];
+          Sc y = pr.first.a[so][si];
           if (y == 0.0) continue;
           bool merged = false;
           for (auto& dt : db.t)
@@ -872,19 +950,19 @@ void Engine::compile_side(Side& S, const Catalogue& cat, bool left) {
             }
           if (!merged) db.t.push_back({y, pr.second});
         }
-        std::vector<DotTerm> keep;
+        std::vector<DotTermT<Sc>> keep;
         for (auto& dt : db.t)
           if (dt.s != 0.0) keep.push_back(dt);
         db.t = keep;
         if (db.t.empty()) continue;
         if (db.t.size() > 2) {
-          std::vector<Term> ts;
+          std::vector<TermT<Sc>> ts;
           for (auto& dt : db.t)
             for (auto& tm : S.exprs[dt.expr].t) ts.push_back({dt.s * tm.c, tm.op, tm.tr, tm.par});
           int e = B.comb(ts);
           db.t.clear();
           if (e < 0) continue;
-          db.t.push_back({1.0, e});
+          db.t.push_back({Sc(1.0), e});
         }
         QN dq = S.exprs[db.t[0].expr].dq + kSiteQN[so] - kSiteQN[si];
         if (!have_dq) {
@@ -1667,4 +1745,13 @@ int Engine::heff_adjoint(const double* X, const double* Yb, double* Xb, double* 
   return 0;
 }
 
+}  // namespace tns
+
+namespace tns {
+template void Engine::build_left_eops<double>(const Catalogue&, int, SideT<double>&);
+template void Engine::build_left_eops<Lin>(const Catalogue&, int, SideT<Lin>&);
+template void Engine::build_right_eops<double>(const Catalogue&, int, SideT<double>&);
+template void Engine::build_right_eops<Lin>(const Catalogue&, int, SideT<Lin>&);
+template void Engine::compile_side<double>(SideT<double>&, const Catalogue&, bool);
+template void Engine::compile_side<Lin>(SideT<Lin>&, const Catalogue&, bool);
 }  // namespace tns

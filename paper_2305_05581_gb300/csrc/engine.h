@@ -110,39 +110,82 @@ struct Catalogue {
   void assign_offsets();
 };
 
-struct M4 {
-  double a[4][4];
-  M4() {
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) a[i][j] = 0.0;
+// Scalar that carries, besides its value, its (sparse) derivative with
+// respect to the integrals theta = (h_ij, v_ijkl) as independent entries:
+// index i*N+j for h_ij and N^2 + ((i*N+j)*N+k)*N+l for v_ijkl.  Every
+// coefficient of the operator construction is linear in theta, so running
+// the same construction with this type records where each coefficient comes
+// from (used by the integral gradients of the differentiation form).
+struct Lin {
+  double v = 0.0;
+  std::vector<std::pair<long long, double>> c;
+  Lin() = default;
+  Lin(double x) : v(x) {}
+  static Lin var(double x, long long idx) {
+    Lin r(x);
+    r.c.push_back({idx, 1.0});
+    return r;
   }
-  static M4 eye() {
-    M4 m;
-    for (int i = 0; i < 4; ++i) m.a[i][i] = 1.0;
+  bool is_const() const { return c.empty(); }
+  void compact();
+};
+Lin operator+(const Lin& a, const Lin& b);
+Lin operator-(const Lin& a);
+Lin operator-(const Lin& a, const Lin& b);
+Lin operator*(double s, const Lin& a);
+inline Lin operator*(const Lin& a, double s) { return s * a; }
+Lin operator*(const Lin& a, const Lin& b);  // one factor must be constant
+inline Lin& operator+=(Lin& a, const Lin& b) { return a = a + b; }
+inline bool operator==(const Lin& a, double x) { return a.v == x; }
+inline bool operator!=(const Lin& a, double x) { return a.v != x; }
+inline double value(double x) { return x; }
+inline double value(const Lin& x) { return x.v; }
+
+template <class S>
+struct M4T {
+  S a[4][4];
+  M4T() {
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) a[i][j] = S(0.0);
+  }
+  template <class S2>
+  explicit M4T(const M4T<S2>& o) {
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) a[i][j] = S(o.a[i][j]);
+  }
+  static M4T eye() {
+    M4T m;
+    for (int i = 0; i < 4; ++i) m.a[i][i] = S(1.0);
     return m;
   }
-  M4 operator*(const M4& b) const {
-    M4 r;
+  // product with a plain (or same-type) 4x4 on the right
+  template <class S2>
+  M4T operator*(const M4T<S2>& b) const {
+    M4T r;
     for (int i = 0; i < 4; ++i)
       for (int k = 0; k < 4; ++k)
         if (a[i][k] != 0.0)
-          for (int j = 0; j < 4; ++j) r.a[i][j] += a[i][k] * b.a[k][j];
+          for (int j = 0; j < 4; ++j)
+            if (b.a[k][j] != 0.0) r.a[i][j] += a[i][k] * b.a[k][j];
     return r;
   }
-  M4 operator+(const M4& b) const {
-    M4 r;
+  M4T operator+(const M4T& b) const {
+    M4T r;
     for (int i = 0; i < 4; ++i)
       for (int j = 0; j < 4; ++j) r.a[i][j] = a[i][j] + b.a[i][j];
     return r;
   }
-  M4 scale(double c) const {
-    M4 r;
+  // c * this, c a plain or a tracked scalar
+  template <class C>
+  auto scale(const C& c) const -> M4T<decltype(c * a[0][0])> {
+    M4T<decltype(c * a[0][0])> r;
     for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) r.a[i][j] = c * a[i][j];
+      for (int j = 0; j < 4; ++j)
+        if (a[i][j] != 0.0) r.a[i][j] = c * a[i][j];
     return r;
   }
-  M4 T() const {
-    M4 r;
+  M4T T() const {
+    M4T r;
     for (int i = 0; i < 4; ++i)
       for (int j = 0; j < 4; ++j) r.a[i][j] = a[j][i];
     return r;
@@ -154,37 +197,48 @@ struct M4 {
     return true;
   }
 };
+using M4 = M4T<double>;
 
 // one term of an expression: c * op^(T) * P^(par)
 //   op = -1: identity; par: 0 none, 1 parity of the in-sector, 2 of the out-sector
-struct Term {
-  double c;
+template <class S>
+struct TermT {
+  S c;
   int op;
   bool tr;
   int par;
 };
+using Term = TermT<double>;
 
-struct Expr {
-  std::vector<Term> t;
+template <class S>
+struct ExprT {
+  std::vector<TermT<S>> t;
   QN dq;          // shift of the expression (in -> in + dq)
   int mat = -1;   // materialised: index into Step::mats
 };
+using Expr = ExprT<double>;
 
 // enlarged operator = sum_parts (expr (x) y) ; dot blocks compiled from it
-struct DotTerm {
-  double s;
+template <class S>
+struct DotTermT {
+  S s;
   int expr;
 };
-struct DotBlock {
+using DotTerm = DotTermT<double>;
+template <class S>
+struct DotBlockT {
   int so, si;
-  std::vector<DotTerm> t;
+  std::vector<DotTermT<S>> t;
 };
-struct EOp {
+using DotBlock = DotBlockT<double>;
+template <class S>
+struct EOpT {
   int kind, i, j;   // catalogue key of the enlarged block this operator belongs to
   QN dq;            // total shift (expr dq + dot shift)
-  std::vector<std::pair<M4, int>> parts;  // (dot operator, expr id)
-  std::vector<DotBlock> dots;
+  std::vector<std::pair<M4T<S>, int>> parts;  // (dot operator, expr id)
+  std::vector<DotBlockT<S>> dots;
 };
+using EOp = EOpT<double>;
 
 // a materialised expression: its own operator on the block basis
 struct Mat {
@@ -286,14 +340,16 @@ struct Site {
 // ---------------------------------------------------------------------------
 // per two-site step state
 // ---------------------------------------------------------------------------
-struct Side {  // enlarged operators of one side for a step
-  std::vector<Expr> exprs;
-  std::vector<EOp> eops;
+template <class S>
+struct SideT {  // enlarged operators of one side for a step
+  std::vector<ExprT<S>> exprs;
+  std::vector<EOpT<S>> eops;
   std::map<long long, int> eop_index;  // catalogue key -> eop
   std::vector<Mat> mats;
   double* d = nullptr;  // materialised arena
   long long size = 0;
 };
+using Side = SideT<double>;
 
 struct PsiBlock {
   int ql, s1, s2, qr;  // ql: bond-k sector index; qr: index in the right block basis
@@ -368,6 +424,11 @@ class Engine {
   // integrals
   double t(int p, int q) const;
   double W(int p, int q, int r, int s) const;
+  // the same integrals as plain (double) or tracked (Lin) scalars
+  template <class Sc>
+  Sc tc(int p, int q) const;
+  template <class Sc>
+  Sc Wc(int p, int q, int r, int s) const;
 
  private:
   Backend* be_;
@@ -389,9 +450,12 @@ class Engine {
   int alloc_cat(Catalogue& c, std::string& err);
   void empty_left(Catalogue& c);
   void empty_right(Catalogue& c);
-  void build_left_eops(const Catalogue& L, int site, Side& S);
-  void build_right_eops(const Catalogue& R, int site, Side& S);
-  void compile_side(Side& S, const Catalogue& cat, bool left);
+  template <class Sc>
+  void build_left_eops(const Catalogue& L, int site, SideT<Sc>& S);
+  template <class Sc>
+  void build_right_eops(const Catalogue& R, int site, SideT<Sc>& S);
+  template <class Sc>
+  void compile_side(SideT<Sc>& S, const Catalogue& cat, bool left);
   int materialize(Side& S, Catalogue& cat, std::string& err);
   int rotate(Side& S, const Catalogue& src, Catalogue& dst, int site, bool left, std::string& err);
   void build_psi(int k);

@@ -491,16 +491,15 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int nb, in
 
 void launch_multidot(CudaBackend& be, const double* V, long long ldv, int k, const double* w, long long n,
                      double* out) {
-  if (k <= 0) return;
-  if (k > MAXK) {
-    be.note(cudaErrorInvalidValue, "multidot: too many vectors");
-    return;
-  }
+  // in chunks of at most MAXK vectors (the kernel keeps one accumulator per vector)
   double* partial = (double*)be.scratch(sizeof(double) * MAXK * RED_BLOCKS, 0);
-  k_multidot<<<RED_BLOCKS, RED_NT, 0, be.stream()>>>(V, ldv, k, w, n, partial);
-  k_reduce_partials<<<k, 32, 0, be.stream()>>>(partial, RED_BLOCKS, k, out);
-  be.launches += 2;
-  be.note(cudaGetLastError(), "multidot");
+  for (int i0 = 0; i0 < k; i0 += MAXK) {
+    const int kc = std::min(MAXK, k - i0);
+    k_multidot<<<RED_BLOCKS, RED_NT, 0, be.stream()>>>(V + (long long)i0 * ldv, ldv, kc, w, n, partial);
+    k_reduce_partials<<<kc, 32, 0, be.stream()>>>(partial, RED_BLOCKS, kc, out + i0);
+    be.launches += 2;
+    be.note(cudaGetLastError(), "multidot");
+  }
 }
 
 // w += sign * sum_i coef[i] V_i
@@ -518,10 +517,12 @@ __global__ void k_axpy_multi(const double* __restrict__ V, long long ldv, int k,
 
 void launch_axpy_multi(CudaBackend& be, const double* V, long long ldv, int k, const double* coef, double sign,
                        double* w, long long n) {
-  if (k <= 0) return;
-  k_axpy_multi<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(V, ldv, k, coef, sign, w, n);
-  be.launches++;
-  be.note(cudaGetLastError(), "axpy_multi");
+  for (int i0 = 0; i0 < k; i0 += MAXK) {
+    const int kc = std::min(MAXK, k - i0);
+    k_axpy_multi<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(V + (long long)i0 * ldv, ldv, kc, coef + i0, sign, w, n);
+    be.launches++;
+    be.note(cudaGetLastError(), "axpy_multi");
+  }
 }
 
 __global__ void k_combine(const double* __restrict__ V, long long ldv, int k, const double* __restrict__ coef,
@@ -538,9 +539,12 @@ __global__ void k_combine(const double* __restrict__ V, long long ldv, int k, co
 
 void launch_combine(CudaBackend& be, const double* V, long long ldv, int k, const double* coef, double* out,
                     long long n) {
-  k_combine<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(V, ldv, k, coef, out, n);
+  if (k <= 0) return;
+  const int kc = std::min(MAXK, k);
+  k_combine<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(V, ldv, kc, coef, out, n);
   be.launches++;
   be.note(cudaGetLastError(), "combine");
+  if (k > kc) launch_axpy_multi(be, V + (long long)kc * ldv, ldv, k - kc, coef + kc, 1.0, out, n);
 }
 
 // x *= f(num): inv_sqrt ? 1/sqrt(num) : num
@@ -845,6 +849,10 @@ void launch_gather(CudaBackend& be, const double* src, const long long* so, cons
 // backend
 // ---------------------------------------------------------------------------
 CudaBackend::CudaBackend(int device, cudaStream_t s, bool own) : device_(device), stream_(s), own_(own) {
+  const char* gr = std::getenv("TNS_GRAPHS");
+  if (gr && std::strcmp(gr, "0") == 0) use_graphs = false;
+  const char* at = std::getenv("TNS_AUTOTUNE");
+  if (at && std::strcmp(at, "0") == 0) autotune = false;
   const char* k = std::getenv("TNS_FP64_KERNEL");
   if (k && std::strcmp(k, "dfma") == 0) fp64_kernel = 0;
   if (k && std::strcmp(k, "dmma") == 0) fp64_kernel = 1;
@@ -854,6 +862,9 @@ CudaBackend::~CudaBackend() {
   for (auto& kv : lists_) free_list(kv.second);
   for (auto& s : scratch_)
     if (s.first) cudaFree(s.first);
+  if (gstream_) cudaStreamDestroy(gstream_);
+  for (cudaEvent_t e : gev_)
+    if (e) cudaEventDestroy(e);
   if (own_ && stream_) cudaStreamDestroy(stream_);
 }
 
@@ -929,14 +940,27 @@ static T* dev_copy(const std::vector<T>& v, CudaBackend& be) {
   return (T*)p;
 }
 
+void CudaBackend::free_graphs(DevList& d) {
+  for (auto& kv : d.graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.xbuf) cudaFree(kv.second.xbuf);
+    if (kv.second.ybuf) cudaFree(kv.second.ybuf);
+  }
+  d.graphs.clear();
+}
+
 void CudaBackend::free_list(DevList& d) {
   cudaStreamSynchronize(stream_);
+  if (gstream_) cudaStreamSynchronize(gstream_);
+  free_graphs(d);
   if (d.tasks) cudaFree(d.tasks);
   if (d.groups) cudaFree(d.groups);
-  if (d.tiles) cudaFree(d.tiles);
   if (d.wtiles) cudaFree(d.wtiles);
-  if (d.reds) cudaFree(d.reds);
-  if (d.part) cudaFree(d.part);
+  for (FpVariant& f : d.fv) {
+    if (f.tiles) cudaFree(f.tiles);
+    if (f.reds) cudaFree(f.reds);
+    if (f.part) cudaFree(f.part);
+  }
   if (d.tc) release_tc_plan(d.tc);
   d = DevList();
 }
@@ -951,10 +975,39 @@ static double task_cost(const Task& t) {
 
 void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
   free_list(d);
-  // tiles of at most 64 x 64, split into size classes; a tile whose task
-  // list is long is cut into pieces of similar cost (split-K), each written
-  // to a partial tile and summed afterwards in piece order, so that every
-  // class fills the GPU and no CTA walks a much longer list than the rest
+  d.tasks = dev_copy(tl.tasks, *this);
+  d.groups = dev_copy(tl.groups, *this);
+  std::vector<Tile> wt;
+  for (int g = 0; g < (int)tl.groups.size(); ++g) {
+    const Group& G = tl.groups[g];
+    for (int r0 = 0; r0 < G.q; r0 += DM_WR)
+      for (int c0 = 0; c0 < G.r; c0 += DM_WC) {
+        Tile t;
+        t.g = g;
+        t.row0 = r0;
+        t.col0 = c0;
+        t.nrows = std::min(DM_WR, G.q - r0);
+        t.ncols = std::min(DM_WC, G.r - c0);
+        t.t0 = G.t0;
+        t.t1 = G.t1;
+        t.poff = -1;
+        wt.push_back(t);
+      }
+  }
+  d.nwtiles = (int)wt.size();
+  d.wtiles = dev_copy(wt, *this);
+  d.gen = tl.gen;
+  note(cudaStreamSynchronize(stream_), "work list upload");
+}
+
+// schedule variant v of the FP64 kernels: tiles of at most 64 x 64 in size
+// classes; a tile whose task list is long is cut into pieces of similar cost
+// (split-K), each written to a partial tile and summed afterwards in piece
+// order, so that every class fills the GPU and no CTA walks a much longer
+// list than the rest
+void CudaBackend::plan_variant(const TaskList& tl, DevList& d, int v) {
+  FpVariant& f = d.fv[v];
+  if (f.planned) return;
   std::vector<Tile> cls[3];
   std::vector<double> cost[3];
   double ctot[3] = {0, 0, 0};
@@ -981,10 +1034,11 @@ void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
         ctot[c] += w;
       }
   }
-  // resident CTAs per SM of each class (registers) x SMs x 2 rounds
+  // resident CTAs per SM of each class (registers) x SMs x rounds
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device_);
-  const double slots[3] = {16.0 * sms * 2, 4.0 * sms * 2, 2.0 * sms * 2};
+  const double rounds = kRounds[v];
+  const double slots[3] = {16.0 * sms * rounds, 4.0 * sms * rounds, 2.0 * sms * rounds};
   std::vector<Tile> all;
   std::vector<SplitRed> reds;
   long long poff = 0;
@@ -1037,36 +1091,34 @@ void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
       R.nsplit = made + 1;
       reds.push_back(R);
     }
-    d.ncls[c] = count;
+    f.ncls[c] = count;
   }
-  d.psize = poff;
-  d.nreds = (int)reds.size();
-  d.reds = dev_copy(reds, *this);
-  d.ntiles = (int)all.size();
-  d.tasks = dev_copy(tl.tasks, *this);
-  d.groups = dev_copy(tl.groups, *this);
-  d.tiles = dev_copy(all, *this);
-  std::vector<Tile> wt;
-  for (int g = 0; g < (int)tl.groups.size(); ++g) {
-    const Group& G = tl.groups[g];
-    for (int r0 = 0; r0 < G.q; r0 += DM_WR)
-      for (int c0 = 0; c0 < G.r; c0 += DM_WC) {
-        Tile t;
-        t.g = g;
-        t.row0 = r0;
-        t.col0 = c0;
-        t.nrows = std::min(DM_WR, G.q - r0);
-        t.ncols = std::min(DM_WC, G.r - c0);
-        t.t0 = G.t0;
-        t.t1 = G.t1;
-        t.poff = -1;
-        wt.push_back(t);
-      }
+  f.psize = poff;
+  f.nreds = (int)reds.size();
+  f.reds = dev_copy(reds, *this);
+  f.ntiles = (int)all.size();
+  f.tiles = dev_copy(all, *this);
+  f.planned = true;
+  note(cudaStreamSynchronize(stream_), "schedule upload");
+}
+
+bool CudaBackend::ensure_part(FpVariant& f, int nvec) {
+  if (f.psize == 0 || f.part_nvec >= nvec) return true;
+  if (f.part) {
+    cudaStreamSynchronize(stream_);
+    if (gstream_) cudaStreamSynchronize(gstream_);
+    cudaFree(f.part);
   }
-  d.nwtiles = (int)wt.size();
-  d.wtiles = dev_copy(wt, *this);
-  d.gen = tl.gen;
-  note(cudaStreamSynchronize(stream_), "work list upload");
+  f.part = nullptr;
+  f.part_nvec = 0;
+  if (cudaMalloc(&f.part, sizeof(double) * f.psize * nvec) != cudaSuccess) {
+    cudaGetLastError();
+    note(cudaErrorMemoryAllocation, "split partial tiles");
+    f.part = nullptr;
+    return false;
+  }
+  f.part_nvec = nvec;
+  return true;
 }
 
 DevList& CudaBackend::dev(const TaskList& tl) {
@@ -1083,76 +1135,181 @@ void CudaBackend::drop(const TaskList& tl) {
   }
 }
 
-void launch_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, const double* xv, double* yv, int nvec,
-                     long long xs, long long ys, int precision);
+void CudaBackend::enqueue_fp64(const DevList& d, int v, const double* xv, double* yv, int nvec, long long xs,
+                               long long ys) {
+  const FpVariant& f = d.fv[v];
+  int t0 = 0;
+  for (int c = 0; c < 3; ++c) {
+    int n = f.ncls[c];
+    if (n == 0) continue;
+    dim3 grid(n, nvec);
+    if (c == 0)
+      k_tasks_fp64<C0_NT, C0_ACC, C0_TR, C0_TC><<<grid, C0_NT, 0, stream_>>>(d.tasks, d.groups, f.tiles, t0, xv, yv,
+                                                                             xs, ys, f.part, f.psize);
+    else if (c == 1)
+      k_tasks_fp64<C1_NT, C1_ACC, C1_TR, C1_TC><<<grid, C1_NT, 0, stream_>>>(d.tasks, d.groups, f.tiles, t0, xv, yv,
+                                                                             xs, ys, f.part, f.psize);
+    else
+      k_tasks_fp64<C2_NT, C2_ACC, C2_TR, C2_TC><<<grid, C2_NT, 0, stream_>>>(d.tasks, d.groups, f.tiles, t0, xv, yv,
+                                                                             xs, ys, f.part, f.psize);
+    launches++;
+    note(cudaGetLastError(), "k_tasks_fp64");
+    t0 += n;
+  }
+  if (f.nreds > 0) {
+    dim3 grid(std::min(f.nreds, 65535), nvec);
+    k_reduce_splits<<<grid, 128, 0, stream_>>>(f.reds, f.nreds, d.groups, f.part, f.psize, yv, ys);
+    launches++;
+    note(cudaGetLastError(), "k_reduce_splits");
+  }
+}
+
+// Replay (capturing it first if needed) the launch sequence `enqueue` of one
+// (precision, nvec) use of a persistent list as a CUDA graph on the side
+// stream, ordered after the context stream's prior work and before its next:
+// input copied into the graph's fixed buffer, output copied out.  Falls back
+// to direct launches where capture is not possible.
+template <class F>
+void CudaBackend::launch_graphed(DevList& d, int key, const double* xv, double* yv, int nvec, long long xs,
+                                 long long ys, F&& enqueue) {
+  GraphSlot& gs = d.graphs[key];
+  const long long elems = (long long)nvec * xs;
+  if (!use_graphs || gs.failed || xs != ys) {
+    enqueue(xv, yv);
+    return;
+  }
+  if (!gstream_) {
+    if (cudaStreamCreateWithFlags(&gstream_, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&gev_[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&gev_[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      gs.failed = true;
+      enqueue(xv, yv);
+      return;
+    }
+  }
+  if (!gs.exec) {
+    if (cudaMalloc(&gs.xbuf, sizeof(double) * elems) != cudaSuccess ||
+        cudaMalloc(&gs.ybuf, sizeof(double) * elems) != cudaSuccess) {
+      cudaGetLastError();
+      gs.failed = true;
+      enqueue(xv, yv);
+      return;
+    }
+    gs.elems = elems;
+    gs.stride = xs;
+    cudaStream_t saved = stream_;
+    stream_ = gstream_;
+    const long long l0 = launches;
+    const std::string saved_err = err_;
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(gstream_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      enqueue(gs.xbuf, gs.ybuf);
+      ok = cudaStreamEndCapture(gstream_, &g) == cudaSuccess && g;
+    }
+    stream_ = saved;
+    if (ok) ok = cudaGraphInstantiate(&gs.exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    gs.kernels = (int)(launches - l0);
+    launches = l0;
+    if (!ok) {
+      cudaGetLastError();
+      err_ = saved_err;
+      gs.failed = true;
+      gs.exec = nullptr;
+      enqueue(xv, yv);
+      return;
+    }
+  }
+  note(cudaEventRecord(gev_[0], stream_), "graph order");
+  note(cudaStreamWaitEvent(gstream_, gev_[0], 0), "graph order");
+  note(cudaMemcpyAsync(gs.xbuf, xv, sizeof(double) * elems, cudaMemcpyDeviceToDevice, gstream_), "graph input");
+  note(cudaGraphLaunch(gs.exec, gstream_), "graph launch");
+  note(cudaMemcpyAsync(yv, gs.ybuf, sizeof(double) * elems, cudaMemcpyDeviceToDevice, gstream_), "graph output");
+  note(cudaEventRecord(gev_[1], gstream_), "graph order");
+  note(cudaStreamWaitEvent(stream_, gev_[1], 0), "graph order");
+  launches += gs.kernels;
+}
 
 void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec, long long xs, long long ys,
                       int precision) {
   if (tl.groups.empty()) return;
-  DevList tmp;
-  DevList* d;
-  if (tl.persistent) {
-    d = &dev(tl);
-  } else {
+  if (!tl.persistent) {
+    // one-off list (rotations, truncation products): default schedule, direct launches
+    DevList tmp;
     upload_list(tl, tmp);
-    d = &tmp;
+    if (precision != 0) {
+      if (prepare_tasks_tc(*this, tl, tmp, nvec, 1, precision)) {
+        enqueue_tasks_tc(*this, tmp, xv, yv, nvec, xs, ys, precision, 1);
+        check_tasks_tc(*this, tmp);
+      }
+    } else if (fp64_kernel == 1) {
+      if (tmp.nwtiles > 0) {
+        dim3 grid((tmp.nwtiles + DM_WARPS - 1) / DM_WARPS, nvec);
+        k_tasks_dmma<<<grid, 32 * DM_WARPS, 0, stream_>>>(tmp.tasks, tmp.groups, tmp.wtiles, tmp.nwtiles, xv, yv, xs,
+                                                           ys);
+        launches++;
+        note(cudaGetLastError(), "k_tasks_dmma");
+      }
+    } else {
+      plan_variant(tl, tmp, 1);
+      if (ensure_part(tmp.fv[1], nvec)) enqueue_fp64(tmp, 1, xv, yv, nvec, xs, ys);
+    }
+    free_list(tmp);
+    return;
   }
-  if (!d->tiles) return;
-  if (precision != 0) {
-    launch_tasks_tc(*this, tl, *d, xv, yv, nvec, xs, ys, precision);
-  } else if (fp64_kernel == 1) {
-    if (d->nwtiles > 0) {
-      dim3 grid((d->nwtiles + DM_WARPS - 1) / DM_WARPS, nvec);
-      k_tasks_dmma<<<grid, 32 * DM_WARPS, 0, stream_>>>(d->tasks, d->groups, d->wtiles, d->nwtiles, xv, yv, xs, ys);
+  DevList& d = dev(tl);
+  if (precision == 0 && fp64_kernel == 1) {
+    if (d.nwtiles > 0) {
+      dim3 grid((d.nwtiles + DM_WARPS - 1) / DM_WARPS, nvec);
+      k_tasks_dmma<<<grid, 32 * DM_WARPS, 0, stream_>>>(d.tasks, d.groups, d.wtiles, d.nwtiles, xv, yv, xs, ys);
       launches++;
       note(cudaGetLastError(), "k_tasks_dmma");
     }
-  } else {
-    if (d->psize > 0 && d->part_nvec < nvec) {
-      if (d->part) {
-        cudaStreamSynchronize(stream_);
-        cudaFree(d->part);
-      }
-      d->part = nullptr;
-      d->part_nvec = 0;
-      if (cudaMalloc(&d->part, sizeof(double) * d->psize * nvec) != cudaSuccess) {
-        cudaGetLastError();
-        note(cudaErrorMemoryAllocation, "split partial tiles");
-        d->part = nullptr;
-      } else {
-        d->part_nvec = nvec;
-      }
-    }
-    if (d->psize > 0 && !d->part) {
-      if (!tl.persistent) free_list(tmp);
-      return;
-    }
-    int t0 = 0;
-    for (int c = 0; c < 3; ++c) {
-      int n = d->ncls[c];
-      if (n == 0) continue;
-      dim3 grid(n, nvec);
-      if (c == 0)
-        k_tasks_fp64<C0_NT, C0_ACC, C0_TR, C0_TC><<<grid, C0_NT, 0, stream_>>>(
-            d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys, d->part, d->psize);
-      else if (c == 1)
-        k_tasks_fp64<C1_NT, C1_ACC, C1_TR, C1_TC><<<grid, C1_NT, 0, stream_>>>(
-            d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys, d->part, d->psize);
-      else
-        k_tasks_fp64<C2_NT, C2_ACC, C2_TR, C2_TC><<<grid, C2_NT, 0, stream_>>>(
-            d->tasks, d->groups, d->tiles, t0, xv, yv, xs, ys, d->part, d->psize);
-      launches++;
-      note(cudaGetLastError(), "k_tasks_fp64");
-      t0 += n;
-    }
-    if (d->nreds > 0) {
-      dim3 grid(std::min(d->nreds, 65535), nvec);
-      k_reduce_splits<<<grid, 128, 0, stream_>>>(d->reds, d->nreds, d->groups, d->part, d->psize, yv, ys);
-      launches++;
-      note(cudaGetLastError(), "k_reduce_splits");
-    }
+    return;
   }
-  if (!tl.persistent) free_list(tmp);
+  // online autotuner: the first products of this (precision, nvec) use run
+  // one schedule variant each, timed with events; the fastest is kept
+  const int key = precision * 64 + nvec;
+  Tune& tu = d.tune[key];
+  if (!autotune && tu.best < 0) tu.best = 1;
+  const bool timing = tu.best < 0;
+  const int v = timing ? tu.next : tu.best;
+  if (precision != 0) {
+    if (!prepare_tasks_tc(*this, tl, d, nvec, v, precision)) return;
+  } else {
+    plan_variant(tl, d, v);
+    if (!ensure_part(d.fv[v], nvec)) return;
+  }
+  auto enqueue = [&](const double* x, double* y) {
+    if (precision != 0)
+      enqueue_tasks_tc(*this, d, x, y, nvec, xs, ys, precision, v);
+    else
+      enqueue_fp64(d, v, x, y, nvec, xs, ys);
+  };
+  if (timing) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, stream_);
+    enqueue(xv, yv);
+    cudaEventRecord(b, stream_);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    tu.ms[v] = ms;
+    if (++tu.next == kNumVariants) {
+      tu.best = 0;
+      for (int i = 1; i < kNumVariants; ++i)
+        if (tu.ms[i] < tu.ms[tu.best]) tu.best = i;
+    }
+  } else {
+    launch_graphed(d, key, xv, yv, nvec, xs, ys, enqueue);
+  }
+  if (precision != 0) check_tasks_tc(*this, d);
 }
 
 void CudaBackend::lincomb(const LCList& l) {

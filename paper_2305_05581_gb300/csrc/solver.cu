@@ -111,20 +111,25 @@ int check(CudaBackend& be, std::string& err) {
 // Davidson
 // ---------------------------------------------------------------------------
 int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, int precision, double* energy,
-             int* iters, Acc* acc, std::string& err) {
+             int* iters, Acc* acc, std::string& err, int block) {
   Step& st = E.step();
   const long long n = st.length;
   if (n <= 0) {
     err = "davidson: empty wavefunction space";
     return -1;
   }
-  const int kmax = (int)std::min<long long>(24, n);
+  block = std::max(1, std::min(block, 4));
+  // block form: a larger subspace and a thick restart that keeps 2*block
+  // Ritz vectors (fewer restarts per correction added)
+  const int kmax = (int)std::min<long long>(block > 1 ? 48 : 24, n);
+  block = std::min(block, std::max(1, kmax / 8));
   DBuf V(be, sizeof(double) * kmax * n), AV(be, sizeof(double) * kmax * n);
   DBuf diag(be, sizeof(double) * n), x(be, sizeof(double) * n), r(be, sizeof(double) * n),
       avs(be, sizeof(double) * n), t(be, sizeof(double) * n);
+  DBuf tmp(be, sizeof(double) * (block > 1 ? 4 * block : 1) * n);
   DBuf sm(be, sizeof(double) * (3 * 64 * 64 + 256));  // subspace matrix, eigvecs, eigvals, coefs
   DBuf aux(be, 256);
-  if (!V.p || !AV.p || !diag.p || !x.p || !r.p || !avs.p || !t.p || !sm.p || !aux.p) {
+  if (!V.p || !AV.p || !diag.p || !x.p || !r.p || !avs.p || !t.p || !tmp.p || !sm.p || !aux.p) {
     err = "davidson: device allocation failed";
     return -3;
   }
@@ -132,12 +137,10 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
   double* dVs = dA + 64 * 64;
   double* dw = dVs + 64 * 64;
   double* dcoef = dw + 64 * 64;
-  double* dscal = dcoef + 128;  // [0] theta, [1] dot result, ...
+  double* dscal = dcoef + 128;  // [0] theta, [1] dot result, [2] scale, [8 + i] theta of pair i
   long long* didx = aux.as<long long>();
   DBuf jac_meta(be, 64);
   long long zero_off = 0;
-  int nmat = 1;
-  (void)nmat;
   // diagonal
   {
     DevList& dl = be.dev(st.heff);
@@ -154,15 +157,31 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
     get(be, h, dscal + 1, 1);
     return h[0];
   };
-  auto matvec = [&](const double* in, double* out, int prec) {
+  // nv products in one launch (the block of Davidson vectors shares every
+  // operator block read)
+  auto matvec = [&](const double* in, double* out, int nv, int prec) {
     Timer tm(be.stream());
-    be.run(st.heff, in, out, 1, n, n, prec);
+    be.run(st.heff, in, out, nv, n, n, prec);
     float ms = tm.stop();
     if (acc) {
       acc->heff_ms += ms;
-      acc->matvecs++;
-      acc->flops += st.heff.flops;
+      acc->matvecs += nv;
+      acc->flops += st.heff.flops * nv;
     }
+  };
+  auto scale_by = [&](double* v, double f) {
+    std::vector<double> sc = {f};
+    put(be, dscal + 2, sc);
+    launch_scale(be, v, dscal + 2, 0, n);
+  };
+  // orthogonalise w twice against the first kk basis vectors; returns |w|^2
+  auto orth = [&](double* w, int kk) {
+    if (kk > 0)
+      for (int pass = 0; pass < 2; ++pass) {
+        launch_multidot(be, V.d(), n, kk, w, n, dcoef);
+        launch_axpy_multi(be, V.d(), n, kk, dcoef, -1.0, w, n);
+      }
+    return dot1(w, w);
   };
   // start vector
   be.note(cudaMemcpyAsync(V.d(), X, sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()), "copy");
@@ -172,62 +191,66 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
     launch_fill_unit(be, V.d(), n, didx);
     nx = 1.0;
   }
-  {
-    std::vector<double> s1 = {1.0 / std::sqrt(nx)};
-    put(be, dscal + 2, s1);
-    launch_scale(be, V.d(), dscal + 2, 0, n);
-  }
+  scale_by(V.d(), 1.0 / std::sqrt(nx));
   std::vector<double> H((size_t)kmax * kmax, 0.0);
-  int k = 0, it = 0;
+  int k = 0, it = 0, nnew = 1;
   double theta = 0.0, rn = 1e300;
   bool conv = false;
   const int lowp = precision != 0;
   double fp64_res = 1e300;
-  bool have_fp64 = false;
   while (true) {
-    // expand
-    matvec(V.d() + (long long)k * n, AV.d() + (long long)k * n, (lowp && k > 0) ? precision : 0);
-    ++it;
-    launch_multidot(be, V.d(), n, k + 1, AV.d() + (long long)k * n, n, dcoef);
-    std::vector<double> hc;
-    get(be, hc, dcoef, k + 1);
-    if (lowp && k > 0) {
-      // couplings to V_0 from its exact FP64 product: <V_k, H V_0> instead of
-      // <V_0, H~ V_k>; near convergence the reduced-precision error of the
-      // latter exceeds the coupling itself and would stall the refinement
-      hc[0] = dot1(V.d() + (long long)k * n, AV.d());
+    // expand by the nnew vectors V[k..k+nnew)
+    matvec(V.d() + (long long)k * n, AV.d() + (long long)k * n, nnew, (lowp && k > 0) ? precision : 0);
+    it += nnew;
+    for (int j = 0; j < nnew; ++j) {
+      const int kj = k + j;
+      launch_multidot(be, V.d(), n, kj + 1, AV.d() + (long long)kj * n, n, dcoef);
+      std::vector<double> hc;
+      get(be, hc, dcoef, kj + 1);
+      if (lowp && kj > 0) {
+        // couplings to V_0 from its exact FP64 product: <V_k, H V_0> instead of
+        // <V_0, H~ V_k>; near convergence the reduced-precision error of the
+        // latter exceeds the coupling itself and would stall the refinement
+        hc[0] = dot1(V.d() + (long long)kj * n, AV.d());
+      }
+      for (int i = 0; i <= kj; ++i) H[(size_t)i * kmax + kj] = H[(size_t)kj * kmax + i] = hc[i];
     }
-    for (int i = 0; i <= k; ++i) H[(size_t)i * kmax + k] = H[(size_t)k * kmax + i] = hc[i];
-    ++k;
+    k += nnew;
     // Rayleigh-Ritz on the device
     std::vector<double> Hk((size_t)k * k);
     for (int i = 0; i < k; ++i)
       for (int j = 0; j < k; ++j) Hk[(size_t)i * k + j] = 0.5 * (H[(size_t)i * kmax + j] + H[(size_t)j * kmax + i]);
     put(be, dA, Hk);
     std::vector<long long> offv = {zero_off};
-    std::vector<int> nv = {k}, wo = {0};
+    std::vector<int> nvv = {k}, wo = {0};
     put(be, jac_meta.as<long long>(), offv);
-    put(be, (int*)(jac_meta.as<long long>() + 1), nv);
+    put(be, (int*)(jac_meta.as<long long>() + 1), nvv);
     put(be, (int*)(jac_meta.as<long long>() + 1) + 1, wo);
     launch_jacobi(be, dA, dVs, dw, jac_meta.as<long long>(), (int*)(jac_meta.as<long long>() + 1),
                   (int*)(jac_meta.as<long long>() + 1) + 1, 1, k, nullptr);
     std::vector<double> w, vs;
     get(be, w, dw, k);
     get(be, vs, dVs, (size_t)k * k);
-    int j0 = 0;
-    for (int i = 1; i < k; ++i)
-      if (w[i] < w[j0]) j0 = i;
-    theta = w[j0];
-    std::vector<double> s(k);
-    for (int i = 0; i < k; ++i) s[i] = vs[(size_t)i * k + j0];
-    std::vector<double> th = {theta};
-    put(be, dcoef, s);
-    put(be, dscal, th);
+    std::vector<int> order(k);
+    for (int i = 0; i < k; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] < w[b]; });
+    auto ritz_coef = [&](int i) {
+      std::vector<double> s(k);
+      for (int q = 0; q < k; ++q) s[q] = vs[(size_t)q * k + order[i]];
+      return s;
+    };
+    theta = w[order[0]];
+    {
+      std::vector<double> s = ritz_coef(0), th = {theta};
+      put(be, dcoef, s);
+      put(be, dscal, th);
+    }
     launch_combine(be, V.d(), n, k, dcoef, x.d(), n);
     launch_combine(be, AV.d(), n, k, dcoef, avs.d(), n);
     launch_residual(be, avs.d(), x.d(), dscal, r.d(), n);
     rn = std::sqrt(std::max(0.0, dot1(r.d(), r.d())));
     if (check(be, err)) return -6;
+    bool restarted = false;
     if (lowp) {
       // FP64 residual correction: V_0 always carries an exact FP64 product,
       // the other basis vectors reduced-precision ones; the Ritz pair is
@@ -235,84 +258,109 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
       // subspace from the exact pair (x, H x)
       if (k == 1) {
         fp64_res = rn;  // x = V_0 and A V_0 is exact
-        have_fp64 = true;
         if (rn < tol || it >= max_iter) {
           conv = rn < tol;
           break;
         }
       }
-      bool stalled = k > 1 && (rn < std::max(0.5 * tol, 1e-3 * fp64_res) || k == kmax || it >= max_iter);
+      bool stalled = k > 1 && (rn < std::max(0.5 * tol, 1e-3 * fp64_res) || k + block > kmax || it >= max_iter);
       if (stalled) {
-        matvec(x.d(), avs.d(), 0);
+        matvec(x.d(), avs.d(), 1, 0);
         ++it;
         double xx = dot1(x.d(), x.d());
         double xh = dot1(x.d(), avs.d());
         theta = xh / xx;
-        th[0] = theta;
+        std::vector<double> th = {theta};
         put(be, dscal, th);
         launch_residual(be, avs.d(), x.d(), dscal, r.d(), n);
         rn = std::sqrt(std::max(0.0, dot1(r.d(), r.d())) / xx);
         fp64_res = rn;
-        have_fp64 = true;
         if (rn < tol || it >= max_iter) {
           conv = rn < tol;
           break;
         }
         // restart from the FP64-exact pair
-        std::vector<double> sc = {1.0 / std::sqrt(xx)};
-        put(be, dscal + 2, sc);
-        launch_scale(be, x.d(), dscal + 2, 0, n);
-        launch_scale(be, avs.d(), dscal + 2, 0, n);
-        launch_scale(be, r.d(), dscal + 2, 0, n);
+        const double f = 1.0 / std::sqrt(xx);
+        scale_by(x.d(), f);
+        scale_by(avs.d(), f);
+        scale_by(r.d(), f);
         be.note(cudaMemcpyAsync(V.d(), x.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()), "copy");
         be.note(cudaMemcpyAsync(AV.d(), avs.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()), "copy");
         k = 1;
         H[0] = theta;
+        restarted = true;
       }
     } else {
       if (rn < tol || it >= max_iter) {
         conv = rn < tol;
         break;
       }
-      if (k == kmax) {
-        be.note(cudaMemcpyAsync(V.d(), x.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()), "copy");
-        be.note(cudaMemcpyAsync(AV.d(), avs.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()), "copy");
-        k = 1;
-        H[0] = theta;
+      if (k + block > kmax) {
+        // thick restart: keep the lowest 2*block Ritz vectors (H becomes diagonal)
+        const int keep = block > 1 ? std::min(2 * block, k) : 1;
+        if (keep == 1) {
+          be.note(cudaMemcpyAsync(V.d(), x.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()), "copy");
+          be.note(cudaMemcpyAsync(AV.d(), avs.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()),
+                  "copy");
+        } else {
+          for (int i = 0; i < keep; ++i) {
+            std::vector<double> s = ritz_coef(i);
+            put(be, dcoef, s);
+            launch_combine(be, V.d(), n, k, dcoef, tmp.d() + (long long)i * n, n);
+            launch_combine(be, AV.d(), n, k, dcoef, tmp.d() + (long long)(keep + i) * n, n);
+          }
+          be.note(cudaMemcpyAsync(V.d(), tmp.d(), sizeof(double) * n * keep, cudaMemcpyDeviceToDevice, be.stream()),
+                  "copy");
+          be.note(cudaMemcpyAsync(AV.d(), tmp.d() + (long long)keep * n, sizeof(double) * n * keep,
+                                  cudaMemcpyDeviceToDevice, be.stream()),
+                  "copy");
+        }
+        std::fill(H.begin(), H.end(), 0.0);
+        for (int i = 0; i < keep; ++i) H[(size_t)i * kmax + i] = w[order[i]];
+        k = keep;
+        restarted = true;
       }
     }
-    // correction vector, orthogonalised twice against the basis
-    launch_precond(be, r.d(), diag.d(), dscal, t.d(), n);
-    for (int pass = 0; pass < 2; ++pass) {
-      launch_multidot(be, V.d(), n, k, t.d(), n, dcoef);
-      launch_axpy_multi(be, V.d(), n, k, dcoef, -1.0, t.d(), n);
-    }
-    double nt = dot1(t.d(), t.d());
-    if (!(nt > 1e-26)) {
-      // preconditioner gave nothing new: use the residual itself
-      be.note(cudaMemcpyAsync(t.d(), r.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()), "copy");
-      for (int pass = 0; pass < 2; ++pass) {
-        launch_multidot(be, V.d(), n, k, t.d(), n, dcoef);
-        launch_axpy_multi(be, V.d(), n, k, dcoef, -1.0, t.d(), n);
+    // corrections: preconditioned residuals of the lowest Ritz pairs (block
+    // form: up to `block` of them), each orthogonalised twice against the
+    // basis and the corrections before it
+    const int npairs = restarted ? 1 : std::min(block, k);
+    nnew = 0;
+    for (int i = 0; i < npairs && k + nnew < kmax; ++i) {
+      double* slot = V.d() + (long long)(k + nnew) * n;
+      double* thp = dscal + 8 + i;
+      std::vector<double> thi = {i == 0 ? theta : w[order[i]]};
+      put(be, thp, thi);
+      const double* ri = r.d();
+      if (i > 0) {
+        std::vector<double> s = ritz_coef(i);
+        put(be, dcoef, s);
+        launch_combine(be, V.d(), n, k, dcoef, tmp.d(), n);
+        launch_combine(be, AV.d(), n, k, dcoef, t.d(), n);
+        launch_residual(be, t.d(), tmp.d(), thp, tmp.d() + n, n);
+        ri = tmp.d() + n;
       }
-      nt = dot1(t.d(), t.d());
-      if (!(nt > 1e-28)) {
-        conv = rn < tol;
-        break;
+      launch_precond(be, ri, diag.d(), thp, slot, n);
+      double nt = orth(slot, k + nnew);
+      if (!(nt > 1e-26) && i == 0) {
+        // preconditioner gave nothing new: use the residual itself
+        be.note(cudaMemcpyAsync(slot, r.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()), "copy");
+        nt = orth(slot, k + nnew);
+        if (!(nt > 1e-28)) continue;
+      } else if (!(nt > 1e-26)) {
+        continue;
       }
+      scale_by(slot, 1.0 / std::sqrt(nt));
+      ++nnew;
     }
-    std::vector<double> sc = {1.0 / std::sqrt(nt)};
-    put(be, dscal + 2, sc);
-    launch_scale(be, t.d(), dscal + 2, 0, n);
-    be.note(cudaMemcpyAsync(V.d() + (long long)k * n, t.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice,
-                            be.stream()),
-            "copy");
+    if (nnew == 0) {
+      conv = rn < tol;
+      break;
+    }
   }
   // normalised eigenvector out
   double xx = dot1(x.d(), x.d());
-  std::vector<double> sc = {1.0 / std::sqrt(xx)};
-  put(be, dscal + 2, sc);
-  launch_scale(be, x.d(), dscal + 2, 0, n);
+  scale_by(x.d(), 1.0 / std::sqrt(xx));
   be.note(cudaMemcpyAsync(X, x.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()), "copy");
   be.sync();
   if (check(be, err)) return -6;
@@ -836,7 +884,7 @@ static int backend_davidson(tns::Engine& E, double* X, double tol, int max_iter,
                             int* iters, std::string& err) {
   tns::CudaBackend& be = *static_cast<tns::CudaBackend*>(E.be());
   cudaSetDevice(be.device());
-  return tns::davidson(E, be, X, tol, max_iter, precision, energy, iters, nullptr, err);
+  return tns::davidson(E, be, X, tol, max_iter, precision, energy, iters, nullptr, err, 1);
 }
 
 namespace tns {
@@ -863,7 +911,7 @@ int one_step(Engine& E, CudaBackend& be, int k, bool ltr, const tns_sweep_opts* 
   } else {
     two_site_guess(E, be, X.d(), k, st.psi);
   }
-  int rc = davidson(E, be, X.d(), o->tol, o->max_iter, o->precision, e, its, &acc, err);
+  int rc = davidson(E, be, X.d(), o->tol, o->max_iter, o->precision, e, its, &acc, err, o->block);
   *conv = rc == 0;
   if (rc && rc != -4) return rc;
   err.clear();

@@ -1,44 +1,66 @@
 // tc.cu -- reduced-precision form of the grouped triple product on the
 // 5th-generation tensor cores (tcgen05, accumulators in TMEM).
 //
-// The products of one output tile that read the same input block X are
-// fused the way Alg. 2 fuses the position sum (Sec. II.C): with
-// p products sharing X,
-//     GEMM1:  [T_1 | ... | T_p] = X [R_1; ...; R_p]^T        (N = p*r, one MMA chain)
-//     GEMM2:  Y += [a_1 L_1 | ... | a_p L_p] [T_1; ...; T_p]   (K = p*m, accumulated in TMEM)
-// so the sum over positions, operator pairs and dot blocks is the K loop of
-// one accumulation, as SBMM4S does with cuBLAS, but without leaving the SM:
-// T goes TMEM -> registers -> shared memory (re-split) -> GEMM2.
+// Every product of H_eff*psi is Y += a op(L) X op(R)^T (Eq. 2); an identity
+// operator is a small identity image, so all products take one path.  The
+// products of one output tile that read the same X block are fused the way
+// Alg. 2 fuses the position sum (Sec. II.C):
+//     GEMM1:  [T_1^T; ...; T_p^T] = [R_1; ...; R_p] X^T    (R rows stacked into M = 128)
+//     GEMM2:  Y += sum_t (a_t L_t) T_t                       (one TMEM accumulator)
+// The TMEM rows of GEMM1 are rows of T_t^T, so in the T pass each thread
+// holds eight consecutive K elements of GEMM2's B operand and writes them,
+// scaled by a_t and re-split, as one 16-byte vector.
 //
-// Precisions: TNS_TF32 (kind::tf32, operands rounded to TF32) and TNS_BF16X3
-// (x = x_hi + x_lo in bf16, three products hi*hi + hi*lo + lo*hi, FP32
-// accumulation).  Operands are converted from the FP64 arenas while staged
-// into shared memory in the no-swizzle K-major layout (8 x 16-byte core
-// matrices, consecutive along K).  One CTA of 128 threads per output tile
-// (<= 128 rows x <= 64 columns); thread 0 issues the MMAs; every wait on the
-// MMA-completion mbarrier is bounded and reports a timeout flag instead of
-// hanging.
+// Operands: the L/R operator blocks are fixed during the ~50 products of a
+// two-site step, so they are converted once per step into images -- bf16 hi +
+// bf16 lo (TNS_BF16X3: x = hi + lo, three products hi*hi + hi*lo + lo*hi) or
+// tf32 (TNS_TF32) -- already in the K-major, no-swizzle core-matrix layout the
+// MMA reads: K in chunks of 64 bytes per row; inside a chunk, groups of 8 rows
+// of 16-byte core matrices.  X is converted once per product call.  Staging
+// is a few cp.async.bulk copies per chunk with mbarrier completion; the FP64
+// pipe stays out of the product loop.
+//
+// One CTA (256 threads) per output tile piece (128 rows x <= 64 columns);
+// thread 0 issues copies and MMAs, all threads do the T pass and the epilogue.
+// Every wait is bounded; a timeout sets a flag the host reads, after the CTA
+// has drained (bounded) its own copies and MMAs and released its TMEM.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdio>
+#include <map>
+#include <string>
+#include <tuple>
 #include <vector>
 
+#include "../../include/tns.h"
 #include "cuda_backend.h"
 
 namespace tns {
 
 namespace {
 
-// two CTAs of 8 warps per SM: ~105 KB shared memory and 256 TMEM columns each
 constexpr int TC_NT = 256;
-constexpr int TC_M = 128;    // MMA M (rows of a tile / of an X chunk)
-constexpr int TC_RMAX = 64;  // tile columns
-constexpr int TC_N1 = 128;   // GEMM1 N limit (p * r_pad) = TMEM columns of D1
-constexpr int TC_K1 = 32;    // GEMM1 K chunk (elements)
-constexpr int TC_K2 = 96;    // GEMM2 K limit per chunk (p * mc16)
-constexpr long long TC_SPIN = 20000000;
+constexpr int TC_M = 128;     // MMA M: output tile rows; stacked R rows of GEMM1
+constexpr int TC_NC = 64;     // output tile columns (GEMM2 N <= 64)
+constexpr int TC_MC = 64;     // X rows per GEMM1 step (GEMM1 N <= 64, GEMM2 K <= 64)
+constexpr int CH_BYTES = 64;  // bytes of one K chunk of one row (4 core matrices)
+constexpr unsigned long long TC_WAIT_NS = 200000000ull;  // bound of one wait: 0.2 s
+
+// operand image: rows padded to 8, K padded to 32 bytes, K chunks of 64 bytes
+struct Img {
+  long long off;  // byte offset in the image arena (hi; lo at the same offset)
+  int rg;         // row groups (rows / 8, rounded up)
+  int kb;         // padded K in bytes (multiple of 32)
+};
+
+struct TcTask {
+  float alpha;
+  int xb;  // X block index (its image is converted per call)
+  Img L, R;
+  int m, n;  // X block m x n (= columns of op(L), columns of op(R))
+};
 
 struct TcTile {
   int g;
@@ -46,24 +68,66 @@ struct TcTile {
   int c0, c1;      // chunk range of this piece
   long long poff;  // -1: write the output block; else offset of this piece's partial tile
 };
+
 struct TcChunk {
-  int t0, t1;  // tasks (indices into the permuted task array)
-  int kind;    // 0: T = X R^T (GEMM1 + GEMM2); 1: T = X directly (R identity)
-  int pad;
+  int t0, t1;  // products sharing one X block
 };
 
-struct TcPlan {
-  Task* tasks = nullptr;
+struct XBlock {
+  long long src;  // element offset of the block in the psi vector
+  int m, n;
+  Img img;
+};
+
+struct ImgJob {  // convert one operand block into its image
+  const double* src;
+  int rows, cols;  // op(M) is rows x cols
+  int trans;       // op(M)[i][k] = trans ? M[k * rows + i] : M[i * cols + k]; identity if src == null
+  Img img;
+};
+
+struct TcVariant {
+  bool planned = false;
   TcTile* tiles = nullptr;
-  TcChunk* chunks = nullptr;
   int ntiles = 0;
-  int* flag = nullptr;
-  SplitRed* reds = nullptr;  // split tiles (pieces summed in order afterwards)
+  SplitRed* reds = nullptr;
   int nreds = 0;
   long long psize = 0;
   double* part = nullptr;
   int part_nvec = 0;
 };
+
+struct TcPlan {
+  int precision = 0;
+  TcTask* tasks = nullptr;
+  TcChunk* chunks = nullptr;
+  XBlock* xblocks = nullptr;
+  int nxb = 0;
+  int* flag = nullptr;
+  unsigned char* ops_hi = nullptr;  // L/R images (built once per plan)
+  unsigned char* ops_lo = nullptr;
+  long long ops_bytes = 0;
+  unsigned char* x_hi = nullptr;  // X images (per product call, per vector)
+  unsigned char* x_lo = nullptr;
+  long long x_bytes = 0;  // per vector
+  int x_nvec = 0;
+  std::vector<TcTask> tasks_h;
+  std::vector<TcTile> tiles_h;
+  std::vector<TcChunk> chunks_h;
+  std::vector<XBlock> xbs_h;
+  TcVariant var[kNumVariants];
+  int sms = 152;
+};
+
+__host__ __device__ inline long long img_bytes(const Img& g) { return (long long)g.rg * 8 * g.kb; }
+// bytes per row of K chunk c, and the chunk's offset
+__host__ __device__ inline int chunk_w(const Img& g, int c) {
+  const int w = g.kb - c * CH_BYTES;
+  return w < CH_BYTES ? w : CH_BYTES;
+}
+__host__ __device__ inline long long chunk_off(const Img& g, int c) {
+  return g.off + (long long)g.rg * 8 * c * CH_BYTES;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -100,324 +164,536 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
 }
 
-// bounded wait for phase `ph`; returns false on timeout
+__device__ __forceinline__ void bar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bulk global -> shared copy completing on `bar` (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for phase `ph`, bounded in time; returns false on timeout
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t ph) {
   uint32_t done = 0;
-  for (long long it = 0; it < TC_SPIN && !done; ++it) {
+  const unsigned long long t0 = gtimer();
+  while (!done) {
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
                  : "=r"(done)
-                 : "r"(smem_u32(bar)), "r"(ph));
+                 : "r"(smem_u32(bar)), "r"(ph)
+                 : "memory");
+    if (!done && gtimer() - t0 > TC_WAIT_NS) break;
   }
   return done != 0;
 }
 
-// element (row, k) of a K-major no-swizzle operand with kc elements per row
-template <int ES>
-__device__ __forceinline__ int coff(int row, int k, int kc) {
-  constexpr int KPC = 16 / ES;
-  return (row >> 3) * (kc / KPC) * 128 + (k / KPC) * 128 + (row & 7) * 16 + (k % KPC) * ES;
-}
-
+// ---------------------------------------------------------------------------
+// image conversion: one thread per 16-byte unit of the destination
+// ---------------------------------------------------------------------------
 template <int TF32>
-__device__ __forceinline__ void put(unsigned char* hi, unsigned char* lo, int off, float x) {
+__device__ __forceinline__ void convert_unit(const double* v, unsigned char* hi, unsigned char* lo, long long off) {
   if (TF32) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    *(uint32_t*)(hi + off) = r;
+    uint32_t r[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r[e]) : "f"((float)v[e]));
+    *(uint4*)(hi + off) = make_uint4(r[0], r[1], r[2], r[3]);
   } else {
-    __nv_bfloat16 h = __float2bfloat16_rn(x);
-    __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-    *(__nv_bfloat16*)(hi + off) = h;
-    *(__nv_bfloat16*)(lo + off) = l;
+    __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float x = (float)v[e];
+      h[e] = __float2bfloat16_rn(x);
+      l[e] = __float2bfloat16_rn(x - __bfloat162float(h[e]));
+    }
+    *(uint4*)(hi + off) = *(const uint4*)h;
+    *(uint4*)(lo + off) = *(const uint4*)l;
   }
 }
 
-__device__ __forceinline__ double g_opL(const Task& t, int i, int k) {
-  if (t.flags & TF_LI) return i == k ? 1.0 : 0.0;
-  return (t.flags & TF_LT) ? __ldg(t.L + (long long)k * t.q + i) : __ldg(t.L + (long long)i * t.m + k);
-}
-__device__ __forceinline__ double g_opR(const Task& t, int j, int k) {
-  if (t.flags & TF_RI) return j == k ? 1.0 : 0.0;
-  return (t.flags & TF_RT) ? __ldg(t.R + (long long)k * t.r + j) : __ldg(t.R + (long long)j * t.n + k);
+// 16-byte unit u of an image (units in byte order: chunk, row group, core
+// matrix, row) -> its row, first K element and byte offset
+template <int TF32>
+__device__ __forceinline__ void unit_pos(const Img& g, long long u, int& row, int& k0, long long& off) {
+  constexpr int ES = TF32 ? 4 : 2;
+  long long rem = u;
+  int c = 0;
+  for (;; ++c) {
+    const long long cu = (long long)g.rg * 8 * chunk_w(g, c) / 16;
+    if (rem < cu) break;
+    rem -= cu;
+  }
+  const int kcm = chunk_w(g, c) / 16;
+  const int r8 = (int)(rem % 8);
+  const long long t = rem / 8;
+  const int kk = (int)(t % kcm);
+  const int rgi = (int)(t / kcm);
+  row = rgi * 8 + r8;
+  k0 = (c * CH_BYTES + kk * 16) / ES;
+  off = chunk_off(g, c) + ((long long)rgi * kcm + kk) * 128 + r8 * 16;
 }
 
 template <int TF32>
-__global__ void __launch_bounds__(TC_NT, 2) k_tasks_tc(const Task* __restrict__ tasks, const Group* __restrict__ groups,
-                                                        const TcTile* __restrict__ tiles,
-                                                        const TcChunk* __restrict__ chunks, const double* xv,
-                                                        double* yv, long long xs, long long ys, int* flag,
-                                                        double* part_all, long long psize) {
-  constexpr int ES = TF32 ? 4 : 2;
+__global__ void __launch_bounds__(256) k_img_ops(const ImgJob* __restrict__ jobs, unsigned char* hi,
+                                                 unsigned char* lo) {
+  constexpr int EPU = TF32 ? 4 : 8;  // elements per 16-byte unit
+  const ImgJob J = jobs[blockIdx.x];
+  const long long units = img_bytes(J.img) / 16;
+  for (long long u = threadIdx.x; u < units; u += blockDim.x) {
+    int row, k0;
+    long long off;
+    unit_pos<TF32>(J.img, u, row, k0, off);
+    double v[EPU];
+#pragma unroll
+    for (int e = 0; e < EPU; ++e) {
+      const int k = k0 + e;
+      double x = 0.0;
+      if (row < J.rows && k < J.cols) {
+        if (!J.src)
+          x = row == k ? 1.0 : 0.0;
+        else
+          x = J.trans ? J.src[(long long)k * J.rows + row] : J.src[(long long)row * J.cols + k];
+      }
+      v[e] = x;
+    }
+    convert_unit<TF32>(v, hi, lo, off);
+  }
+}
+
+template <int TF32>
+__global__ void __launch_bounds__(256) k_img_x(const XBlock* __restrict__ xb, const double* xv, long long xs,
+                                               unsigned char* hi, unsigned char* lo, long long xbytes) {
+  constexpr int EPU = TF32 ? 4 : 8;
+  const XBlock B = xb[blockIdx.x];
+  const int vec = blockIdx.y;
+  const double* X = xv + (long long)vec * xs + B.src;
+  unsigned char* h = hi + (long long)vec * xbytes;
+  unsigned char* l = TF32 ? nullptr : lo + (long long)vec * xbytes;
+  const long long units = img_bytes(B.img) / 16;
+  for (long long u = threadIdx.x; u < units; u += blockDim.x) {
+    int row, k0;
+    long long off;
+    unit_pos<TF32>(B.img, u, row, k0, off);
+    double v[EPU];
+#pragma unroll
+    for (int e = 0; e < EPU; ++e) {
+      const int k = k0 + e;
+      v[e] = (row < B.m && k < B.n) ? X[(long long)row * B.n + k] : 0.0;
+    }
+    convert_unit<TF32>(v, h, l, off);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the product kernel
+// ---------------------------------------------------------------------------
+template <int TF32>
+struct TcSmem {
+  static constexpr int ES = TF32 ? 4 : 2;
+  static constexpr int NS = TF32 ? 1 : 2;       // planes: hi (+ lo)
+  static constexpr int A1 = TC_M * CH_BYTES;    // stacked R rows, one K chunk
+  static constexpr int B1 = TC_MC * CH_BYTES;   // X rows, one K chunk
+  static constexpr int CB2 = TC_M * CH_BYTES;   // one K chunk of B2 (all 128 rows)
+  static constexpr int B2 = TC_MC * ES / CH_BYTES * CB2;  // T^T of all products, K = TC_MC
+  static constexpr int A2 = TC_M * CH_BYTES;    // L rows, one K chunk (two buffers)
+  static constexpr int total = NS * (A1 + B1 + B2 + 2 * A2) + 1024;
+};
+
+template <int TF32>
+__global__ void __launch_bounds__(TC_NT, 2)
+    k_tasks_tc(const TcTask* __restrict__ tasks, const Group* __restrict__ groups, const TcTile* __restrict__ tiles,
+               const TcChunk* __restrict__ chunks, const unsigned char* __restrict__ ops_hi,
+               const unsigned char* __restrict__ ops_lo, const unsigned char* __restrict__ x_hi,
+               const unsigned char* __restrict__ x_lo, long long x_bytes, const XBlock* __restrict__ xblocks,
+               double* yv, long long ys, int* flag, double* part_all, long long psize) {
+  using S = TcSmem<TF32>;
+  constexpr int ES = S::ES;
   constexpr int NPROD = TF32 ? 1 : 3;
-  constexpr int KSTEP = 16 / ES * 2;  // elements per MMA k-step (32 bytes)
-  constexpr int SZ_A1 = TC_M * TC_K1 * ES, SZ_B1 = TC_N1 * TC_K1 * ES;
-  constexpr int SZ_A2 = TC_M * TC_K2 * ES, SZ_B2 = TC_RMAX * TC_K2 * ES;
+  constexpr int EPC = CH_BYTES / ES;              // elements per K chunk
+  constexpr uint32_t SBO_FULL = (CH_BYTES / 16) * 128;
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* A1h = smem;
-  unsigned char* A1l = A1h + SZ_A1;
-  unsigned char* B1h = A1l + (TF32 ? 0 : SZ_A1);
-  unsigned char* B1l = B1h + SZ_B1;
-  unsigned char* A2h = B1l + (TF32 ? 0 : SZ_B1);
-  unsigned char* A2l = A2h + SZ_A2;
-  unsigned char* B2h = A2l + (TF32 ? 0 : SZ_A2);
-  unsigned char* B2l = B2h + SZ_B2;
-  __shared__ uint64_t bar;
+  unsigned char* const sA1 = smem;                          // planes at + p * S::A1
+  unsigned char* const sB1 = smem + S::NS * S::A1;          // planes at + p * S::B1
+  unsigned char* const sB2 = sB1 + S::NS * S::B1;           // planes at + p * S::B2
+  unsigned char* const sA2 = sB2 + S::NS * S::B2;           // buffer b, plane p at + (b * NS + p) * S::A2
+  __shared__ uint64_t lbar1, mbar1, lbar2[2], mbar2[2];
   __shared__ uint32_t tbase;
   __shared__ int bad;
+  __shared__ float salpha[TC_M / 16];
   const int tid = threadIdx.x;
   const TcTile TL = tiles[blockIdx.x];
   const Group G = groups[TL.g];
   const int vec = blockIdx.y;
-  const double* X0 = xv + (long long)vec * xs;
-  const int rpad = (TL.ncols + 15) & ~15;
-  double* part = TL.poff >= 0 ? part_all : nullptr;  // split piece: write the partial tile
+  const unsigned char* xh = x_hi + (long long)vec * x_bytes;
+  const unsigned char* xl = TF32 ? nullptr : x_lo + (long long)vec * x_bytes;
+  const int rp = (TL.ncols + 15) & ~15;  // GEMM2 N; rows of one product in the GEMM1 stack
+  const bool has_work = TL.c1 > TL.c0;   // uniform: this piece issues at least one GEMM2 chain
+  double* part = TL.poff >= 0 ? part_all : nullptr;
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    bar_init(&lbar1);
+    bar_init(&mbar1);
+    bar_init(&lbar2[0]);
+    bar_init(&lbar2[1]);
+    bar_init(&mbar2[0]);
+    bar_init(&mbar2[1]);
     asm volatile("fence.mbarrier_init.release.cluster;");
     bad = 0;
   }
   if (tid < 32) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tbase)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&tbase)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tD1 = tbase, tD2 = tbase + TC_N1;
-  uint32_t phase = 0;
+  const uint32_t tD1 = tbase, tD2 = tbase + 64;
+  // barrier bookkeeping (thread 0 only): phases and outstanding completions
+  uint32_t pl1 = 0, pm1 = 0, pl2[2] = {0, 0}, pm2[2] = {0, 0};
+  int l1_out = 0, m1_out = 0, l2_out[2] = {0, 0}, m2_out[2] = {0, 0};
+  int g2_steps = 0;
   bool d2 = false;
+  int where_c = -1, where_m0 = -1, where_s = -1;
+  auto drain = [&](uint64_t* bar, uint32_t& ph, int& out) {
+    if (!out) return;
+    if (wait_bar(bar, ph)) {
+      ph ^= 1;
+      out = 0;
+    } else {
+      if (!bad && atomicCAS(flag, 0, 1) == 0) {
+        const int which = bar == &lbar1 ? 1 : bar == &mbar1 ? 2 : bar == &lbar2[0] ? 3 : bar == &lbar2[1] ? 4
+                        : bar == &mbar2[0] ? 5 : 6;
+        flag[1] = blockIdx.x;
+        flag[2] = which;
+        flag[3] = where_c;
+        flag[4] = where_m0;
+        flag[5] = where_s;
+        flag[6] = (int)ph;
+      }
+      bad = 1;
+    }
+  };
 
   for (int c = TL.c0; c < TL.c1 && !bad; ++c) {
     const TcChunk C = chunks[c];
     const int pc = C.t1 - C.t0;
-    const Task t0 = tasks[C.t0];
-    const double* Xp = X0 + (long long)(size_t)t0.X;
-    const int m = t0.m, n = t0.n;
-    const long long sXi = (t0.flags & TF_XT) ? 1 : n, sXk = (t0.flags & TF_XT) ? m : 1;
-    for (int m0 = 0; m0 < m && !bad; m0 += TC_M) {
-      const int mc = min(TC_M, m - m0);
+    const TcTask t0 = tasks[C.t0];
+    const XBlock XB = xblocks[t0.xb];
+    const int m = t0.m;
+    if (tid < pc) salpha[tid] = tasks[C.t0 + tid].alpha;
+    where_c = c;
+    for (int m0 = 0; m0 < m && !bad; m0 += TC_MC) {
+      where_m0 = m0;
+      const int mc = min(TC_MC, m - m0);
       const int mc16 = (mc + 15) & ~15;
-      if (C.kind == 0) {
-        // GEMM1: D1[128 x pc*rpad] = X[m0.., :] * [R_t]^T
-        const int N1 = pc * rpad;
-        for (int n0 = 0; n0 < n && !bad; n0 += TC_K1) {
-          // only rows that reach the output are staged: D1 rows >= mc and
-          // columns of j >= ncols are never read back (K padding is zeroed)
-          for (int e = tid; e < mc * TC_K1; e += TC_NT) {
-            const int i = e / TC_K1, k = e % TC_K1;
-            float x = (n0 + k < n) ? (float)__ldg(Xp + (m0 + i) * sXi + (n0 + k) * sXk) : 0.f;
-            put<TF32>(A1h, A1l, coff<ES>(i, k, TC_K1), x);
+      // ---- GEMM1: D1[t*rp + j][i] = sum_k R_t[col0 + j][k] X[m0 + i][k] ----
+      if (tid == 0) {
+        const int nch = (XB.img.kb + CH_BYTES - 1) / CH_BYTES;
+        const int xg0 = m0 / 8, xng = min(mc16 / 8, XB.img.rg - xg0);
+        for (int kc = 0; kc < nch && !bad; ++kc) {
+          where_s = kc;
+          const int kcm = chunk_w(XB.img, kc) / 16;
+          const uint32_t rowb = kcm * 128;  // bytes of one row group in this chunk
+          uint32_t bytes = (xng > 0 ? xng * rowb : 0) * S::NS;
+          for (int t = 0; t < pc; ++t) {
+            const int ng = min(rp / 8, tasks[C.t0 + t].R.rg - TL.col0 / 8);
+            if (ng > 0) bytes += ng * rowb * S::NS;
           }
-          for (int e = tid; e < pc * TL.ncols * TC_K1; e += TC_NT) {
-            const int tj = e / TC_K1, k = e % TC_K1;
-            const int t = tj / TL.ncols, j = tj % TL.ncols;
-            const Task tk = tasks[C.t0 + t];
-            float x = (n0 + k < n) ? (float)g_opR(tk, TL.col0 + j, n0 + k) : 0.f;
-            put<TF32>(B1h, B1l, coff<ES>(t * rpad + j, k, TC_K1), x);
+          expect_tx(&lbar1, bytes);
+          l1_out = 1;
+          if (xng > 0) {
+            const long long xo = chunk_off(XB.img, kc) + (long long)xg0 * rowb;
+            bulk_g2s(sB1, xh + xo, xng * rowb, &lbar1);
+            if (!TF32) bulk_g2s(sB1 + S::B1, xl + xo, xng * rowb, &lbar1);
           }
-          asm volatile("fence.proxy.async.shared::cta;");
-          __syncthreads();
-          if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t id = idesc(TF32 ? 2 : 1, N1);
-            const uint32_t sboA = (TC_K1 / (16 / ES)) * 128, sboB = sboA;
-            for (int ks = 0; ks < TC_K1 / KSTEP; ++ks)
-              for (int pr = 0; pr < NPROD; ++pr) {
-                const unsigned char* a = (pr == 2) ? A1l : A1h;
-                const unsigned char* b = (pr == 1) ? B1l : B1h;
-                uint32_t acc = (n0 > 0 || ks > 0 || pr > 0) ? 1u : 0u;
-                mma<TF32>(tD1, sdesc(smem_u32(a) + ks * 256, sboA), sdesc(smem_u32(b) + ks * 256, sboB), id, acc);
-              }
-            commit(&bar);
+          for (int t = 0; t < pc; ++t) {
+            const Img R = tasks[C.t0 + t].R;
+            const int ng = min(rp / 8, R.rg - TL.col0 / 8);
+            if (ng <= 0) continue;
+            const long long ro = chunk_off(R, kc) + (long long)(TL.col0 / 8) * rowb;
+            const uint32_t dst = (uint32_t)(t * rp / 8) * rowb;
+            bulk_g2s(sA1 + dst, ops_hi + ro, ng * rowb, &lbar1);
+            if (!TF32) bulk_g2s(sA1 + S::A1 + dst, ops_lo + ro, ng * rowb, &lbar1);
           }
-          if (!wait_bar(&bar, phase)) {
-            bad = 1;
-          }
-          phase ^= 1;
+          drain(&lbar1, pl1, l1_out);
+          if (bad) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
-          __syncthreads();
+          const uint32_t id = idesc(TF32 ? 2 : 1, mc16);
+          for (int ks = 0; ks < kcm / 2; ++ks)
+            for (int pr = 0; pr < NPROD; ++pr) {
+              const unsigned char* a = sA1 + (pr == 2 ? S::A1 : 0);
+              const unsigned char* b = sB1 + (pr == 1 ? S::B1 : 0);
+              const uint32_t acc = (kc > 0 || ks > 0 || pr > 0) ? 1u : 0u;
+              mma<TF32>(tD1, sdesc(smem_u32(a) + ks * 256, rowb), sdesc(smem_u32(b) + ks * 256, rowb), id, acc);
+            }
+          commit(&mbar1);
+          m1_out = 1;
+          drain(&mbar1, pm1, m1_out);
         }
-        if (bad) break;
+        // the T pass rewrites B2: GEMM2 MMAs still reading it must be done
+        drain(&mbar2[0], pm2[0], m2_out[0]);
+        drain(&mbar2[1], pm2[1], m2_out[1]);
       }
-      // stage A2 = [a_t L_t] (128 x pc*mc16) and B2 = [T_t]^T (rpad x pc*mc16)
-      const int K2 = pc * mc16;
-      for (int e = tid; e < TL.nrows * K2; e += TC_NT) {  // D2 rows >= nrows are never read back
-        const int i = e / K2, kk = e % K2;
-        const int t = kk / mc16, k = kk % mc16;
-        const Task tk = tasks[C.t0 + t];
-        float x = (k < mc) ? (float)(tk.alpha * g_opL(tk, TL.row0 + i, m0 + k)) : 0.f;
-        put<TF32>(A2h, A2l, coff<ES>(i, kk, TC_K2), x);
-      }
-      if (C.kind == 0) {
-        // from TMEM: warp w reads lane quarter w%4 (rows 32(w%4)..+31 of D1,
-        // row = k index inside a task's slot); the two warpgroups split the
-        // column chunks
-        const int warp = tid >> 5, row = ((warp & 3) << 5) | (tid & 31), wg = warp >> 2;
-        for (int t = 0; t < pc; ++t)
-          for (int j0 = 8 * wg; j0 < rpad; j0 += 16) {
-            uint32_t r[8];
-            const uint32_t addr = tD1 + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(t * rpad + j0);
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7])
-                         : "r"(addr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (row < mc16)
-              for (int q = 0; q < 8; ++q) {
-                float x = (row < mc && j0 + q < TL.ncols) ? __uint_as_float(r[q]) : 0.f;
-                put<TF32>(B2h, B2l, coff<ES>(j0 + q, t * mc16 + row, TC_K2), x);
-              }
+      __syncthreads();
+      if (bad) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      // ---- T pass: D1 (fp32) -> B2 = a_t T_t^T in the K-major operand layout ----
+      {
+        const int warp = tid >> 5, wg = warp >> 2;
+        const int row = (warp & 3) * 32 + (tid & 31);  // TMEM lane = stacked R row = B2 row
+        const int t = row / rp;
+        const float al = (t < pc) ? salpha[t] : 0.f;
+        for (int i0 = 8 * wg; i0 < mc16; i0 += 16) {
+          uint32_t r[8];
+          const uint32_t addr = tD1 + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)i0;
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                         "=r"(r[7])
+                       : "r"(addr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          if (t >= pc) continue;
+          float v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = (i0 + e < mc) ? al * __uint_as_float(r[e]) : 0.f;
+          if (TF32) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int i = i0 + 4 * h;
+              const int off = (i / EPC) * S::CB2 + ((row >> 3) * (CH_BYTES / 16) + (i % EPC) * ES / 16) * 128 +
+                              (row & 7) * 16;
+              uint32_t q[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(q[e]) : "f"(v[4 * h + e]));
+              *(uint4*)(sB2 + off) = make_uint4(q[0], q[1], q[2], q[3]);
+            }
+          } else {
+            const int off = (i0 / EPC) * S::CB2 + ((row >> 3) * (CH_BYTES / 16) + (i0 % EPC) * ES / 16) * 128 +
+                            (row & 7) * 16;
+            __align__(16) __nv_bfloat16 hh[8], ll[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              hh[e] = __float2bfloat16_rn(v[e]);
+              ll[e] = __float2bfloat16_rn(v[e] - __bfloat162float(hh[e]));
+            }
+            *(uint4*)(sB2 + off) = *(const uint4*)hh;
+            *(uint4*)(sB2 + S::B2 + off) = *(const uint4*)ll;
           }
-      } else {
-        // T = X directly (product with R = identity)
-        for (int e = tid; e < rpad * K2; e += TC_NT) {
-          const int j = e / K2, kk = e % K2;
-          const int t = kk / mc16, k = kk % mc16;
-          const Task tk = tasks[C.t0 + t];
-          const double* Xt = X0 + (long long)(size_t)tk.X;
-          const long long si = (tk.flags & TF_XT) ? 1 : tk.n, sk = (tk.flags & TF_XT) ? tk.m : 1;
-          float x = (k < mc && j < TL.ncols) ? (float)__ldg(Xt + (m0 + k) * si + (TL.col0 + j) * sk) : 0.f;
-          put<TF32>(B2h, B2l, coff<ES>(j, kk, TC_K2), x);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
       __syncthreads();
+      // ---- GEMM2: D2 += sum_t L_t[row0.., m0 + k] * B2_t^T (thread 0) ----
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t id = idesc(TF32 ? 2 : 1, rpad);
-        const uint32_t sboA = (TC_K2 / (16 / ES)) * 128, sboB = sboA;
-        for (int ks = 0; ks < K2 / KSTEP; ++ks)
-          for (int pr = 0; pr < NPROD; ++pr) {
-            const unsigned char* a = (pr == 2) ? A2l : A2h;
-            const unsigned char* b = (pr == 1) ? B2l : B2h;
-            uint32_t acc = (d2 || ks > 0 || pr > 0) ? 1u : 0u;
-            mma<TF32>(tD2, sdesc(smem_u32(a) + ks * 256, sboA), sdesc(smem_u32(b) + ks * 256, sboB), id, acc);
+        const int nk2 = mc16 * ES / 32;  // 32-byte MMA k-steps over this X row range
+        const int nch2 = (mc16 * ES + CH_BYTES - 1) / CH_BYTES;
+        const uint32_t id = idesc(TF32 ? 2 : 1, rp);
+        for (int t = 0; t < pc && !bad; ++t) {
+          const Img Lm = tasks[C.t0 + t].L;
+          const int lg0 = TL.row0 / 8, lng = min(TC_M / 8, Lm.rg - lg0);
+          const uint32_t bt = (uint32_t)(t * rp / 8) * SBO_FULL;  // product t's rows inside a B2 chunk
+          for (int c2 = 0; c2 < nch2 && !bad; ++c2) {
+            const int b = g2_steps & 1;
+            where_s = 1000 + t * 16 + c2;
+            drain(&mbar2[b], pm2[b], m2_out[b]);  // buffer b free
+            if (bad) break;
+            const int lc = (m0 * ES) / CH_BYTES + c2;  // chunk of L's K (= X rows)
+            const int kcm = chunk_w(Lm, lc) / 16;
+            const uint32_t rowb = kcm * 128;
+            unsigned char* a2 = sA2 + b * S::NS * S::A2;
+            expect_tx(&lbar2[b], lng * rowb * S::NS);
+            l2_out[b] = 1;
+            const long long lo_ = chunk_off(Lm, lc) + (long long)lg0 * rowb;
+            bulk_g2s(a2, ops_hi + lo_, lng * rowb, &lbar2[b]);
+            if (!TF32) bulk_g2s(a2 + S::A2, ops_lo + lo_, lng * rowb, &lbar2[b]);
+            drain(&lbar2[b], pl2[b], l2_out[b]);
+            if (bad) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int ks_here = min(kcm / 2, nk2 - c2 * (CH_BYTES / 32));
+            for (int ks = 0; ks < ks_here; ++ks)
+              for (int pr = 0; pr < NPROD; ++pr) {
+                const unsigned char* a = a2 + (pr == 2 ? S::A2 : 0);
+                const unsigned char* bb = sB2 + (pr == 1 ? S::B2 : 0) + c2 * S::CB2 + bt;
+                const uint32_t acc = (d2 || ks > 0 || pr > 0) ? 1u : 0u;
+                mma<TF32>(tD2, sdesc(smem_u32(a) + ks * 256, rowb), sdesc(smem_u32(bb) + ks * 256, SBO_FULL), id,
+                          acc);
+              }
+            d2 = true;
+            commit(&mbar2[b]);
+            m2_out[b] = 1;
+            ++g2_steps;
           }
-        commit(&bar);
+        }
       }
-      if (!wait_bar(&bar, phase)) bad = 1;
-      phase ^= 1;
-      d2 = true;
-      asm volatile("tcgen05.fence::after_thread_sync;");
       __syncthreads();
     }
   }
-  // epilogue: D2 -> Y (FP64)
-  double* Y = yv + (long long)vec * ys + G.yoff;
-  const int warp = tid >> 5, row = ((warp & 3) << 5) | (tid & 31), wg = warp >> 2;
-  for (int j0 = 8 * wg; j0 < rpad; j0 += 16) {
-    uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (d2 && !bad) {
-      const uint32_t addr = tD2 + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)j0;
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                   : "r"(addr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
+  // every copy and MMA of this CTA done (bounded) before TMEM is read or released
+  if (tid == 0) {
+    drain(&lbar1, pl1, l1_out);
+    drain(&mbar1, pm1, m1_out);
+    for (int b = 0; b < 2; ++b) {
+      drain(&lbar2[b], pl2[b], l2_out[b]);
+      drain(&mbar2[b], pm2[b], m2_out[b]);
     }
-    if (row < TL.nrows)
-      for (int q = 0; q < 8; ++q)
-        if (j0 + q < TL.ncols) {
-          if (part)
-            part[(long long)vec * psize + TL.poff + row * TL.ncols + j0 + q] = (double)__uint_as_float(r[q]);
-          else
-            Y[(long long)(TL.row0 + row) * G.r + TL.col0 + j0 + q] = (double)__uint_as_float(r[q]);
-        }
   }
-  if (bad && tid == 0) {
-    // let any MMA still in flight finish (bounded) before the TMEM is released
-    wait_bar(&bar, phase);
-    atomicExch(flag, 1);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  // epilogue: D2 -> Y (FP64) or the partial tile
+  double* Y = yv + (long long)vec * ys + G.yoff;
+  {
+    const int warp = tid >> 5, row = ((warp & 3) << 5) | (tid & 31), wg = warp >> 2;
+    for (int j0 = 8 * wg; j0 < rp; j0 += 16) {
+      uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      // warp-collective load: the condition must be uniform over the CTA (d2 is
+      // thread 0's own bookkeeping; a tile with chunks always issued GEMM2)
+      if (has_work && !bad) {
+        const uint32_t addr = tD2 + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)j0;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7])
+                     : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+      }
+      if (row < TL.nrows)
+        for (int q = 0; q < 8; ++q)
+          if (j0 + q < TL.ncols) {
+            if (part)
+              part[(long long)vec * psize + TL.poff + row * TL.ncols + j0 + q] = (double)__uint_as_float(r[q]);
+            else
+              Y[(long long)(TL.row0 + row) * G.r + TL.col0 + j0 + q] = (double)__uint_as_float(r[q]);
+          }
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tbase));
+  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tbase));
 }
 
-template <int TF32>
-constexpr int tc_smem() {
-  constexpr int ES = TF32 ? 4 : 2;
-  constexpr int mult = TF32 ? 1 : 2;
-  return mult * (TC_M * TC_K1 + TC_N1 * TC_K1 + TC_M * TC_K2 + TC_RMAX * TC_K2) * ES + 1024;
+// ---------------------------------------------------------------------------
+// host planning
+// ---------------------------------------------------------------------------
+Img make_img(int rows, int cols, int es, long long& arena) {
+  Img g;
+  g.off = arena;
+  g.rg = (rows + 7) / 8;
+  g.kb = ((cols * es + 31) / 32) * 32;
+  arena += img_bytes(g);
+  return g;
 }
 
-void build_plan(const TaskList& tl, std::vector<Task>& perm, std::vector<TcTile>& tiles, std::vector<TcChunk>& chunks) {
-  perm.clear();
-  tiles.clear();
-  chunks.clear();
+// products of a group ordered by X block; tiles of 128 rows x 64 columns;
+// chunks of products sharing X with (products x padded tile columns) <= 128
+void build_plan(const TaskList& tl, int es, TcPlan& P, std::vector<ImgJob>& jobs, std::vector<XBlock>& xbs) {
+  std::map<std::tuple<const double*, int, int, int>, Img> imgs;  // (src, trans, rows, cols)
+  std::map<long long, int> xidx;
+  long long arena = 0, xarena = 0;
+  auto image = [&](const double* src, int trans, int rows, int cols) {
+    auto key = std::make_tuple(src, trans, rows, cols);
+    auto it = imgs.find(key);
+    if (it != imgs.end()) return it->second;
+    Img g = make_img(rows, cols, es, arena);
+    imgs[key] = g;
+    jobs.push_back({src, rows, cols, trans, g});
+    return g;
+  };
+  P.tasks_h.clear();
+  P.tiles_h.clear();
+  P.chunks_h.clear();
   for (int g = 0; g < (int)tl.groups.size(); ++g) {
     const Group& G = tl.groups[g];
-    // tasks of the group ordered by (kind, X block)
     std::vector<int> idx;
     for (int t = G.t0; t < G.t1; ++t) idx.push_back(t);
-    auto kind = [&](int t) { return (tl.tasks[t].flags & TF_RI) ? 1 : 0; };
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
-      int ka = kind(a), kb = kind(b);
-      if (ka != kb) return ka < kb;
-      return (size_t)tl.tasks[a].X < (size_t)tl.tasks[b].X;
-    });
-    const int base = (int)perm.size();
-    for (int t : idx) perm.push_back(tl.tasks[t]);
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int a, int b) { return (size_t)tl.tasks[a].X < (size_t)tl.tasks[b].X; });
+    const int base = (int)P.tasks_h.size();
+    for (int t : idx) {
+      const Task& k = tl.tasks[t];
+      TcTask c;
+      c.alpha = (float)k.alpha;
+      c.m = k.m;
+      c.n = k.n;
+      // op(L): q x m ; op(R): r x n ; identities become identity images
+      c.L = (k.flags & TF_LI) ? image(nullptr, 0, k.q, k.m) : image(k.L, (k.flags & TF_LT) ? 1 : 0, k.q, k.m);
+      c.R = (k.flags & TF_RI) ? image(nullptr, 0, k.r, k.n) : image(k.R, (k.flags & TF_RT) ? 1 : 0, k.r, k.n);
+      const long long xo = (long long)(size_t)k.X;
+      auto it = xidx.find(xo);
+      if (it == xidx.end()) {
+        XBlock B;
+        B.src = xo;
+        B.m = k.m;
+        B.n = k.n;
+        B.img = make_img(k.m, k.n, es, xarena);
+        xidx[xo] = (int)xbs.size();
+        xbs.push_back(B);
+        c.xb = (int)xbs.size() - 1;
+      } else {
+        c.xb = it->second;
+      }
+      P.tasks_h.push_back(c);
+    }
+    const int nt = (int)idx.size();
     for (int r0 = 0; r0 < G.q; r0 += TC_M)
-      for (int c0 = 0; c0 < G.r; c0 += TC_RMAX) {
+      for (int c0 = 0; c0 < G.r; c0 += TC_NC) {
         TcTile T;
         T.g = g;
         T.row0 = r0;
         T.col0 = c0;
         T.nrows = std::min(TC_M, G.q - r0);
-        T.ncols = std::min(TC_RMAX, G.r - c0);
-        T.c0 = (int)chunks.size();
-        const int rpad = (T.ncols + 15) & ~15;
+        T.ncols = std::min(TC_NC, G.r - c0);
+        T.c0 = (int)P.chunks_h.size();
+        const int rp = (T.ncols + 15) & ~15;
+        const int cap = std::max(1, TC_M / rp);
         int i = 0;
-        const int nt = (int)idx.size();
         while (i < nt) {
-          const Task& a = perm[base + i];
-          const int kd = (a.flags & TF_RI) ? 1 : 0;
-          const int mc16 = ((std::min(a.m, TC_M) + 15) & ~15);
-          int cap = TC_K2 / mc16;
-          if (kd == 0) cap = std::min(cap, TC_N1 / rpad);
-          cap = std::max(cap, 1);
+          const TcTask& a = P.tasks_h[base + i];
           int j = i + 1;
-          while (j < nt && j - i < cap) {
-            const Task& b = perm[base + j];
-            const int kb = (b.flags & TF_RI) ? 1 : 0;
-            if (kb != kd || (kd == 0 && b.X != a.X) || b.m != a.m) break;
-            ++j;
-          }
-          TcChunk C;
-          C.t0 = base + i;
-          C.t1 = base + j;
-          C.kind = kd;
-          C.pad = 0;
-          chunks.push_back(C);
+          while (j < nt && j - i < cap && P.tasks_h[base + j].xb == a.xb) ++j;
+          P.chunks_h.push_back({base + i, base + j});
           i = j;
         }
-        T.c1 = (int)chunks.size();
+        T.c1 = (int)P.chunks_h.size();
         T.poff = -1;
-        tiles.push_back(T);
+        P.tiles_h.push_back(T);
       }
   }
+  P.ops_bytes = arena;
+  P.x_bytes = xarena;
 }
 
 // cut tiles whose chunk lists are long into pieces of similar cost (each piece
 // accumulates its own TMEM tile and writes a partial tile; the pieces are
 // summed in order afterwards), so the CTAs of one launch finish together
-void split_plan(const TaskList& tl, const std::vector<Task>& perm, std::vector<TcTile>& tiles,
-                const std::vector<TcChunk>& chunks, std::vector<SplitRed>& reds, long long& psize, int sms) {
-  auto ccost = [&](const TcChunk& C) {
-    double s = 4.0e4;  // fixed cost of one chunk (staging passes and two MMA round trips)
-    for (int t = C.t0; t < C.t1; ++t) {
-      const Task& k = perm[t];
-      s += 2.0 * k.m * k.n * std::min(k.r, TC_RMAX) + 2.0 * std::min(k.q, TC_M) * k.m * std::min(k.r, TC_RMAX);
-    }
+void split_plan(const std::vector<TcTask>& tasks, std::vector<TcTile>& tiles, const std::vector<TcChunk>& chunks,
+                std::vector<SplitRed>& reds, long long& psize, int sms, double rounds) {
+  auto ccost = [&](const TcChunk& C, const TcTile& T) {
+    double s = 1.5e4;  // fixed cost of one chunk (copies, T pass, barriers)
+    const TcTask& a = tasks[C.t0];
+    const int p = C.t1 - C.t0;
+    const int rp = (T.ncols + 15) & ~15;
+    const double mm = ((a.m + 15) / 16) * 16.0, nn = ((a.n + 15) / 16) * 16.0;
+    s += 2.0 * TC_M * mm * nn + p * 2.0 * TC_M * mm * rp;
     return s;
   };
   std::vector<double> tcost(tiles.size(), 0.0);
   double tot = 0;
   for (size_t i = 0; i < tiles.size(); ++i) {
-    for (int c = tiles[i].c0; c < tiles[i].c1; ++c) tcost[i] += ccost(chunks[c]);
+    for (int c = tiles[i].c0; c < tiles[i].c1; ++c) tcost[i] += ccost(chunks[c], tiles[i]);
     tot += tcost[i];
   }
-  const double target = std::max(tot / (2.0 * sms * 2.0), 1.0);
+  const double target = std::max(tot / (2.0 * sms * rounds), 1.0);
   std::vector<TcTile> out;
   psize = 0;
   reds.clear();
@@ -440,7 +716,7 @@ void split_plan(const TaskList& tl, const std::vector<Task>& perm, std::vector<T
     int start = T.c0, made = 0;
     double acc = 0;
     for (int c = T.c0; c < T.c1 && made < ns - 1; ++c) {
-      acc += ccost(chunks[c]);
+      acc += ccost(chunks[c], T);
       if (acc >= tcost[i] * (made + 1) / ns) {
         TcTile p = T;
         p.c0 = start;
@@ -462,7 +738,116 @@ void split_plan(const TaskList& tl, const std::vector<Task>& perm, std::vector<T
     reds.push_back(R);
   }
   tiles.swap(out);
-  (void)tl;
+}
+
+// Walk every tile piece the way k_tasks_tc does and check each bulk copy and
+// operand range against its image and its shared-memory region; a plan that
+// fails is never launched.
+bool check_plan(const TcPlan& P, const std::vector<TcTile>& tiles, const std::vector<XBlock>& xbs, int es,
+                std::string& why) {
+  const int ns = es == 2 ? 2 : 1;
+  const long long A1 = TC_M * CH_BYTES, B1 = TC_MC * CH_BYTES, CB2 = TC_M * CH_BYTES;
+  const long long B2 = (long long)TC_MC * es / CH_BYTES * CB2, A2 = TC_M * CH_BYTES;
+  auto inside = [&](const Img& g, long long off, long long bytes, long long arena) {
+    return off >= g.off && bytes >= 0 && off + bytes <= g.off + img_bytes(g) && g.off + img_bytes(g) <= arena &&
+           off % 16 == 0 && bytes % 16 == 0;
+  };
+  for (const TcTile& T : tiles) {
+    const int rp = (T.ncols + 15) & ~15;
+    if (T.col0 % 64 || T.row0 % TC_M || rp > TC_NC) {
+      why = "tile shape";
+      return false;
+    }
+    for (int c = T.c0; c < T.c1; ++c) {
+      const TcChunk& C = P.chunks_h[c];
+      const int pc = C.t1 - C.t0;
+      if (pc < 1 || pc * rp > TC_M || pc > TC_M / 16) {
+        why = "chunk capacity";
+        return false;
+      }
+      const TcTask& t0 = P.tasks_h[C.t0];
+      const XBlock& XB = xbs[t0.xb];
+      for (int t = C.t0; t < C.t1; ++t) {
+        const TcTask& k = P.tasks_h[t];
+        if (k.xb != t0.xb || k.m != XB.m || k.n != XB.n || k.R.kb != XB.img.kb ||
+            k.L.kb != ((XB.m * es + 31) / 32) * 32 || k.R.rg * 8 < T.col0 + 1 || k.L.rg * 8 < T.row0 + 1) {
+          why = "operand shapes";
+          return false;
+        }
+      }
+      for (int m0 = 0; m0 < XB.m; m0 += TC_MC) {
+        const int mc = std::min(TC_MC, XB.m - m0), mc16 = (mc + 15) & ~15;
+        const int nch = (XB.img.kb + CH_BYTES - 1) / CH_BYTES;
+        const int xg0 = m0 / 8, xng = std::min(mc16 / 8, XB.img.rg - xg0);
+        for (int kc = 0; kc < nch; ++kc) {
+          const int w = chunk_w(XB.img, kc);
+          if (w <= 0 || w % 32) {
+            why = "chunk width";
+            return false;
+          }
+          const long long rowb = (w / 16) * 128;
+          if (xng > 0 && (!inside(XB.img, chunk_off(XB.img, kc) + xg0 * rowb, xng * rowb, P.x_bytes) ||
+                          xng * rowb > B1)) {
+            why = "input image copy";
+            return false;
+          }
+          for (int t = C.t0; t < C.t1; ++t) {
+            const Img& R = P.tasks_h[t].R;
+            const int ng = std::min(rp / 8, R.rg - T.col0 / 8);
+            const long long dst = (long long)((t - C.t0) * rp / 8) * rowb;
+            if (ng > 0 && (chunk_w(R, kc) != w || !inside(R, chunk_off(R, kc) + (T.col0 / 8) * rowb, ng * rowb,
+                                                          P.ops_bytes) ||
+                           dst + ng * rowb > A1)) {
+              why = "operator image copy (GEMM1)";
+              return false;
+            }
+          }
+          if (16 * rowb > A1 || (mc16 / 8) * rowb > B1) {
+            why = "GEMM1 operand extent";
+            return false;
+          }
+        }
+        const int nk2 = mc16 * es / 32, nch2 = (mc16 * es + CH_BYTES - 1) / CH_BYTES;
+        if ((long long)nch2 * CB2 > B2) {
+          why = "T pass extent";
+          return false;
+        }
+        for (int t = C.t0; t < C.t1; ++t) {
+          const Img& Lm = P.tasks_h[t].L;
+          const int lg0 = T.row0 / 8, lng = std::min(TC_M / 8, Lm.rg - lg0);
+          for (int c2 = 0; c2 < nch2; ++c2) {
+            const int lc = (m0 * es) / CH_BYTES + c2;
+            const int w = chunk_w(Lm, lc);
+            if (w <= 0 || w % 32) {
+              why = "operator chunk";
+              return false;
+            }
+            const long long rowb = (w / 16) * 128;
+            const int ks_here = std::min((int)(w / 32), nk2 - c2 * (CH_BYTES / 32));
+            if (lng <= 0 || !inside(Lm, chunk_off(Lm, lc) + lg0 * rowb, lng * rowb, P.ops_bytes) ||
+                lng * rowb > A2 || ks_here <= 0) {
+              why = "operator image copy (GEMM2)";
+              return false;
+            }
+          }
+        }
+      }
+    }
+  }
+  (void)ns;
+  return true;
+}
+
+template <class T>
+T* upload_vec(CudaBackend& be, const std::vector<T>& v, bool& ok) {
+  T* p = nullptr;
+  if (cudaMalloc(&p, sizeof(T) * std::max<size_t>(v.size(), 1)) != cudaSuccess) {
+    cudaGetLastError();
+    ok = false;
+    return nullptr;
+  }
+  if (!v.empty()) cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, be.stream());
+  return p;
 }
 
 }  // namespace
@@ -472,101 +857,192 @@ void launch_reduce_splits(CudaBackend& be, const SplitRed* reds, int nreds, cons
 
 void release_tc_plan(void* p);
 
-void launch_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, const double* xv, double* yv, int nvec,
-                     long long xs, long long ys, int precision) {
+bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec, int variant, int precision) {
   TcPlan* plan = (TcPlan*)d.tc;
-  if (!plan || d.tc_gen != tl.gen) {
-    if (plan) {
-      cudaStreamSynchronize(be.stream());
-      release_tc_plan(plan);
-    }
-    std::vector<Task> perm;
-    std::vector<TcTile> tiles;
-    std::vector<TcChunk> chunks;
-    std::vector<SplitRed> reds;
-    long long psize = 0;
-    int sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, be.device());
-    build_plan(tl, perm, tiles, chunks);
-    split_plan(tl, perm, tiles, chunks, reds, psize, sms);
+  if (plan && (d.tc_gen != tl.gen || plan->precision != precision)) {
+    cudaStreamSynchronize(be.stream());
+    release_tc_plan(plan);
+    d.tc = nullptr;
+    plan = nullptr;
+  }
+  const int es = precision == TNS_TF32 ? 4 : 2;
+  if (!plan) {
+    for (const Task& t : tl.tasks)
+      if (!(t.flags & TF_XV) || (t.flags & (TF_XT | TF_XI))) {
+        be.note(cudaErrorInvalidValue, "tensor-core form: work list is not an H_eff*psi list");
+        return false;
+      }
     plan = new TcPlan();
-    bool ok = cudaMalloc(&plan->tasks, sizeof(Task) * std::max<size_t>(perm.size(), 1)) == cudaSuccess &&
-              cudaMalloc(&plan->tiles, sizeof(TcTile) * std::max<size_t>(tiles.size(), 1)) == cudaSuccess &&
-              cudaMalloc(&plan->chunks, sizeof(TcChunk) * std::max<size_t>(chunks.size(), 1)) == cudaSuccess &&
-              cudaMalloc(&plan->flag, sizeof(int)) == cudaSuccess &&
-              cudaMalloc(&plan->reds, sizeof(SplitRed) * std::max<size_t>(reds.size(), 1)) == cudaSuccess;
+    plan->precision = precision;
+    cudaDeviceGetAttribute(&plan->sms, cudaDevAttrMultiProcessorCount, be.device());
+    std::vector<ImgJob> jobs;
+    std::vector<XBlock> xbs;
+    build_plan(tl, es, *plan, jobs, xbs);
+    bool ok = true;
+    plan->tasks = upload_vec(be, plan->tasks_h, ok);
+    plan->chunks = upload_vec(be, plan->chunks_h, ok);
+    plan->xblocks = upload_vec(be, xbs, ok);
+    plan->nxb = (int)xbs.size();
+    plan->xbs_h = xbs;
+    ImgJob* djobs = upload_vec(be, jobs, ok);
+    ok = ok && cudaMalloc(&plan->flag, 8 * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc(&plan->ops_hi, std::max<long long>(plan->ops_bytes, 16)) == cudaSuccess;
+    if (es == 2) ok = ok && cudaMalloc(&plan->ops_lo, std::max<long long>(plan->ops_bytes, 16)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
-      be.note(cudaErrorMemoryAllocation, "tensor-core plan");
+      if (djobs) {
+        cudaStreamSynchronize(be.stream());
+        cudaFree(djobs);
+      }
+      be.note(cudaErrorMemoryAllocation, "tensor-core plan / operand images");
       release_tc_plan(plan);
-      d.tc = nullptr;
-      return;
+      return false;
     }
-    if (!perm.empty()) cudaMemcpyAsync(plan->tasks, perm.data(), sizeof(Task) * perm.size(), cudaMemcpyHostToDevice, be.stream());
-    if (!tiles.empty()) cudaMemcpyAsync(plan->tiles, tiles.data(), sizeof(TcTile) * tiles.size(), cudaMemcpyHostToDevice, be.stream());
-    if (!chunks.empty()) cudaMemcpyAsync(plan->chunks, chunks.data(), sizeof(TcChunk) * chunks.size(), cudaMemcpyHostToDevice, be.stream());
-    if (!reds.empty()) cudaMemcpyAsync(plan->reds, reds.data(), sizeof(SplitRed) * reds.size(), cudaMemcpyHostToDevice, be.stream());
-    plan->ntiles = (int)tiles.size();
-    plan->nreds = (int)reds.size();
-    plan->psize = psize;
+    if (!jobs.empty()) {
+      if (es == 4)
+        k_img_ops<1><<<(unsigned)jobs.size(), 256, 0, be.stream()>>>(djobs, plan->ops_hi, nullptr);
+      else
+        k_img_ops<0><<<(unsigned)jobs.size(), 256, 0, be.stream()>>>(djobs, plan->ops_hi, plan->ops_lo);
+      be.launches++;
+      be.note(cudaGetLastError(), "operand images");
+    }
+    be.note(cudaStreamSynchronize(be.stream()), "operand images");
+    cudaFree(djobs);
     d.tc = plan;
     d.tc_gen = tl.gen;
-    be.note(cudaStreamSynchronize(be.stream()), "tensor-core plan upload");
   }
-  if (plan->ntiles == 0) return;
-  if (plan->psize > 0 && plan->part_nvec < nvec) {
-    if (plan->part) {
+  if (plan->x_nvec < nvec) {
+    if (plan->x_hi) {
       cudaStreamSynchronize(be.stream());
-      cudaFree(plan->part);
+      cudaFree(plan->x_hi);
+      if (plan->x_lo) cudaFree(plan->x_lo);
     }
-    plan->part = nullptr;
-    plan->part_nvec = 0;
-    if (cudaMalloc(&plan->part, sizeof(double) * plan->psize * nvec) != cudaSuccess) {
+    plan->x_hi = plan->x_lo = nullptr;
+    plan->x_nvec = 0;
+    const size_t xb = (size_t)std::max<long long>(plan->x_bytes, 16) * nvec;
+    bool ok = cudaMalloc(&plan->x_hi, xb) == cudaSuccess;
+    if (es == 2) ok = ok && cudaMalloc(&plan->x_lo, xb) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      be.note(cudaErrorMemoryAllocation, "tensor-core input images");
+      return false;
+    }
+    plan->x_nvec = nvec;
+  }
+  TcVariant& V = plan->var[variant];
+  if (!V.planned) {
+    std::vector<TcTile> tiles = plan->tiles_h;
+    std::vector<SplitRed> reds;
+    long long psize = 0;
+    split_plan(plan->tasks_h, tiles, plan->chunks_h, reds, psize, plan->sms, kRounds[variant]);
+    std::string why;
+    if (!check_plan(*plan, tiles, plan->xbs_h, es, why)) {
+      be.note(cudaErrorInvalidValue, ("tensor-core plan check failed: " + why).c_str());
+      return false;
+    }
+    bool ok = true;
+    V.tiles = upload_vec(be, tiles, ok);
+    V.reds = upload_vec(be, reds, ok);
+    if (!ok) {
+      be.note(cudaErrorMemoryAllocation, "tensor-core schedule");
+      return false;
+    }
+    V.ntiles = (int)tiles.size();
+    V.nreds = (int)reds.size();
+    V.psize = psize;
+    V.planned = true;
+    be.note(cudaStreamSynchronize(be.stream()), "tensor-core schedule upload");
+  }
+  if (V.psize > 0 && V.part_nvec < nvec) {
+    if (V.part) {
+      cudaStreamSynchronize(be.stream());
+      cudaFree(V.part);
+    }
+    V.part = nullptr;
+    V.part_nvec = 0;
+    if (cudaMalloc(&V.part, sizeof(double) * V.psize * nvec) != cudaSuccess) {
       cudaGetLastError();
       be.note(cudaErrorMemoryAllocation, "tensor-core partial tiles");
-      plan->part = nullptr;
-      return;
+      return false;
     }
-    plan->part_nvec = nvec;
+    V.part_nvec = nvec;
   }
-  cudaMemsetAsync(plan->flag, 0, sizeof(int), be.stream());
-  dim3 grid(plan->ntiles, nvec);
-  if (precision == 1) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_tasks_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<1>());
-      attr = true;
-    }
-    k_tasks_tc<1><<<grid, TC_NT, tc_smem<1>(), be.stream()>>>(plan->tasks, d.groups, plan->tiles, plan->chunks, xv,
-                                                             yv, xs, ys, plan->flag, plan->part, plan->psize);
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_tasks_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<0>());
-      attr = true;
-    }
-    k_tasks_tc<0><<<grid, TC_NT, tc_smem<0>(), be.stream()>>>(plan->tasks, d.groups, plan->tiles, plan->chunks, xv,
-                                                             yv, xs, ys, plan->flag, plan->part, plan->psize);
+  // kernel attributes once, outside any stream capture
+  static bool attr[2] = {false, false};
+  if (!attr[0]) {
+    cudaFuncSetAttribute(k_tasks_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<0>::total);
+    attr[0] = true;
   }
+  if (!attr[1]) {
+    cudaFuncSetAttribute(k_tasks_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<1>::total);
+    attr[1] = true;
+  }
+  return true;
+}
+
+void enqueue_tasks_tc(CudaBackend& be, DevList& d, const double* xv, double* yv, int nvec, long long xs,
+                      long long ys, int precision, int variant) {
+  TcPlan* plan = (TcPlan*)d.tc;
+  if (!plan) return;
+  TcVariant& V = plan->var[variant];
+  if (V.ntiles == 0) return;
+  be.note(cudaMemsetAsync(plan->flag, 0, 8 * sizeof(int), be.stream()), "tensor-core flag");
+  if (plan->nxb > 0) {
+    dim3 gx(plan->nxb, nvec);
+    if (precision == TNS_TF32)
+      k_img_x<1><<<gx, 256, 0, be.stream()>>>(plan->xblocks, xv, xs, plan->x_hi, nullptr, plan->x_bytes);
+    else
+      k_img_x<0><<<gx, 256, 0, be.stream()>>>(plan->xblocks, xv, xs, plan->x_hi, plan->x_lo, plan->x_bytes);
+    be.launches++;
+    be.note(cudaGetLastError(), "input images");
+  }
+  dim3 grid(V.ntiles, nvec);
+  if (precision == TNS_TF32)
+    k_tasks_tc<1><<<grid, TC_NT, TcSmem<1>::total, be.stream()>>>(plan->tasks, d.groups, V.tiles, plan->chunks,
+                                                                   plan->ops_hi, plan->ops_lo, plan->x_hi, plan->x_lo,
+                                                                   plan->x_bytes, plan->xblocks, yv, ys, plan->flag,
+                                                                   V.part, V.psize);
+  else
+    k_tasks_tc<0><<<grid, TC_NT, TcSmem<0>::total, be.stream()>>>(plan->tasks, d.groups, V.tiles, plan->chunks,
+                                                                   plan->ops_hi, plan->ops_lo, plan->x_hi, plan->x_lo,
+                                                                   plan->x_bytes, plan->xblocks, yv, ys, plan->flag,
+                                                                   V.part, V.psize);
   be.launches++;
   be.note(cudaGetLastError(), "k_tasks_tc");
-  if (plan->nreds > 0)
-    launch_reduce_splits(be, plan->reds, plan->nreds, d.groups, plan->part, plan->psize, yv, ys, nvec);
-  int h = 0;
-  cudaMemcpyAsync(&h, plan->flag, sizeof(int), cudaMemcpyDeviceToHost, be.stream());
+  if (V.nreds > 0) launch_reduce_splits(be, V.reds, V.nreds, d.groups, V.part, V.psize, yv, ys, nvec);
+}
+
+void check_tasks_tc(CudaBackend& be, DevList& d) {
+  TcPlan* plan = (TcPlan*)d.tc;
+  if (!plan) return;
+  int h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  cudaMemcpyAsync(h, plan->flag, sizeof(h), cudaMemcpyDeviceToHost, be.stream());
   be.note(cudaStreamSynchronize(be.stream()), "k_tasks_tc");
-  if (h) be.note(cudaErrorLaunchTimeout, "k_tasks_tc: MMA completion wait timed out");
+  if (h[0]) {
+    char msg[256];
+    std::snprintf(msg, sizeof(msg),
+                  "k_tasks_tc: wait timed out (tile piece %d, barrier %d, chunk %d, row offset %d, step %d, phase %d)",
+                  h[1], h[2], h[3], h[4], h[5], h[6]);
+    be.note(cudaErrorLaunchTimeout, msg);
+  }
 }
 
 void release_tc_plan(void* p) {
   TcPlan* plan = (TcPlan*)p;
   if (!plan) return;
-  if (plan->reds) cudaFree(plan->reds);
-  if (plan->part) cudaFree(plan->part);
-  cudaFree(plan->tasks);
-  cudaFree(plan->tiles);
-  cudaFree(plan->chunks);
-  cudaFree(plan->flag);
+  for (TcVariant& V : plan->var) {
+    if (V.tiles) cudaFree(V.tiles);
+    if (V.reds) cudaFree(V.reds);
+    if (V.part) cudaFree(V.part);
+  }
+  if (plan->tasks) cudaFree(plan->tasks);
+  if (plan->chunks) cudaFree(plan->chunks);
+  if (plan->xblocks) cudaFree(plan->xblocks);
+  if (plan->flag) cudaFree(plan->flag);
+  if (plan->ops_hi) cudaFree(plan->ops_hi);
+  if (plan->ops_lo) cudaFree(plan->ops_lo);
+  if (plan->x_hi) cudaFree(plan->x_hi);
+  if (plan->x_lo) cudaFree(plan->x_lo);
   delete plan;
 }
 

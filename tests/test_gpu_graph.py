@@ -1,0 +1,112 @@
+"""Batched form: online schedule autotuning and CUDA-graph replay of the
+H_eff*psi launch sequence.  Every schedule variant computes the same products
+(only the split-K summation order differs); the graph replay of a schedule is
+bitwise identical to its direct launches."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dmrg as O3
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2305_05581_gb300 import (Context, DEFAULT_LIB, TNS_BF16X3, TNS_FP64,  # noqa: E402
+                                    blocks_to_vector)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(DEFAULT_LIB):
+        from paper_2305_05581_gb300 import build as b
+        b.build()
+
+
+def _ctx(**env):
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        return Context(device=0, stream=torch.cuda.current_stream().cuda_stream)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
+
+
+CASE = (10, 10, 0, 90, 4)
+
+
+def _load(ctx, seed=21):
+    N, n, s2, D, k = CASE
+    h, v = synth.integrals(N, 3.0, seed)
+    bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=seed)
+    ctx.load_integrals(h, v)
+    ctx.mps_import(N, n, s2, D, bonds, sites)
+    ctx.build_env(k)
+    return h, v, bonds, sites
+
+
+def _apply(ctx, x, nvec, prec, times):
+    k = CASE[4]
+    out = []
+    for _ in range(times):
+        y = torch.empty_like(x)
+        ctx.heff_apply_ptr(k, x.data_ptr(), y.data_ptr(), nvec, prec)
+        out.append(y)
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [(TNS_FP64, 1e-13), (TNS_BF16X3, 2e-5)])
+@pytest.mark.parametrize("nvec", [1, 4])
+def test_autotuned_graph_replays_match_fixed_schedule(prec, tol, nvec):
+    ref_ctx = _ctx(TNS_AUTOTUNE="0", TNS_GRAPHS="0")
+    _load(ref_ctx)
+    _, length = ref_ctx.psi_layout(CASE[4])
+    g = torch.Generator(device="cuda").manual_seed(3)
+    x = torch.randn(nvec * length, device="cuda", dtype=torch.float64, generator=g)
+    ref = _apply(ref_ctx, x, nvec, prec, 1)[0]
+    ctx = _ctx()
+    _load(ctx)
+    ys = _apply(ctx, x, nvec, prec, 7)   # 3 tuning products, then capture and replays
+    scale = float(torch.linalg.norm(ref))
+    for y in ys:
+        assert float(torch.linalg.norm(y - ref)) <= tol * scale
+    for y in ys[4:]:
+        assert torch.equal(y, ys[3])
+
+
+@pytest.mark.parametrize("prec", [TNS_FP64, TNS_BF16X3])
+def test_graph_replay_is_bitwise_equal_to_direct_launch(prec):
+    direct = _ctx(TNS_AUTOTUNE="0", TNS_GRAPHS="0")
+    graphed = _ctx(TNS_AUTOTUNE="0")
+    _load(direct)
+    _load(graphed)
+    _, length = direct.psi_layout(CASE[4])
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(2 * length, device="cuda", dtype=torch.float64, generator=g)
+    a = _apply(direct, x, 2, prec, 2)
+    b = _apply(graphed, x, 2, prec, 3)
+    assert torch.equal(a[0], a[1])
+    for y in b:
+        assert torch.equal(y, a[0])
+
+
+def test_graph_replay_matches_oracle():
+    ctx = _ctx()
+    h, v, bonds, sites = _load(ctx, seed=8)
+    N, n, s2, D, k = CASE
+    desc, length = ctx.psi_layout(k)
+    keys = synth.psi_keys(bonds, N, n, s2, k)
+    X = synth.random_psi(keys, seed=2)[0]
+    x = torch.tensor(blocks_to_vector(desc, length, X), device="cuda")
+    ys = _apply(ctx, x, 1, TNS_FP64, 6)
+    ref = blocks_to_vector(desc, length, O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2).apply(X))
+    for y in ys:
+        assert np.linalg.norm(y.cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref)

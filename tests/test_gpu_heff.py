@@ -24,8 +24,16 @@ def built():
         b.build()
 
 
-def _ctx():
-    return Context(device=0, stream=torch.cuda.current_stream().cuda_stream)
+def _ctx(fixed_schedule=False):
+    """Context on the torch stream; fixed_schedule turns the online schedule
+    autotuner off (one schedule throughout: bitwise-reproducible results)."""
+    if not fixed_schedule:
+        return Context(device=0, stream=torch.cuda.current_stream().cuda_stream)
+    os.environ["TNS_AUTOTUNE"] = "0"
+    try:
+        return Context(device=0, stream=torch.cuda.current_stream().cuda_stream)
+    finally:
+        del os.environ["TNS_AUTOTUNE"]
 
 
 def _rel(a, b):
@@ -91,7 +99,7 @@ def test_multivector_and_determinism():
     bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=3)
     keys = synth.psi_keys(bonds, N, n, s2, k)
     Xs = synth.random_psi(keys, seed=4, nvec=3)
-    ctx = _ctx()
+    ctx = _ctx(fixed_schedule=True)
     ctx.load_integrals(h, v)
     ctx.mps_import(N, n, s2, D, bonds, sites)
     ctx.build_env(k)

@@ -30,14 +30,22 @@ def built():
         b.build()
 
 
-def _ctx():
-    return Context(device=0, stream=torch.cuda.current_stream().cuda_stream)
+def _ctx(fixed_schedule=False):
+    """Context on the torch stream; fixed_schedule turns the online schedule
+    autotuner off (one schedule throughout: bitwise-reproducible results)."""
+    if not fixed_schedule:
+        return Context(device=0, stream=torch.cuda.current_stream().cuda_stream)
+    os.environ["TNS_AUTOTUNE"] = "0"
+    try:
+        return Context(device=0, stream=torch.cuda.current_stream().cuda_stream)
+    finally:
+        del os.environ["TNS_AUTOTUNE"]
 
 
-def _setup(N, n, s2, D, k, seed):
+def _setup(N, n, s2, D, k, seed, fixed_schedule=False):
     h, v = synth.integrals(N, 3.0, seed)
     bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=seed + 1)
-    ctx = _ctx()
+    ctx = _ctx(fixed_schedule)
     ctx.load_integrals(h, v)
     ctx.mps_import(N, n, s2, D, bonds, sites)
     ctx.build_env(k)
@@ -118,7 +126,7 @@ def test_sweep_bf16x3_reaches_fci_n8():
 def test_four_vectors_in_one_launch(prec):
     """A block of four Davidson vectors in one call equals four single calls."""
     N, n, s2, D, k = 8, 8, 0, 60, 3
-    ctx, h, v, bonds, sites = _setup(N, n, s2, D, k, 77)
+    ctx, h, v, bonds, sites = _setup(N, n, s2, D, k, 77, fixed_schedule=True)
     desc, length = ctx.psi_layout(k)
     g = torch.Generator(device="cuda").manual_seed(9)
     x = torch.randn(4 * length, device="cuda", dtype=torch.float64, generator=g)
@@ -129,3 +137,30 @@ def test_four_vectors_in_one_launch(prec):
         ctx.heff_apply_ptr(k, x[j * length:].data_ptr(), y1[j * length:].data_ptr(), 1, prec)
     torch.cuda.synchronize()
     assert torch.equal(y4, y1)
+
+
+@pytest.mark.parametrize("prec", [TNS_FP64, TNS_BF16X3])
+def test_block_davidson_sweep_reaches_fci_n8(prec):
+    """Block Davidson (four corrections per iteration, one batched product
+    launch per block): four sweeps at exact D reach FCI."""
+    c = synth.WORKLOADS["n8"]
+    h, v = synth.integrals(c["N"], c["lam"], c["seed"])
+    ctx = _ctx()
+    ctx.load_integrals(h, v)
+    ctx.mps_init(c["N"], c["n_elec"], c["two_sz"], c["D"], seed=1)
+    e, st = ctx.sweep(4, c["D"], tol=1e-8, max_iter=400, precision=prec, block=4)
+    assert abs(e - fci_energy(h, v, c["n_elec"], c["two_sz"])) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [TNS_FP64, TNS_BF16X3])
+def test_block_davidson_step_matches_single_vector(prec):
+    """One two-site step on a random MPS: block-4 and single-vector Davidson
+    reach the same eigenvalue of the same H_eff (shared input)."""
+    N, n, s2, D, k = 10, 10, 0, 80, 4
+    out = []
+    for block in (1, 4):
+        ctx, h, v, bonds, sites = _setup(N, n, s2, D, k, 55)
+        st = ctx.step(k, True, D, tol=1e-9, max_iter=400, precision=prec, block=block)
+        assert st.converged
+        out.append(st.energy)
+    assert abs(out[0] - out[1]) < 1e-9
