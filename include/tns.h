@@ -184,6 +184,24 @@ int tns_heff_diag_noalloc(tns_ctx* ctx, int site, double* diag);
 int tns_davidson(tns_ctx* ctx, int site, double* X, double tol, int max_iter, int precision,
                  double* energy, int* iters);
 
+/* Differentiation form, integral gradients (not in the paper): dE/dh and
+ * dE/dv of E = <psi|H_eff|psi> / <psi|psi> at step (site, site+1) with the
+ * MPS isometries fixed -- by Hellmann-Feynman the 1- and 2-particle reduced
+ * density matrices of the state the MPS and psi represent, for the
+ * Hamiltonian of Eq. (1) written as sum h_ij E_ij + 1/2 sum (ij|kl) e_ijkl.
+ * Computed by reverse mode through the products of Eq. (2) and through the
+ * renormalisation chain (blocking, rotation, partial sums) of both blocks
+ * down to the empty blocks.
+ *  - psi: DEVICE, layout of tns_psi_layout(site), need not be normalised.
+ *  - gamma: HOST N*N, gamma[i*N+j] = dE/dh_ij symmetrised over (i, j)
+ *    = sum_s <a+_is a_js>.
+ *  - Gamma: HOST N^4 or NULL, Gamma[((i*N+j)*N+k)*N+l] = 2 dE/d(ij|kl)
+ *    averaged over the eight index permutations that leave (ij|kl)
+ *    unchanged (only these orbit sums are defined for integrals with the
+ *    8-fold symmetry) = the orbit average of sum_st <a+_is a+_kt a_lt a_js>.
+ * Requires tns_build_env(site).  FP64.  Synchronous. */
+int tns_rdm(tns_ctx* ctx, int site, const double* psi, double* gamma, double* Gamma);
+
 /* Batched dense symmetric eigen-decomposition, the solver the truncation uses
  * on each middle-bond sector's reduced density matrix (the SVD hand-off of the
  * two-site step, Sec. III.A; Householder tridiagonalisation then implicit QR

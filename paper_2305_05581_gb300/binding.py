@@ -22,7 +22,7 @@ DEFAULT_LIB = os.path.join(HERE, "libtns.so")
 SYMBOLS = ["create", "destroy", "last_error", "load_integrals", "mps_init", "mps_define",
            "mps_set_bond", "mps_set_site", "mps_get_bond", "mps_get_site", "build_env",
            "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops", "step", "psi_guess",
-           "heff_diag_noalloc", "env_arena", "heff_adjoint", "sym_eig"]
+           "heff_diag_noalloc", "env_arena", "heff_adjoint", "sym_eig", "rdm"]
 
 
 class TnsError(RuntimeError):
@@ -87,6 +87,7 @@ def load_library(path: str = DEFAULT_LIB, prefix: str = "tns_"):
         "env_arena": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(vp), llp]),
         "heff_adjoint": (C.c_int, [vp, C.c_int, vp, vp, vp, vp, vp]),
         "sym_eig": (C.c_int, [vp, C.c_int, ip, vp, vp, vp]),
+        "rdm": (C.c_int, [vp, C.c_int, vp, dp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = f(name)
@@ -215,6 +216,15 @@ class Context:
         n = (C.c_int * max(1, len(sizes)))(*sizes)
         self._check(self._fn("sym_eig")(self._h, len(sizes), n, C.c_void_p(a_ptr), C.c_void_p(z_ptr),
                                         C.c_void_p(w_ptr)))
+
+    def rdm_ptr(self, site, psi_ptr: int, N: int, two_body: bool = True):
+        """1-RDM (N x N) and, if two_body, the orbit-averaged 2-RDM (N^4) of the
+        state given by the MPS and psi (pointer in the library's memory space)
+        at step (site, site+1), as dE/dh and 2 dE/dv (tns_rdm)."""
+        g = np.zeros(N * N)
+        G = np.zeros(N ** 4) if two_body else None
+        self._check(self._fn("rdm")(self._h, site, C.c_void_p(psi_ptr), _dptr(g), _dptr(G) if two_body else None))
+        return g.reshape(N, N), (G.reshape(N, N, N, N) if two_body else None)
 
     def heff_flops(self, site):
         f = C.c_double()

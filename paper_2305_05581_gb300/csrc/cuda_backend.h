@@ -96,6 +96,7 @@ class CudaBackend : public Backend {
   void lincomb(const LCList& l) override;
   void run(const TaskList& tl, const double* xv, double* yv, int nvec, long long xs, long long ys,
            int precision) override;
+  void task_values(const TaskList& tl, const double* xv, const double* ybar, double* out) override;
   void sync() override;
   std::string error() override;
 

@@ -1138,10 +1138,19 @@ int Engine::rotate(Side& S, const Catalogue& src, Catalogue& dst, int site, bool
   for (auto& E : S.eops) dst.add_op(E.kind, E.i, E.j, E.dq);
   int rc = alloc_cat(dst, err);
   if (rc) return rc;
+  TaskList tl;
+  rotation_tasks(S, src, dst, site, left, tl, nullptr);
+  tl.nprod = (long long)tl.tasks.size();
+  be_->run(tl, nullptr, dst.d, 1, 0, 0, 0);
+  dst.valid = true;
+  return 0;
+}
+
+void Engine::rotation_tasks(const Side& S, const Catalogue& src, const Catalogue& dst, int site, bool left,
+                            TaskList& tl, std::vector<std::array<int, 3>>* prov) {
   const Site& st = sites_[site];
   const Basis& sb = bonds_[site];        // site tensor left bond
   const Basis& sb1 = bonds_[site + 1];   // site tensor right bond
-  TaskList tl;
   for (size_t ei = 0; ei < S.eops.size(); ++ei) {
     const EOp& E = S.eops[ei];
     const CatOp& o = dst.ops[ei];
@@ -1156,8 +1165,10 @@ int Engine::rotate(Side& S, const Catalogue& src, Catalogue& dst, int site, bool
       g.nrows = g.q;
       g.ncols = g.r;
       g.t0 = (int)tl.tasks.size();
-      for (const auto& db : E.dots) {
-        for (const auto& dt : db.t) {
+      for (size_t di = 0; di < E.dots.size(); ++di) {
+        const DotBlock& db = E.dots[di];
+        for (size_t ti = 0; ti < db.t.size(); ++ti) {
+          const DotTerm& dt = db.t[ti];
           if (left) {
             // new op (q'' <- q) += A^{so}(ql' -> q'')^T  X(ql' <- ql)  A^{si}(ql -> q)
             QN qo = dst.basis.q[qout] - kSiteQN[db.so];
@@ -1183,6 +1194,7 @@ int Engine::rotate(Side& S, const Catalogue& src, Catalogue& dst, int site, bool
             set_order(tk);
             tl.flops += chain_flops(tk);
             tl.tasks.push_back(tk);
+            if (prov) prov->push_back({(int)ei, (int)di, (int)ti});
           } else {
             // new op (Q' <- Q) += B^{so}(Q') X(Q'-so <- Q-si) B^{si}(Q)^T ; Q right counted
             QN Qo = dst.basis.q[qout], Qi = dst.basis.q[qin];
@@ -1211,6 +1223,7 @@ int Engine::rotate(Side& S, const Catalogue& src, Catalogue& dst, int site, bool
             set_order(tk);
             tl.flops += chain_flops(tk);
             tl.tasks.push_back(tk);
+            if (prov) prov->push_back({(int)ei, (int)di, (int)ti});
             (void)sb1;
           }
         }
@@ -1219,10 +1232,6 @@ int Engine::rotate(Side& S, const Catalogue& src, Catalogue& dst, int site, bool
       tl.groups.push_back(g);
     }
   }
-  tl.nprod = (long long)tl.tasks.size();
-  be_->run(tl, nullptr, dst.d, 1, 0, 0, 0);
-  dst.valid = true;
-  return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1336,6 +1345,7 @@ void Engine::build_heff_tasks() {
   const int nqr = Rc.basis.size();
   TaskList& tl = st.heff;
   tl.clear();
+  st.heff_prov.clear();
 
   struct Pair {
     int eL;
@@ -1378,8 +1388,9 @@ void Engine::build_heff_tasks() {
   for (int a = 0; a < nLL; ++a)
     for (int b = 0; b < nLL; ++b) pairs.push_back({eL(K_B, a, b), false, eR(K_Q, a, b), false, 1.0, 0});
 
-  // per output block task buckets
+  // per output block task buckets (and where each coefficient comes from)
   std::vector<std::vector<Task>> bucket(st.psi.size());
+  std::vector<std::vector<std::array<int, 6>>> pbucket(st.psi.size());
   static const DotBlock kIdent[4] = {{0, 0, {{1.0, -1}}}, {1, 1, {{1.0, -1}}}, {2, 2, {{1.0, -1}}}, {3, 3, {{1.0, -1}}}};
 
   for (const Pair& pr : pairs) {
@@ -1389,12 +1400,16 @@ void Engine::build_heff_tasks() {
     else dl = st.L.eops[pr.eL].dots;
     if (pr.eR == -2) dr.assign(kIdent, kIdent + 4);
     else dr = st.R.eops[pr.eR].dots;
-    for (const auto& a : dl) {
+    for (size_t ai = 0; ai < dl.size(); ++ai) {
+      const auto& a = dl[ai];
       int s1o = pr.trL ? a.si : a.so, s1i = pr.trL ? a.so : a.si;
-      for (const auto& b : dr) {
+      for (size_t bi = 0; bi < dr.size(); ++bi) {
+        const auto& b = dr[bi];
         int s2o = pr.trR ? b.si : b.so, s2i = pr.trR ? b.so : b.si;
-        for (const auto& ta : a.t)
-          for (const auto& tb : b.t) {
+        for (size_t tai = 0; tai < a.t.size(); ++tai)
+          for (size_t tbi = 0; tbi < b.t.size(); ++tbi) {
+            const auto& ta = a.t[tai];
+            const auto& tb = b.t[tbi];
             for (int ql = 0; ql < Lb.size(); ++ql) {
               Operand Lo;
               if (ta.expr == -1) {
@@ -1439,6 +1454,8 @@ void Engine::build_heff_tasks() {
                 tk.pad = xb;
                 set_order(tk);
                 bucket[yb].push_back(tk);
+                pbucket[yb].push_back({pr.eL == -2 ? -1 : pr.eL, pr.eL == -2 ? -1 : (int)ai, (int)tai,
+                                       pr.eR == -2 ? -1 : pr.eR, pr.eR == -2 ? -1 : (int)bi, (int)tbi});
               }
             }
           }
@@ -1459,6 +1476,7 @@ void Engine::build_heff_tasks() {
       tl.flops += chain_flops(tk);
       tl.tasks.push_back(tk);
     }
+    for (auto& pv : pbucket[yb]) st.heff_prov.push_back(pv);
     g.t1 = (int)tl.tasks.size();
     tl.groups.push_back(g);
   }
@@ -1737,6 +1755,407 @@ int Engine::heff_adjoint(const double* X, const double* Yb, double* Xb, double* 
   be_->sync();
   for (double* p : {GL, GR, ML, MR})
     if (p) be_->release(p);
+  std::string e = be_->error();
+  if (!e.empty()) {
+    err = e;
+    return -6;
+  }
+  return 0;
+}
+
+
+// ===========================================================================
+// differentiation form: gradient of E = <psi|H_eff|psi>/<psi|psi> with
+// respect to the integrals (1-RDM = dE/dh, 2-RDM = 2 dE/dv), MPS isometries
+// fixed.  Reverse mode: per-product values <Ybar, op(L) op(X) op(R)^T> give
+// the derivatives of the products' coefficients (which are linear in the
+// integrals; Lin records which integrals), operand adjoints carry the
+// gradient of every operator block down the renormalisation chain
+// (rotation O' = U^T O U, partial sums) to the empty blocks.
+// ===========================================================================
+namespace {
+// a used operand: ident ? I : (trans ? stored^T : stored), rows x cols as used
+struct Opd {
+  const double* p;
+  bool ident, trans;
+  int rows, cols;
+};
+Opd opd_T(Opd o) {
+  std::swap(o.rows, o.cols);
+  if (!o.ident) o.trans = !o.trans;
+  return o;
+}
+// product a * A B C^T as a task (A rows x C rows)
+Task mk(double a, const Opd& A, const Opd& B, const Opd& C) {
+  Task t;
+  t.alpha = a;
+  t.L = A.p;
+  t.X = B.p;
+  t.R = C.p;
+  t.q = A.rows;
+  t.m = A.cols;
+  t.n = B.cols;
+  t.r = C.rows;
+  t.flags = (A.ident ? TF_LI : A.trans ? TF_LT : 0) | (B.ident ? TF_XI : B.trans ? TF_XT : 0) |
+            (C.ident ? TF_RI : C.trans ? TF_RT : 0);
+  t.pad = 0;
+  return t;
+}
+
+// gradient buffers mirroring forward arenas; adjoint products grouped by the
+// stored block they write
+struct AdjSink {
+  struct Region {
+    const double* base;
+    long long size;
+    double* grad;
+    std::map<long long, std::pair<std::pair<int, int>, std::vector<Task>>> blocks;
+  };
+  std::vector<Region> regions;
+  void region(const double* base, long long size, double* grad) { regions.push_back({base, size, grad, {}}); }
+  int find(const double* p) const {
+    for (size_t i = 0; i < regions.size(); ++i)
+      if (p >= regions[i].base && p < regions[i].base + regions[i].size) return (int)i;
+    return -1;
+  }
+  void add(const double* stored, int rows, int cols, const Task& t) {
+    const int r = find(stored);
+    if (r < 0) return;
+    auto& e = regions[r].blocks[stored - regions[r].base];
+    e.first = {rows, cols};
+    e.second.push_back(t);
+  }
+  // adjoint of one forward product Y(q x r) += a A B C^T with output gradient Yb
+  void adjoint(const Task& t, const double* xv, const double* Yb) {
+    const Opd A{t.L, (t.flags & TF_LI) != 0, (t.flags & TF_LT) != 0, t.q, t.m};
+    const double* xp = (t.flags & TF_XV) ? xv + (long long)(size_t)t.X : t.X;
+    const Opd B{xp, (t.flags & TF_XI) != 0, (t.flags & TF_XT) != 0, t.m, t.n};
+    const Opd C{t.R, (t.flags & TF_RI) != 0, (t.flags & TF_RT) != 0, t.r, t.n};
+    const Opd Y{Yb, false, false, t.q, t.r};
+    const double a = t.alpha;
+    if (!A.ident && find(A.p) >= 0) {  // dA = Yb C B^T
+      if (!A.trans)
+        add(A.p, t.q, t.m, mk(a, Y, C, B));
+      else
+        add(A.p, t.m, t.q, mk(a, B, opd_T(C), Y));
+    }
+    if (!B.ident && find(B.p) >= 0) {  // dB = A^T Yb C
+      if (!B.trans)
+        add(B.p, t.m, t.n, mk(a, opd_T(A), Y, opd_T(C)));
+      else
+        add(B.p, t.n, t.m, mk(a, opd_T(C), opd_T(Y), opd_T(A)));
+    }
+    if (!C.ident && find(C.p) >= 0) {  // dC = Yb^T A B
+      if (!C.trans)
+        add(C.p, t.r, t.n, mk(a, opd_T(Y), A, opd_T(B)));
+      else
+        add(C.p, t.n, t.r, mk(a, opd_T(B), opd_T(A), opd_T(Y)));
+    }
+  }
+  // write every region's gradient blocks (blocks without products are left as they are)
+  void flush(Backend* be) {
+    for (auto& R : regions) {
+      TaskList tl;
+      for (auto& kv : R.blocks) {
+        Group g;
+        g.yoff = kv.first;
+        g.q = kv.second.first.first;
+        g.r = kv.second.first.second;
+        g.row0 = g.col0 = 0;
+        g.nrows = g.q;
+        g.ncols = g.r;
+        g.t0 = (int)tl.tasks.size();
+        for (auto& t : kv.second.second) tl.tasks.push_back(t);
+        g.t1 = (int)tl.tasks.size();
+        tl.groups.push_back(g);
+      }
+      if (!tl.groups.empty()) be->run(tl, nullptr, R.grad, 1, 0, 0, 0);
+      R.blocks.clear();
+    }
+  }
+};
+
+// every block (offset, rows, cols) of a catalogue
+std::vector<std::array<long long, 3>> blocks_of(const Catalogue& c) {
+  std::vector<std::array<long long, 3>> v;
+  for (auto& o : c.ops) {
+    const Layout& L = c.layouts[o.layout];
+    for (size_t b = 0; b < L.in.size(); ++b)
+      v.push_back({o.off + L.off[b], c.basis.dim[L.out[b]], c.basis.dim[L.in[b]]});
+  }
+  return v;
+}
+
+void acc_lin(std::vector<double>& g, const Lin& f, double w) {
+  for (auto& x : f.c) g[x.first] += w * x.second;
+}
+}  // namespace
+
+int Engine::integral_gradient(const double* psi, std::vector<double>& g, std::string& err) {
+  if (!step_.valid) {
+    err = "integral_gradient: call build_env first";
+    return -2;
+  }
+  Step& st = step_;
+  const int k = st.k;
+  const long long N = N_, len = st.length;
+  g.assign(N * N + N * N * N * N, 0.0);
+  std::vector<double> ph(len);
+  be_->download(ph.data(), psi, len);
+  be_->sync();
+  double n2 = 0.0;
+  for (double x : ph) n2 += x * x;
+  if (!(n2 > 0.0)) {
+    err = "integral_gradient: zero wavefunction";
+    return -1;
+  }
+  std::vector<double> yh(len);
+  for (long long i = 0; i < len; ++i) yh[i] = ph[i] / n2;
+  double* Yb = be_->alloc(std::max(len, 1LL));
+  if (!Yb) {
+    err = "integral_gradient: allocation failed";
+    return -3;
+  }
+  be_->upload(Yb, yh.data(), len);
+  std::vector<double*> owned = {Yb};
+  auto galloc = [&](long long n) {
+    double* p = be_->alloc(std::max(n, 1LL));
+    if (p) {
+      be_->zero(p, std::max(n, 1LL));
+      owned.push_back(p);
+    }
+    return p;
+  };
+  auto gfree = [&](double* p) {
+    if (!p) return;
+    for (auto& q : owned)
+      if (q == p) q = nullptr;
+    be_->release(p);
+  };
+  auto cleanup = [&]() {
+    be_->sync();
+    for (double* p : owned)
+      if (p) be_->release(p);
+  };
+  auto values = [&](const TaskList& tl, const double* xv, const double* yb) {
+    std::vector<double> v(tl.tasks.size(), 0.0);
+    if (tl.tasks.empty()) return v;
+    double* d = be_->alloc((long long)tl.tasks.size());
+    be_->task_values(tl, xv, yb, d);
+    be_->download(v.data(), d, (long long)v.size());
+    be_->sync();
+    be_->release(d);
+    return v;
+  };
+  // coefficient derivative of one dot term (and of its expression's single
+  // coefficient when the expression is not materialised): weight w = dE/d(alpha) * alpha
+  auto dot_term = [&](const Side& S, const SideT<Lin>& SL, int e, int d, int t, double w) {
+    const DotTerm& dt = S.eops[e].dots[d].t[t];
+    const Lin& dl = SL.eops[e].dots[d].t[t].s;
+    if (!dl.is_const()) acc_lin(g, dl, w / dt.s);
+    const Expr& x = S.exprs[dt.expr];
+    if (x.mat < 0 && !x.t.empty()) {
+      const Lin& cl = SL.exprs[dt.expr].t[0].c;
+      if (!cl.is_const()) acc_lin(g, cl, w / x.t[0].c);
+    }
+  };
+  // partial sums: Gm (gradient of S's materialised arena) -> Gc (+= adjoint)
+  // and the derivatives of their coefficients; Gd: direct catalogue gradient
+  auto partial_sums = [&](const Side& S, const SideT<Lin>& SL, const Catalogue& C, const double* Gm, const double* Gd,
+                          double* Gc) {
+    const Basis& bs = C.basis;
+    TaskList lc;  // forward partial sums as products (I * op(src) * I)
+    std::vector<std::array<int, 2>> lprov;  // (expr, term) per product
+    std::vector<double> lsign;
+    AdjSink sink;
+    sink.region(C.d, C.size, Gc);
+    for (auto& b : blocks_of(C)) {  // carry the direct gradient
+      Opd I1{nullptr, true, false, (int)b[1], (int)b[1]}, I2{nullptr, true, false, (int)b[2], (int)b[2]};
+      sink.add(C.d + b[0], (int)b[1], (int)b[2], mk(1.0, I1, Opd{Gd + b[0], false, false, (int)b[1], (int)b[2]}, I2));
+    }
+    for (auto& mt : S.mats) {
+      const Expr& x = S.exprs[mt.expr];
+      const Layout& L = C.layouts[mt.layout];
+      for (size_t b = 0; b < L.in.size(); ++b) {
+        const int in = L.in[b], out = L.out[b];
+        const int rows = bs.dim[out], cols = bs.dim[in];
+        Group gr;
+        gr.yoff = mt.off + L.off[b];
+        gr.q = rows;
+        gr.r = cols;
+        gr.row0 = gr.col0 = 0;
+        gr.nrows = rows;
+        gr.ncols = cols;
+        gr.t0 = (int)lc.tasks.size();
+        for (size_t ti = 0; ti < x.t.size(); ++ti) {
+          const Term& tm = x.t[ti];
+          const double sign = tm.par == 1 ? sgn_n(bs.q[in].n) : tm.par == 2 ? sgn_n(bs.q[out].n) : 1.0;
+          Opd I1{nullptr, true, false, rows, rows}, I2{nullptr, true, false, cols, cols};
+          if (tm.op < 0) {
+            if (in != out) continue;
+            lc.tasks.push_back(mk(tm.c * sign, I1, Opd{nullptr, true, false, rows, cols}, I2));
+          } else {
+            const CatOp& o = C.ops[tm.op];
+            const Layout& OL = C.layouts[o.layout];
+            int ob = tm.tr ? OL.blk_of_in[out] : OL.blk_of_in[in];
+            if (ob < 0) continue;
+            if (tm.tr && OL.out[ob] != in) continue;
+            if (!tm.tr && OL.out[ob] != out) continue;
+            const double* src = C.d + o.off + OL.off[ob];
+            Opd X{src, false, tm.tr, rows, cols};
+            lc.tasks.push_back(mk(tm.c * sign, I1, X, I2));
+            sink.adjoint(lc.tasks.back(), nullptr, Gm + gr.yoff);
+          }
+          lprov.push_back({mt.expr, (int)ti});
+          lsign.push_back(sign);
+        }
+        gr.t1 = (int)lc.tasks.size();
+        lc.groups.push_back(gr);
+      }
+    }
+    const std::vector<double> v = values(lc, nullptr, Gm);
+    for (size_t i = 0; i < v.size(); ++i) {
+      const Lin& cl = SL.exprs[lprov[i][0]].t[lprov[i][1]].c;
+      if (!cl.is_const()) acc_lin(g, cl, v[i] * lsign[i]);
+    }
+    sink.flush(be_);
+  };
+  // Lin twins of the step's sides
+  SideT<Lin> SLl, SLr;
+  build_left_eops<Lin>(Lcat_[k], k, SLl);
+  compile_side<Lin>(SLl, Lcat_[k], true);
+  build_right_eops<Lin>(Rcat_[k + 2], k + 1, SLr);
+  compile_side<Lin>(SLr, Rcat_[k + 2], false);
+  if (SLl.eops.size() != st.L.eops.size() || SLr.eops.size() != st.R.eops.size() ||
+      SLl.exprs.size() != st.L.exprs.size() || SLr.exprs.size() != st.R.exprs.size()) {
+    cleanup();
+    err = "integral_gradient: tracked operator structure differs";
+    return -6;
+  }
+  // ---- H_eff*psi: coefficients and operand adjoints ----
+  {
+    const TaskList& tl = st.heff;
+    const std::vector<double> v = values(tl, psi, Yb);
+    for (size_t i = 0; i < tl.tasks.size(); ++i) {
+      const auto& pv = st.heff_prov[i];
+      const double w = v[i] * tl.tasks[i].alpha;
+      if (w == 0.0) continue;
+      if (pv[0] >= 0) dot_term(st.L, SLl, pv[0], pv[1], pv[2], w);
+      if (pv[3] >= 0) dot_term(st.R, SLr, pv[3], pv[4], pv[5], w);
+    }
+  }
+  Catalogue& Lk = Lcat_[k];
+  Catalogue& Rk = Rcat_[k + 2];
+  double* GdL = galloc(Lk.size);
+  double* GmL = galloc(st.L.size);
+  double* GdR = galloc(Rk.size);
+  double* GmR = galloc(st.R.size);
+  if (!GdL || !GmL || !GdR || !GmR) {
+    cleanup();
+    err = "integral_gradient: allocation failed";
+    return -3;
+  }
+  {
+    AdjSink sink;
+    sink.region(Lk.d, Lk.size, GdL);
+    if (st.L.size) sink.region(st.L.d, st.L.size, GmL);
+    sink.region(Rk.d, Rk.size, GdR);
+    if (st.R.size) sink.region(st.R.d, st.R.size, GmR);
+    for (const Group& gr : st.heff.groups)
+      for (int i = gr.t0; i < gr.t1; ++i) sink.adjoint(st.heff.tasks[i], psi, Yb + gr.yoff);
+    sink.flush(be_);
+  }
+  double* GL = galloc(Lk.size);
+  double* GR = galloc(Rk.size);
+  if (!GL || !GR) {
+    cleanup();
+    err = "integral_gradient: allocation failed";
+    return -3;
+  }
+  partial_sums(st.L, SLl, Lk, GmL, GdL, GL);
+  partial_sums(st.R, SLr, Rk, GmR, GdR, GR);
+  gfree(GdL);
+  gfree(GmL);
+  gfree(GdR);
+  gfree(GmR);
+  // ---- renormalisation chain: block l+1 = U^T (block l (x) dot l) U ----
+  auto level = [&](int site, bool left, double* Gnext, double*& Gout) -> int {
+    Catalogue& src = left ? Lcat_[site] : Rcat_[site + 1];
+    Catalogue& dst = left ? Lcat_[site + 1] : Rcat_[site];
+    Side S;
+    SideT<Lin> SL;
+    if (left) {
+      build_left_eops<double>(src, site, S);
+      compile_side<double>(S, src, true);
+      build_left_eops<Lin>(src, site, SL);
+      compile_side<Lin>(SL, src, true);
+    } else {
+      build_right_eops<double>(src, site, S);
+      compile_side<double>(S, src, false);
+      build_right_eops<Lin>(src, site, SL);
+      compile_side<Lin>(SL, src, false);
+    }
+    int rc = materialize(S, src, err);
+    if (rc) return rc;
+    TaskList rt;
+    std::vector<std::array<int, 3>> prov;
+    rotation_tasks(S, src, dst, site, left, rt, &prov);
+    const std::vector<double> v = values(rt, nullptr, Gnext);
+    for (size_t i = 0; i < rt.tasks.size(); ++i) {
+      const double w = v[i] * rt.tasks[i].alpha;
+      if (w != 0.0) dot_term(S, SL, prov[i][0], prov[i][1], prov[i][2], w);
+    }
+    double* Gd = galloc(src.size);
+    double* Gm = galloc(S.size);
+    Gout = galloc(src.size);
+    if (!Gd || !Gm || !Gout) {
+      free_side(S);
+      err = "integral_gradient: allocation failed";
+      return -3;
+    }
+    AdjSink sink;
+    sink.region(src.d, src.size, Gd);
+    if (S.size) sink.region(S.d, S.size, Gm);
+    for (const Group& gr : rt.groups)
+      for (int i = gr.t0; i < gr.t1; ++i) sink.adjoint(rt.tasks[i], nullptr, Gnext + gr.yoff);
+    sink.flush(be_);
+    partial_sums(S, SL, src, Gm, Gd, Gout);
+    be_->sync();
+    gfree(Gd);
+    gfree(Gm);
+    free_side(S);
+    std::string e = be_->error();
+    if (!e.empty()) {
+      err = e;
+      return -6;
+    }
+    return 0;
+  };
+  double* cur = GL;
+  for (int site = k - 1; site >= 0; --site) {
+    double* nxt = nullptr;
+    int rc = level(site, true, cur, nxt);
+    if (rc) {
+      cleanup();
+      return rc;
+    }
+    gfree(cur);
+    cur = nxt;
+  }
+  gfree(cur);
+  cur = GR;
+  for (int site = k + 2; site <= N_ - 1; ++site) {
+    double* nxt = nullptr;
+    int rc = level(site, false, cur, nxt);
+    if (rc) {
+      cleanup();
+      return rc;
+    }
+    gfree(cur);
+    cur = nxt;
+  }
+  gfree(cur);
+  cleanup();
   std::string e = be_->error();
   if (!e.empty()) {
     err = e;

@@ -27,6 +27,7 @@
 // (op = identity, plain or transposed), grouped by output block.
 #pragma once
 
+#include <array>
 #include <cstdint>
 #include <map>
 #include <string>
@@ -318,6 +319,9 @@ struct Backend {
   // its tasks.  xv/yv: bases for TF_XV offsets and group yoff.
   virtual void run(const TaskList& tl, const double* xv, double* yv, int nvec,
                    long long xstride, long long ystride, int precision) = 0;
+  // out[t] = < Ybar_g, op(L_t) op(X_t) op(R_t)^T > for every task t of group g
+  // (alpha not included); out is backend memory of tl.tasks.size() doubles
+  virtual void task_values(const TaskList& tl, const double* xv, const double* ybar, double* out) = 0;
   virtual void sync() = 0;
   virtual std::string error() = 0;  // "" if fine
 };
@@ -365,6 +369,9 @@ struct Step {
   std::vector<long long> desc;
   long long length = 0;
   TaskList heff;
+  // per H_eff task, where its coefficient comes from: (eop, dot block, dot
+  // term) on the left side and on the right side; -1 for an identity side
+  std::vector<std::array<int, 6>> heff_prov;
   std::vector<int> diag_tasks;  // tasks contributing to the diagonal, in group order
   std::vector<int> diag_rng;    // per group: range [diag_rng[g], diag_rng[g+1]) of diag_tasks
   bool valid = false;
@@ -392,6 +399,11 @@ class Engine {
   // gradients of <Yb, H_eff X> w.r.t. the arenas of L_k (Lb) and R_{k+2} (Rb);
   // any output may be null.  All pointers in the backend's memory space.
   int heff_adjoint(const double* X, const double* Yb, double* Xb, double* Lb, double* Rb, std::string& err);
+  // gradient of E = <psi|H_eff|psi>/<psi|psi> at the current step with respect
+  // to every stored integral (h_ij at i*N+j, (ij|kl) at N^2+((i*N+j)*N+k)*N+l),
+  // the MPS isometries fixed: reverse mode through H_eff*psi and through the
+  // renormalisation chain of both blocks.  psi: backend memory, step layout.
+  int integral_gradient(const double* psi, std::vector<double>& g, std::string& err);
   // refresh the step's partial sums after the catalogue arenas were changed
   int refresh_step(std::string& err) { return step_.valid ? prepare_step(step_.k, err) : -2; }
   double e_core() const { return e_core_; }
@@ -458,6 +470,11 @@ class Engine {
   void compile_side(SideT<Sc>& S, const Catalogue& cat, bool left);
   int materialize(Side& S, Catalogue& cat, std::string& err);
   int rotate(Side& S, const Catalogue& src, Catalogue& dst, int site, bool left, std::string& err);
+  // the renormalisation task list of rotate() into an existing dst layout;
+  // prov (optional) receives (eop, dot block, dot term) per task
+  void rotation_tasks(const Side& S, const Catalogue& src, const Catalogue& dst, int site, bool left, TaskList& tl,
+                      std::vector<std::array<int, 3>>* prov);
+
   void build_psi(int k);
   void build_heff_tasks();
 };

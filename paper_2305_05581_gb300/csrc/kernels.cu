@@ -1312,6 +1312,58 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
   if (precision != 0) check_tasks_tc(*this, d);
 }
 
+// out[t] = < Ybar_g, op(L) op(X) op(R)^T > for every task t (alpha excluded):
+// one CTA per task; each thread takes elements (k, j) of the m x r product
+// P = op(L)^T Ybar and T = op(X) op(R)^T and accumulates P_kj T_kj
+__global__ void __launch_bounds__(128) k_task_values(const Task* __restrict__ tasks, const int* __restrict__ tgroup,
+                                                     const Group* __restrict__ groups, const double* xv,
+                                                     const double* __restrict__ ybar, double* out) {
+  const Task T = tasks[blockIdx.x];
+  const Group G = groups[tgroup[blockIdx.x]];
+  const double* Y = ybar + G.yoff;
+  const double* X = (T.flags & TF_XV) ? xv + (long long)(size_t)T.X : T.X;
+  double s = 0.0;
+  for (long long e = threadIdx.x; e < (long long)T.m * T.r; e += blockDim.x) {
+    const int k = (int)(e / T.r), j = (int)(e % T.r);
+    double P = 0.0;
+    if (T.flags & TF_LI)
+      P = Y[(long long)k * G.r + j];
+    else
+      for (int i = 0; i < T.q; ++i) P = fma(opL(T, i, k), Y[(long long)i * G.r + j], P);
+    double V = 0.0;
+    if (T.flags & TF_RI)
+      V = opX(T, X, k, j);
+    else if (T.flags & TF_XI)
+      V = opR(T, j, k);
+    else
+      for (int l = 0; l < T.n; ++l) V = fma(opX(T, X, k, l), opR(T, j, l), V);
+    s = fma(P, V, s);
+  }
+  __shared__ double red[4];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+}
+
+void CudaBackend::task_values(const TaskList& tl, const double* xv, const double* ybar, double* out) {
+  if (tl.tasks.empty()) return;
+  std::vector<int> tg(tl.tasks.size(), 0);
+  for (int g = 0; g < (int)tl.groups.size(); ++g)
+    for (int i = tl.groups[g].t0; i < tl.groups[g].t1; ++i) tg[i] = g;
+  Task* dt = dev_copy(tl.tasks, *this);
+  Group* dg = dev_copy(tl.groups, *this);
+  int* dtg = dev_copy(tg, *this);
+  if (dt && dg && dtg) {
+    k_task_values<<<(unsigned)tl.tasks.size(), 128, 0, stream_>>>(dt, dtg, dg, xv, ybar, out);
+    launches++;
+    note(cudaGetLastError(), "k_task_values");
+  }
+  cudaStreamSynchronize(stream_);
+  for (void* p : {(void*)dt, (void*)dg, (void*)dtg})
+    if (p) cudaFree(p);
+}
+
 void CudaBackend::lincomb(const LCList& l) {
   if (l.blocks.empty()) return;
   LCBlock* b = dev_copy(l.blocks, *this);

@@ -69,6 +69,27 @@ struct HostBackend : tns::Backend {
         }
       }
   }
+  void task_values(const tns::TaskList& tl, const double* xv, const double* ybar, double* out) override {
+    for (const auto& g : tl.groups) {
+      const double* Y = ybar + g.yoff;
+      for (int ti = g.t0; ti < g.t1; ++ti) {
+        const tns::Task& t = tl.tasks[ti];
+        const double* X = (t.flags & tns::TF_XV) ? xv + (long long)(uintptr_t)t.X : t.X;
+        double v = 0.0;
+        for (int i = 0; i < t.q; ++i)
+          for (int j = 0; j < t.r; ++j) {
+            double s = 0.0;
+            for (int a = 0; a < t.m; ++a) {
+              double la = opL(t, i, a);
+              if (la == 0.0) continue;
+              for (int b = 0; b < t.n; ++b) s += la * opX(t, X, a, b) * opR(t, j, b);
+            }
+            v += Y[(long long)i * g.r + j] * s;
+          }
+        out[ti] = v;
+      }
+    }
+  }
   void sync() override {}
   std::string error() override { return ""; }
 };
