@@ -31,9 +31,10 @@ METRIC = "H_eff\u00b7\u03c8 useful TFLOP/s and s per two-site step at \u0394E\u2
 UNIT = "TFLOP/s"
 
 # DRAM bytes (read + write) of the dominant kernel per H_eff*psi at this
-# workload, from the ncu captures summarised under profiles/ (None until
-# captured for the current kernel of that precision).
-TRAFFIC_BYTES_PER_HEFF = {"fp64": None, "tf32": None, "bf16x3": None}
+# workload's middle bond, from the ncu capture summarised in
+# profiles/k_tasks_tc_bf16x3_n24_state.md (None until captured for the
+# current kernel of that precision).
+TRAFFIC_BYTES_PER_HEFF = {"fp64": None, "tf32": None, "bf16x3": 5.21e9}
 
 
 def parse():

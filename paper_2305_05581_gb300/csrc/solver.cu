@@ -198,16 +198,20 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
   bool conv = false;
   const int lowp = precision != 0;
   double fp64_res = 1e300;
+  // reduced precision: the start vector's product is reduced too (the first
+  // phase only has to cut the residual by 1e-3); V_0 carries an exact FP64
+  // product from the first refresh on
+  bool v0_exact = !lowp;
   while (true) {
     // expand by the nnew vectors V[k..k+nnew)
-    matvec(V.d() + (long long)k * n, AV.d() + (long long)k * n, nnew, (lowp && k > 0) ? precision : 0);
+    matvec(V.d() + (long long)k * n, AV.d() + (long long)k * n, nnew, lowp ? precision : 0);
     it += nnew;
     for (int j = 0; j < nnew; ++j) {
       const int kj = k + j;
       launch_multidot(be, V.d(), n, kj + 1, AV.d() + (long long)kj * n, n, dcoef);
       std::vector<double> hc;
       get(be, hc, dcoef, kj + 1);
-      if (lowp && kj > 0) {
+      if (lowp && v0_exact && kj > 0) {
         // couplings to V_0 from its exact FP64 product: <V_k, H V_0> instead of
         // <V_0, H~ V_k>; near convergence the reduced-precision error of the
         // latter exceeds the coupling itself and would stall the refinement
@@ -252,18 +256,20 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
     if (check(be, err)) return -6;
     bool restarted = false;
     if (lowp) {
-      // FP64 residual correction: V_0 always carries an exact FP64 product,
-      // the other basis vectors reduced-precision ones; the Ritz pair is
-      // accepted only on an FP64 residual, and every refresh restarts the
-      // subspace from the exact pair (x, H x)
+      // FP64 residual correction: after the first refresh V_0 carries an
+      // exact FP64 product, the other basis vectors reduced-precision ones;
+      // the Ritz pair is accepted only on an FP64 residual, and every refresh
+      // restarts the subspace from the exact pair (x, H x)
       if (k == 1) {
-        fp64_res = rn;  // x = V_0 and A V_0 is exact
-        if (rn < tol || it >= max_iter) {
+        fp64_res = rn;  // x = V_0: exact after a refresh, a reference residual before the first one
+        if (v0_exact && (rn < tol || it >= max_iter)) {
           conv = rn < tol;
           break;
         }
       }
-      bool stalled = k > 1 && (rn < std::max(0.5 * tol, 1e-3 * fp64_res) || k + block > kmax || it >= max_iter);
+      bool stalled = (k > 1 || !v0_exact) &&
+                     (rn < std::max(0.5 * tol, 1e-3 * fp64_res) || k + block > kmax || it >= max_iter);
+      if (k == 1 && !v0_exact && !(it >= max_iter)) stalled = false;
       if (stalled) {
         matvec(x.d(), avs.d(), 1, 0);
         ++it;
@@ -280,6 +286,7 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
           break;
         }
         // restart from the FP64-exact pair
+        v0_exact = true;
         const double f = 1.0 / std::sqrt(xx);
         scale_by(x.d(), f);
         scale_by(avs.d(), f);
