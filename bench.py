@@ -160,6 +160,19 @@ def fp64_gemm_peak(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
+def combine_ranks(dist, elapsed, flops, device):
+    """Whole-job numbers of N independent replicas: the slowest rank's time and
+    the flops of all ranks (no data-path collective: replicas only)."""
+    if not dist:
+        return elapsed, flops
+    import torch
+    t = torch.tensor([elapsed], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    f = torch.tensor([flops], device=device, dtype=torch.float64)
+    dist.all_reduce(f)
+    return float(t), float(f)
+
+
 def workload_config(args, c):
     N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
     return {"workload": f"{args.workload}: N={N} n_elec={n} 2Sz={s2} D={D} lambda={c['lam']} seed={c['seed']}; "
@@ -253,15 +266,7 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     elapsed = e0.elapsed_time(e1) * 1e-3
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t)
-        f = torch.tensor([flops], device="cuda", dtype=torch.float64)
-        dist.all_reduce(f)
-        flops_all = float(f)
-    else:
-        flops_all = flops
+    elapsed, flops_all = combine_ranks(dist, elapsed, flops, "cuda")
     value = flops_all / elapsed / 1e12
 
     # energy check at the next step's H_eff: Davidson in this precision (FP64

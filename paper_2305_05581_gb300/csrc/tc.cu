@@ -500,42 +500,59 @@ __global__ void __launch_bounds__(TC_NT, 2)
         const int nk2 = mc16 * ES / 32;  // 32-byte MMA k-steps over this X row range
         const int nch2 = (mc16 * ES + CH_BYTES - 1) / CH_BYTES;
         const uint32_t id = idesc(TF32 ? 2 : 1, rp);
-        for (int t = 0; t < pc && !bad; ++t) {
+        // two-stage pipeline over the steps s = (product t, K chunk c2): the
+        // L slice of step s+1 is copied while step s's MMAs run
+        const int nsteps = pc * nch2;
+        auto issue = [&](int st, int b) {  // bulk copy of step st's L slice into buffer b
+          const int t = st / nch2, c2 = st % nch2;
           const Img Lm = tasks[C.t0 + t].L;
           const int lg0 = TL.row0 / 8, lng = min(TC_M / 8, Lm.rg - lg0);
-          const uint32_t bt = (uint32_t)(t * rp / 8) * SBO_FULL;  // product t's rows inside a B2 chunk
-          for (int c2 = 0; c2 < nch2 && !bad; ++c2) {
-            const int b = g2_steps & 1;
-            where_s = 1000 + t * 16 + c2;
-            drain(&mbar2[b], pm2[b], m2_out[b]);  // buffer b free
-            if (bad) break;
-            const int lc = (m0 * ES) / CH_BYTES + c2;  // chunk of L's K (= X rows)
-            const int kcm = chunk_w(Lm, lc) / 16;
-            const uint32_t rowb = kcm * 128;
-            unsigned char* a2 = sA2 + b * S::NS * S::A2;
-            expect_tx(&lbar2[b], lng * rowb * S::NS);
-            l2_out[b] = 1;
-            const long long lo_ = chunk_off(Lm, lc) + (long long)lg0 * rowb;
-            bulk_g2s(a2, ops_hi + lo_, lng * rowb, &lbar2[b]);
-            if (!TF32) bulk_g2s(a2 + S::A2, ops_lo + lo_, lng * rowb, &lbar2[b]);
-            drain(&lbar2[b], pl2[b], l2_out[b]);
-            if (bad) break;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const int ks_here = min(kcm / 2, nk2 - c2 * (CH_BYTES / 32));
-            for (int ks = 0; ks < ks_here; ++ks)
-              for (int pr = 0; pr < NPROD; ++pr) {
-                const unsigned char* a = a2 + (pr == 2 ? S::A2 : 0);
-                const unsigned char* bb = sB2 + (pr == 1 ? S::B2 : 0) + c2 * S::CB2 + bt;
-                const uint32_t acc = (d2 || ks > 0 || pr > 0) ? 1u : 0u;
-                mma<TF32>(tD2, sdesc(smem_u32(a) + ks * 256, rowb), sdesc(smem_u32(bb) + ks * 256, SBO_FULL), id,
-                          acc);
-              }
-            d2 = true;
-            commit(&mbar2[b]);
-            m2_out[b] = 1;
-            ++g2_steps;
-          }
+          const int lc = (m0 * ES) / CH_BYTES + c2;  // chunk of L's K (= X rows)
+          const uint32_t rowb = (chunk_w(Lm, lc) / 16) * 128;
+          unsigned char* a2 = sA2 + b * S::NS * S::A2;
+          expect_tx(&lbar2[b], lng * rowb * S::NS);
+          l2_out[b] = 1;
+          const long long lo_ = chunk_off(Lm, lc) + (long long)lg0 * rowb;
+          bulk_g2s(a2, ops_hi + lo_, lng * rowb, &lbar2[b]);
+          if (!TF32) bulk_g2s(a2 + S::A2, ops_lo + lo_, lng * rowb, &lbar2[b]);
+        };
+        if (nsteps > 0) {
+          const int b0 = g2_steps & 1;
+          drain(&mbar2[b0], pm2[b0], m2_out[b0]);  // buffer free
+          if (!bad) issue(0, b0);
         }
+        for (int st = 0; st < nsteps && !bad; ++st) {
+          const int b = (g2_steps + st) & 1, bn = (g2_steps + st + 1) & 1;
+          where_s = 1000 + st;
+          if (st + 1 < nsteps) {
+            drain(&mbar2[bn], pm2[bn], m2_out[bn]);  // the MMAs of step st-1 read buffer bn
+            if (bad) break;
+            issue(st + 1, bn);
+          }
+          drain(&lbar2[b], pl2[b], l2_out[b]);
+          if (bad) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const int t = st / nch2, c2 = st % nch2;
+          const Img Lm = tasks[C.t0 + t].L;
+          const int lc = (m0 * ES) / CH_BYTES + c2;
+          const int kcm = chunk_w(Lm, lc) / 16;
+          const uint32_t rowb = kcm * 128;
+          const unsigned char* a2 = sA2 + b * S::NS * S::A2;
+          const uint32_t bt = (uint32_t)(t * rp / 8) * SBO_FULL;  // product t's rows inside a B2 chunk
+          const int ks_here = min(kcm / 2, nk2 - c2 * (CH_BYTES / 32));
+          for (int ks = 0; ks < ks_here; ++ks)
+            for (int pr = 0; pr < NPROD; ++pr) {
+              const unsigned char* a = a2 + (pr == 2 ? S::A2 : 0);
+              const unsigned char* bb = sB2 + (pr == 1 ? S::B2 : 0) + c2 * S::CB2 + bt;
+              const uint32_t acc = (d2 || ks > 0 || pr > 0) ? 1u : 0u;
+              mma<TF32>(tD2, sdesc(smem_u32(a) + ks * 256, rowb), sdesc(smem_u32(bb) + ks * 256, SBO_FULL), id,
+                        acc);
+            }
+          d2 = true;
+          commit(&mbar2[b]);
+          m2_out[b] = 1;
+        }
+        g2_steps += nsteps;
       }
       __syncthreads();
     }
