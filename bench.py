@@ -48,9 +48,10 @@ def parse():
                    help="sector products: bf16x3 (split-BF16, FP32 accumulation; the precision form, default), "
                         "tf32, or fp64; Davidson, residuals and truncation are FP64 in every case")
     p.add_argument("--tol", type=float, default=1e-8)
-    p.add_argument("--case", default="step", choices=["step", "heff"],
+    p.add_argument("--case", default="step", choices=["step", "heff", "rdm"],
                    help="step: two-site DMRG steps (the benchmark); heff: H_eff*psi alone at the middle bond "
-                        "of a random MPS of the workload (kernel micro-benchmark, used for ncu captures)")
+                        "of a random MPS of the workload (kernel micro-benchmark, used for ncu captures); "
+                        "rdm: integral gradients (1- and 2-RDM) at the middle bond of a random MPS")
     p.add_argument("--nvec", type=int, default=1)
     return p.parse_args()
 
@@ -92,6 +93,49 @@ def run_heff_case(args):
                       "useful_flops": flops * args.nvec, "ms": dt * 1e3,
                       "tflops": flops * args.nvec / dt / 1e12, "max_sector_dim": max(dims),
                       "bond_dim": sum(dims)}), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_rdm_case(args):
+    """Integral gradients (tns_rdm: gamma and the orbit-averaged Gamma) at the
+    middle bond of a random MPS of the workload, with H_eff*psi for scale."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2305_05581_gb300 import Context, TNS_FP64
+    c = synth.WORKLOADS[args.workload]
+    N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
+    k = N // 2 - 1
+    h, v = synth.integrals(N, c["lam"], c["seed"])
+    bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=c["seed"])
+    stream = torch.cuda.current_stream()
+    ctx = Context(device=0, stream=stream.cuda_stream)
+    ctx.load_integrals(h, v)
+    ctx.mps_import(N, n, s2, D, bonds, sites)
+    t0 = time.perf_counter()
+    ctx.build_env(k)
+    torch.cuda.synchronize()
+    t_env = time.perf_counter() - t0
+    desc, length = ctx.psi_layout(k)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(length, device="cuda", dtype=torch.float64, generator=g)
+    y = torch.empty_like(x)
+    ctx.heff_apply_ptr(k, x.data_ptr(), y.data_ptr(), 1, TNS_FP64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.heff_apply_ptr(k, x.data_ptr(), y.data_ptr(), 1, TNS_FP64)
+    torch.cuda.synchronize()
+    t_heff = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gamma, Gamma = ctx.rdm_ptr(k, x.data_ptr(), N)
+    t_rdm = time.perf_counter() - t0
+    e = float(torch.dot(x, y) / torch.dot(x, x))
+    print(json.dumps({"case": "rdm", "workload": args.workload, "N": N, "D": D, "psi_length": int(length),
+                      "build_env_s": t_env, "heff_fp64_s": t_heff, "rdm_s": t_rdm,
+                      "trace_gamma": float(np.trace(gamma)), "n_elec": n,
+                      "energy_identity_err": abs(e - (float(np.sum(h * gamma)) + 0.5 * float(np.sum(v * Gamma))))}),
+          flush=True)
     ctx.close()
     return 0
 
@@ -213,6 +257,8 @@ def main():
     torch.cuda.set_device(local)
     if args.case == "heff":
         return run_heff_case(args)
+    if args.case == "rdm":
+        return run_rdm_case(args)
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -103,6 +103,10 @@ class CudaBackend : public Backend {
   cudaStream_t stream() const { return stream_; }
   int device() const { return device_; }
   void note(cudaError_t e, const char* what);
+  // false once a failure (an allocation, a launch) has been noted in the
+  // current call: later launches are skipped so that no kernel runs on a
+  // buffer that does not exist
+  bool ok() const { return err_.empty(); }
   // persistent device copy of a task list (uploaded when tl.gen changes)
   DevList& dev(const TaskList& tl);
   // the device copy of tl if it is resident and current, else nullptr (never uploads)

@@ -197,7 +197,21 @@ __global__ void __launch_bounds__(SY_NT) k_syev(double* A, double* Zall, double*
     const int lo = ctl[0], hi = ctl[1];
     for (int j = tid; j < n; j += SY_NT) {
       double carry = Z[(long long)lo * n + j];
-      for (int i = lo; i < hi; ++i) {
+      int i = lo;
+      // every original row is read once (as y) before its row is written, so
+      // the loads of the next 8 rows are issued together ahead of the stores
+      for (; i + 8 <= hi; i += 8) {
+        double y[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) y[q] = Z[(long long)(i + 1 + q) * n + j];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const double c = v[i + q], s = p[i + q];
+          Z[(long long)(i + q) * n + j] = c * carry + s * y[q];
+          carry = -s * carry + c * y[q];
+        }
+      }
+      for (; i < hi; ++i) {
         const double y = Z[(long long)(i + 1) * n + j];
         const double c = v[i], s = p[i];
         Z[(long long)i * n + j] = c * carry + s * y;
@@ -218,7 +232,7 @@ __global__ void __launch_bounds__(SY_NT) k_syev(double* A, double* Zall, double*
 
 void launch_syev(CudaBackend& be, double* A, double* Z, double* w, const long long* off, const int* n,
                  const int* woff, int nmat, int maxn, int* status) {
-  if (nmat <= 0 || maxn <= 0) return;
+  if (nmat <= 0 || maxn <= 0 || !be.ok()) return;
   if (maxn > SYEV_MAXN) {
     be.note(cudaErrorInvalidValue, "syev: matrix too large");
     return;

@@ -48,13 +48,16 @@ constexpr int C1_NT = 128, C1_ACC = 8, C1_TR = 32, C1_TC = 32;
 constexpr int C2_NT = 256, C2_ACC = 16, C2_TR = 64, C2_TC = 64;
 
 template <int NT, int ACC, int TR, int TC>
-__global__ void __launch_bounds__(NT) k_tasks_fp64(const Task* __restrict__ tasks, const Group* __restrict__ groups,
+__global__ void __launch_bounds__(NT, NT >= 256 ? 2 : NT >= 128 ? 4 : 16) k_tasks_fp64(const Task* __restrict__ tasks, const Group* __restrict__ groups,
                                                    const Tile* __restrict__ tiles, int tile0, const double* xv,
                                                    double* yv, long long xs, long long ys, double* part,
                                                    long long psize) {
   constexpr int SA = CH * (TC + 1);  // L (X R^T): CH rows of X R^T, TC columns
   constexpr int SB = TR * (CH + 1);  // (L X) R^T: TR rows of L X, CH columns
-  __shared__ double S[SA > SB ? SA : SB];
+  constexpr int SR = CH * (TC + 1);  // L (X R^T): a K slice of the tile's R rows, transposed
+  constexpr int TE = CH * TC / NT;   // elements of X R^T per thread and chunk (upper bound)
+  __shared__ double S[(SA > SB ? SA : SB) + SR];
+  double* const Rt = S + (SA > SB ? SA : SB);
   const Tile T = tiles[tile0 + blockIdx.x];
   const Group G = groups[T.g];
   const int vec = blockIdx.y;
@@ -127,13 +130,38 @@ __global__ void __launch_bounds__(NT) k_tasks_fp64(const Task* __restrict__ task
       // L (X R^T): chunks of CH rows of X
       for (int m0 = 0; m0 < tk.m; m0 += CH) {
         const int mc = min(CH, tk.m - m0);
+        // T = X[m0.., :] R[tile cols, :]^T in K slices of CH; the slice of R
+        // is staged transposed so that consecutive threads read consecutive
+        // columns (a strided row read per thread otherwise)
+        double tacc[TE];
+#pragma unroll
+        for (int e = 0; e < TE; ++e) tacc[e] = 0.0;
+        for (int k0 = 0; k0 < tk.n; k0 += CH) {
+          const int kc = min(CH, tk.n - k0);
+          for (int e = tid; e < nc * kc; e += NT) {
+            const int j = e / kc, kk = e % kc;
+            Rt[kk * (TC + 1) + j] = __ldg(pR + (T.col0 + j) * sRj + (k0 + kk) * sRk);
+          }
+          __syncthreads();
+          if (a_ok) {
+#pragma unroll
+            for (int e = 0; e < TE; ++e) {
+              const int i = a_i0 + e * a_st;
+              if (i < mc) {
+                const double* xr = pX + (m0 + i) * sXi + k0 * sXk;
+                double s = tacc[e];
+                for (int kk = 0; kk < kc; ++kk) s = fma(__ldg(xr + kk * sXk), Rt[kk * (TC + 1) + a_j], s);
+                tacc[e] = s;
+              }
+            }
+          }
+          __syncthreads();
+        }
         if (a_ok) {
-          const double* rr = pR + (T.col0 + a_j) * sRj;
-          for (int i = a_i0; i < mc; i += a_st) {
-            const double* xr = pX + (m0 + i) * sXi;
-            double s = 0.0;
-            for (int k = 0; k < tk.n; ++k) s = fma(__ldg(xr + k * sXk), __ldg(rr + k * sRk), s);
-            S[i * (TC + 1) + a_j] = s;
+#pragma unroll
+          for (int e = 0; e < TE; ++e) {
+            const int i = a_i0 + e * a_st;
+            if (i < mc) S[i * (TC + 1) + a_j] = tacc[e];
           }
         }
         __syncthreads();
@@ -427,6 +455,7 @@ __global__ void k_heff_diag(const Task* __restrict__ tasks, const int* __restric
 
 void launch_reduce_splits(CudaBackend& be, const SplitRed* reds, int nreds, const Group* groups, const double* part,
                           long long psize, double* yv, long long ys, int nvec) {
+  if (!be.ok()) return;
   if (nreds <= 0) return;
   dim3 grid(std::min(nreds, 65535), nvec);
   k_reduce_splits<<<grid, 128, 0, be.stream()>>>(reds, nreds, groups, part, psize, yv, ys);
@@ -436,6 +465,7 @@ void launch_reduce_splits(CudaBackend& be, const SplitRed* reds, int nreds, cons
 
 void launch_heff_diag(CudaBackend& be, const Task* d_tasks, const int* d_idx, const int* d_rng, int ngroups,
                       const Group* d_groups, double* diag) {
+  if (!be.ok()) return;
   if (ngroups <= 0) return;
   k_heff_diag<<<std::min(ngroups, 65535), 128, 0, be.stream()>>>(d_tasks, d_idx, d_rng, ngroups, d_groups, diag);
   be.launches++;
@@ -491,6 +521,7 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int nb, in
 
 void launch_multidot(CudaBackend& be, const double* V, long long ldv, int k, const double* w, long long n,
                      double* out) {
+  if (!be.ok()) return;
   // in chunks of at most MAXK vectors (the kernel keeps one accumulator per vector)
   double* partial = (double*)be.scratch(sizeof(double) * MAXK * RED_BLOCKS, 0);
   for (int i0 = 0; i0 < k; i0 += MAXK) {
@@ -517,6 +548,7 @@ __global__ void k_axpy_multi(const double* __restrict__ V, long long ldv, int k,
 
 void launch_axpy_multi(CudaBackend& be, const double* V, long long ldv, int k, const double* coef, double sign,
                        double* w, long long n) {
+  if (!be.ok()) return;
   for (int i0 = 0; i0 < k; i0 += MAXK) {
     const int kc = std::min(MAXK, k - i0);
     k_axpy_multi<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(V + (long long)i0 * ldv, ldv, kc, coef + i0, sign, w, n);
@@ -539,6 +571,7 @@ __global__ void k_combine(const double* __restrict__ V, long long ldv, int k, co
 
 void launch_combine(CudaBackend& be, const double* V, long long ldv, int k, const double* coef, double* out,
                     long long n) {
+  if (!be.ok()) return;
   if (k <= 0) return;
   const int kc = std::min(MAXK, k);
   k_combine<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(V, ldv, kc, coef, out, n);
@@ -556,6 +589,7 @@ __global__ void k_scale(double* x, const double* num, int inv_sqrt, long long n)
 }
 
 void launch_scale(CudaBackend& be, double* x, const double* num, int inv_sqrt, long long n) {
+  if (!be.ok()) return;
   k_scale<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(x, num, inv_sqrt, n);
   be.launches++;
   be.note(cudaGetLastError(), "scale");
@@ -573,6 +607,7 @@ __global__ void k_precond(const double* r, const double* diag, const double* the
 
 void launch_precond(CudaBackend& be, const double* r, const double* diag, const double* theta, double* t,
                     long long n) {
+  if (!be.ok()) return;
   k_precond<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(r, diag, theta, t, n);
   be.launches++;
   be.note(cudaGetLastError(), "precond");
@@ -587,6 +622,7 @@ __global__ void k_residual(const double* AVs, const double* x, const double* the
 
 void launch_residual(CudaBackend& be, const double* AVs, const double* x, const double* theta, double* r,
                      long long n) {
+  if (!be.ok()) return;
   k_residual<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(AVs, x, theta, r, n);
   be.launches++;
   be.note(cudaGetLastError(), "residual");
@@ -620,6 +656,7 @@ __global__ void k_argmin(const double* x, long long n, long long* idx) {
 }
 
 void launch_argmin(CudaBackend& be, const double* x, long long n, long long* idx) {
+  if (!be.ok()) return;
   k_argmin<<<1, 1024, 0, be.stream()>>>(x, n, idx);
   be.launches++;
   be.note(cudaGetLastError(), "argmin");
@@ -632,6 +669,7 @@ __global__ void k_fill_unit(double* x, long long n, const long long* idx) {
 }
 
 void launch_fill_unit(CudaBackend& be, double* x, long long n, const long long* idx) {
+  if (!be.ok()) return;
   k_fill_unit<<<RED_BLOCKS * 2, 256, 0, be.stream()>>>(x, n, idx);
   be.launches++;
   be.note(cudaGetLastError(), "fill_unit");
@@ -755,6 +793,7 @@ __global__ void __launch_bounds__(JAC_NT) k_jacobi(double* A, double* V, double*
 
 void launch_jacobi(CudaBackend& be, double* A, double* V, double* w, const long long* off, const int* n,
                    const int* woff, int nmat, int maxn, int* sweeps_out) {
+  if (!be.ok()) return;
   if (nmat <= 0) return;
   if (maxn > 2 * JAC_MAXPAIR) {
     be.note(cudaErrorInvalidValue, "jacobi: matrix too large");
@@ -813,6 +852,7 @@ __global__ void k_select(const double* w, const int* sec_of, int total, int P, i
 
 void launch_select(CudaBackend& be, const double* w, const int* sec_of, int total, int keep_max, double cut,
                    int* keep_flag, double* disc) {
+  if (!be.ok()) return;
   int P = 1;
   while (P < total) P <<= 1;
   double* kv = (double*)be.scratch(sizeof(double) * P + 64, 1);
@@ -839,6 +879,7 @@ __global__ void k_gather(const double* src, const long long* so, const int* sld,
 void launch_gather(CudaBackend& be, const double* src, const long long* so, const int* sld, double* dst,
                    const long long* dof, const int* dld, const int* rows, const int* cols, const int* trans,
                    int nblk) {
+  if (!be.ok()) return;
   if (nblk <= 0) return;
   k_gather<<<std::min(nblk, 65535), 128, 0, be.stream()>>>(src, so, sld, dst, dof, dld, rows, cols, trans, nblk);
   be.launches++;
@@ -1137,6 +1178,7 @@ void CudaBackend::drop(const TaskList& tl) {
 
 void CudaBackend::enqueue_fp64(const DevList& d, int v, const double* xv, double* yv, int nvec, long long xs,
                                long long ys) {
+  if (!ok()) return;
   const FpVariant& f = d.fv[v];
   int t0 = 0;
   for (int c = 0; c < 3; ++c) {
@@ -1234,6 +1276,7 @@ void CudaBackend::launch_graphed(DevList& d, int key, const double* xv, double* 
 
 void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec, long long xs, long long ys,
                       int precision) {
+  if (!ok()) return;
   if (tl.groups.empty()) return;
   if (!tl.persistent) {
     // one-off list (rotations, truncation products): default schedule, direct launches
@@ -1254,12 +1297,13 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
       }
     } else {
       plan_variant(tl, tmp, 1);
-      if (ensure_part(tmp.fv[1], nvec)) enqueue_fp64(tmp, 1, xv, yv, nvec, xs, ys);
+      if (ok() && tmp.tasks && tmp.groups && ensure_part(tmp.fv[1], nvec)) enqueue_fp64(tmp, 1, xv, yv, nvec, xs, ys);
     }
     free_list(tmp);
     return;
   }
   DevList& d = dev(tl);
+  if (!ok() || !d.tasks || !d.groups) return;
   if (precision == 0 && fp64_kernel == 1) {
     if (d.nwtiles > 0) {
       dim3 grid((d.nwtiles + DM_WARPS - 1) / DM_WARPS, nvec);
@@ -1280,7 +1324,7 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
     if (!prepare_tasks_tc(*this, tl, d, nvec, v, precision)) return;
   } else {
     plan_variant(tl, d, v);
-    if (!ensure_part(d.fv[v], nvec)) return;
+    if (!ok() || !ensure_part(d.fv[v], nvec)) return;
   }
   auto enqueue = [&](const double* x, double* y) {
     if (precision != 0)
@@ -1347,6 +1391,7 @@ __global__ void __launch_bounds__(128) k_task_values(const Task* __restrict__ ta
 }
 
 void CudaBackend::task_values(const TaskList& tl, const double* xv, const double* ybar, double* out) {
+  if (!ok()) return;
   if (tl.tasks.empty()) return;
   std::vector<int> tg(tl.tasks.size(), 0);
   for (int g = 0; g < (int)tl.groups.size(); ++g)
@@ -1365,6 +1410,7 @@ void CudaBackend::task_values(const TaskList& tl, const double* xv, const double
 }
 
 void CudaBackend::lincomb(const LCList& l) {
+  if (!ok()) return;
   if (l.blocks.empty()) return;
   LCBlock* b = dev_copy(l.blocks, *this);
   LCTerm* t = dev_copy(l.terms, *this);

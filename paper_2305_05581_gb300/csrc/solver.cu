@@ -126,7 +126,9 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
   DBuf V(be, sizeof(double) * kmax * n), AV(be, sizeof(double) * kmax * n);
   DBuf diag(be, sizeof(double) * n), x(be, sizeof(double) * n), r(be, sizeof(double) * n),
       avs(be, sizeof(double) * n), t(be, sizeof(double) * n);
-  DBuf tmp(be, sizeof(double) * (block > 1 ? 4 * block : 1) * n);
+  // reduced precision: Ritz vectors kept across a refresh (besides the refreshed one)
+  const int lp_keep = precision != 0 ? std::max(0, std::min(3, kmax - 2)) : 0;
+  DBuf tmp(be, sizeof(double) * std::max(block > 1 ? 4 * block : 1, 2 * lp_keep) * n);
   DBuf sm(be, sizeof(double) * (3 * 64 * 64 + 256));  // subspace matrix, eigvecs, eigvals, coefs
   DBuf aux(be, 256);
   if (!V.p || !AV.p || !diag.p || !x.p || !r.p || !avs.p || !t.p || !tmp.p || !sm.p || !aux.p) {
@@ -285,7 +287,16 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
           conv = rn < tol;
           break;
         }
-        // restart from the FP64-exact pair
+        // restart from the FP64-exact pair, keeping the next Ritz vectors of
+        // the current subspace (their reduced-precision products; diagonal
+        // block) with their couplings to the exact pair from its exact product
+        const int keep = std::max(0, std::min(lp_keep, k - 1));
+        for (int i = 0; i < keep; ++i) {
+          std::vector<double> sc = ritz_coef(i + 1);
+          put(be, dcoef, sc);
+          launch_combine(be, V.d(), n, k, dcoef, tmp.d() + (long long)i * n, n);
+          launch_combine(be, AV.d(), n, k, dcoef, tmp.d() + (long long)(lp_keep + i) * n, n);
+        }
         v0_exact = true;
         const double f = 1.0 / std::sqrt(xx);
         scale_by(x.d(), f);
@@ -293,8 +304,29 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
         scale_by(r.d(), f);
         be.note(cudaMemcpyAsync(V.d(), x.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()), "copy");
         be.note(cudaMemcpyAsync(AV.d(), avs.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()), "copy");
-        k = 1;
+        std::fill(H.begin(), H.end(), 0.0);
         H[0] = theta;
+        for (int i = 0; i < keep; ++i) {
+          be.note(cudaMemcpyAsync(V.d() + (long long)(i + 1) * n, tmp.d() + (long long)i * n, sizeof(double) * n,
+                                  cudaMemcpyDeviceToDevice, be.stream()),
+                  "copy");
+          be.note(cudaMemcpyAsync(AV.d() + (long long)(i + 1) * n, tmp.d() + (long long)(lp_keep + i) * n,
+                                  sizeof(double) * n, cudaMemcpyDeviceToDevice, be.stream()),
+                  "copy");
+        }
+        // orthonormal Ritz vectors: re-orthogonalise against the refreshed x
+        // (x was rescaled, the others are unit and mutually orthogonal)
+        for (int i = 0; i < keep; ++i) {
+          double* vi = V.d() + (long long)(i + 1) * n;
+          const double c0 = dot1(vi, V.d());
+          std::vector<double> cc = {c0};
+          put(be, dcoef, cc);
+          launch_axpy_multi(be, V.d(), n, 1, dcoef, -1.0, vi, n);
+          H[(size_t)(i + 1) * kmax + (i + 1)] = w[order[i + 1]];
+          const double hc = dot1(vi, AV.d());  // exact coupling <u_i, A x>
+          H[(size_t)(i + 1) * kmax] = H[(size_t)(i + 1)] = hc;
+        }
+        k = 1 + keep;
         restarted = true;
       }
     } else {

@@ -308,7 +308,12 @@ struct TcSmem {
   static constexpr int CB2 = TC_M * CH_BYTES;   // one K chunk of B2 (all 128 rows)
   static constexpr int B2 = TC_MC * ES / CH_BYTES * CB2;  // T^T of all products, K = TC_MC
   static constexpr int A2 = TC_M * CH_BYTES;    // L rows, one K chunk (two buffers)
-  static constexpr int total = NS * (A1 + B1 + B2 + 2 * A2) + 1024;
+  // GEMM1's two operand buffers and GEMM2's two L buffers are never live at
+  // the same time (the phases of an m-step are separated by completed MMAs),
+  // so they share one region
+  static constexpr int G1 = 2 * NS * (A1 + B1), G2 = 2 * NS * A2;
+  static constexpr int R1 = G1 > G2 ? G1 : G2;
+  static constexpr int total = R1 + NS * B2 + 1024;
 };
 
 template <int TF32>
@@ -324,11 +329,12 @@ __global__ void __launch_bounds__(TC_NT, 2)
   constexpr int EPC = CH_BYTES / ES;              // elements per K chunk
   constexpr uint32_t SBO_FULL = (CH_BYTES / 16) * 128;
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* const sA1 = smem;                          // planes at + p * S::A1
-  unsigned char* const sB1 = smem + S::NS * S::A1;          // planes at + p * S::B1
-  unsigned char* const sB2 = sB1 + S::NS * S::B1;           // planes at + p * S::B2
-  unsigned char* const sA2 = sB2 + S::NS * S::B2;           // buffer b, plane p at + (b * NS + p) * S::A2
-  __shared__ uint64_t lbar1, mbar1, lbar2[2], mbar2[2];
+  unsigned char* const sR1 = smem;            // GEMM1 buffers, or GEMM2 L buffers
+  unsigned char* const sB2 = smem + S::R1;    // planes at + p * S::B2
+  unsigned char* const sA2 = sR1;             // buffer b, plane p at + (b * NS + p) * S::A2
+  auto sA1 = [&](int b) { return sR1 + b * S::NS * (S::A1 + S::B1); };          // plane p at + p * S::A1
+  auto sB1 = [&](int b) { return sR1 + b * S::NS * (S::A1 + S::B1) + S::NS * S::A1; };  // plane p at + p * S::B1
+  __shared__ uint64_t lbar1[2], mbar1[2], lbar2[2], mbar2[2];
   __shared__ uint32_t tbase;
   __shared__ int bad;
   __shared__ float salpha[TC_M / 16];
@@ -343,8 +349,10 @@ __global__ void __launch_bounds__(TC_NT, 2)
   double* part = TL.poff >= 0 ? part_all : nullptr;
 
   if (tid == 0) {
-    bar_init(&lbar1);
-    bar_init(&mbar1);
+    bar_init(&lbar1[0]);
+    bar_init(&lbar1[1]);
+    bar_init(&mbar1[0]);
+    bar_init(&mbar1[1]);
     bar_init(&lbar2[0]);
     bar_init(&lbar2[1]);
     bar_init(&mbar2[0]);
@@ -360,8 +368,8 @@ __global__ void __launch_bounds__(TC_NT, 2)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tD1 = tbase, tD2 = tbase + 64;
   // barrier bookkeeping (thread 0 only): phases and outstanding completions
-  uint32_t pl1 = 0, pm1 = 0, pl2[2] = {0, 0}, pm2[2] = {0, 0};
-  int l1_out = 0, m1_out = 0, l2_out[2] = {0, 0}, m2_out[2] = {0, 0};
+  uint32_t pl1[2] = {0, 0}, pm1[2] = {0, 0}, pl2[2] = {0, 0}, pm2[2] = {0, 0};
+  int l1_out[2] = {0, 0}, m1_out[2] = {0, 0}, l2_out[2] = {0, 0}, m2_out[2] = {0, 0};
   int g2_steps = 0;
   bool d2 = false;
   int where_c = -1, where_m0 = -1, where_s = -1;
@@ -372,8 +380,8 @@ __global__ void __launch_bounds__(TC_NT, 2)
       out = 0;
     } else {
       if (!bad && atomicCAS(flag, 0, 1) == 0) {
-        const int which = bar == &lbar1 ? 1 : bar == &mbar1 ? 2 : bar == &lbar2[0] ? 3 : bar == &lbar2[1] ? 4
-                        : bar == &mbar2[0] ? 5 : 6;
+        const int which = (bar == &lbar1[0] || bar == &lbar1[1]) ? 1 : (bar == &mbar1[0] || bar == &mbar1[1]) ? 2
+                        : bar == &lbar2[0] ? 3 : bar == &lbar2[1] ? 4 : bar == &mbar2[0] ? 5 : 6;
         flag[1] = blockIdx.x;
         flag[2] = which;
         flag[3] = where_c;
@@ -398,24 +406,27 @@ __global__ void __launch_bounds__(TC_NT, 2)
       const int mc = min(TC_MC, m - m0);
       const int mc16 = (mc + 15) & ~15;
       // ---- GEMM1: D1[t*rp + j][i] = sum_k R_t[col0 + j][k] X[m0 + i][k] ----
+      // two operand buffers: the copies of K chunk kc+1 run while chunk kc's
+      // MMAs do; the region is shared with GEMM2's L buffers, so the previous
+      // GEMM2 MMAs (which also read B2, rewritten below) finish first
       if (tid == 0) {
+        drain(&mbar2[0], pm2[0], m2_out[0]);
+        drain(&mbar2[1], pm2[1], m2_out[1]);
         const int nch = (XB.img.kb + CH_BYTES - 1) / CH_BYTES;
         const int xg0 = m0 / 8, xng = min(mc16 / 8, XB.img.rg - xg0);
-        for (int kc = 0; kc < nch && !bad; ++kc) {
-          where_s = kc;
-          const int kcm = chunk_w(XB.img, kc) / 16;
-          const uint32_t rowb = kcm * 128;  // bytes of one row group in this chunk
+        auto issue1 = [&](int kc, int b) {
+          const uint32_t rowb = (chunk_w(XB.img, kc) / 16) * 128;  // bytes of one row group in this chunk
           uint32_t bytes = (xng > 0 ? xng * rowb : 0) * S::NS;
           for (int t = 0; t < pc; ++t) {
             const int ng = min(rp / 8, tasks[C.t0 + t].R.rg - TL.col0 / 8);
             if (ng > 0) bytes += ng * rowb * S::NS;
           }
-          expect_tx(&lbar1, bytes);
-          l1_out = 1;
+          expect_tx(&lbar1[b], bytes);
+          l1_out[b] = 1;
           if (xng > 0) {
             const long long xo = chunk_off(XB.img, kc) + (long long)xg0 * rowb;
-            bulk_g2s(sB1, xh + xo, xng * rowb, &lbar1);
-            if (!TF32) bulk_g2s(sB1 + S::B1, xl + xo, xng * rowb, &lbar1);
+            bulk_g2s(sB1(b), xh + xo, xng * rowb, &lbar1[b]);
+            if (!TF32) bulk_g2s(sB1(b) + S::B1, xl + xo, xng * rowb, &lbar1[b]);
           }
           for (int t = 0; t < pc; ++t) {
             const Img R = tasks[C.t0 + t].R;
@@ -423,27 +434,38 @@ __global__ void __launch_bounds__(TC_NT, 2)
             if (ng <= 0) continue;
             const long long ro = chunk_off(R, kc) + (long long)(TL.col0 / 8) * rowb;
             const uint32_t dst = (uint32_t)(t * rp / 8) * rowb;
-            bulk_g2s(sA1 + dst, ops_hi + ro, ng * rowb, &lbar1);
-            if (!TF32) bulk_g2s(sA1 + S::A1 + dst, ops_lo + ro, ng * rowb, &lbar1);
+            bulk_g2s(sA1(b) + dst, ops_hi + ro, ng * rowb, &lbar1[b]);
+            if (!TF32) bulk_g2s(sA1(b) + S::A1 + dst, ops_lo + ro, ng * rowb, &lbar1[b]);
           }
-          drain(&lbar1, pl1, l1_out);
+        };
+        if (!bad && nch > 0) issue1(0, 0);
+        for (int kc = 0; kc < nch && !bad; ++kc) {
+          where_s = kc;
+          const int b = kc & 1, bn = (kc + 1) & 1;
+          if (kc + 1 < nch) {
+            drain(&mbar1[bn], pm1[bn], m1_out[bn]);  // chunk kc-1's MMAs read buffer bn
+            if (bad) break;
+            issue1(kc + 1, bn);
+          }
+          drain(&lbar1[b], pl1[b], l1_out[b]);
           if (bad) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
+          const int kcm = chunk_w(XB.img, kc) / 16;
+          const uint32_t rowb = kcm * 128;
           const uint32_t id = idesc(TF32 ? 2 : 1, mc16);
           for (int ks = 0; ks < kcm / 2; ++ks)
             for (int pr = 0; pr < NPROD; ++pr) {
-              const unsigned char* a = sA1 + (pr == 2 ? S::A1 : 0);
-              const unsigned char* b = sB1 + (pr == 1 ? S::B1 : 0);
+              const unsigned char* a = sA1(b) + (pr == 2 ? S::A1 : 0);
+              const unsigned char* bb = sB1(b) + (pr == 1 ? S::B1 : 0);
               const uint32_t acc = (kc > 0 || ks > 0 || pr > 0) ? 1u : 0u;
-              mma<TF32>(tD1, sdesc(smem_u32(a) + ks * 256, rowb), sdesc(smem_u32(b) + ks * 256, rowb), id, acc);
+              mma<TF32>(tD1, sdesc(smem_u32(a) + ks * 256, rowb), sdesc(smem_u32(bb) + ks * 256, rowb), id, acc);
             }
-          commit(&mbar1);
-          m1_out = 1;
-          drain(&mbar1, pm1, m1_out);
+          commit(&mbar1[b]);
+          m1_out[b] = 1;
         }
-        // the T pass rewrites B2: GEMM2 MMAs still reading it must be done
-        drain(&mbar2[0], pm2[0], m2_out[0]);
-        drain(&mbar2[1], pm2[1], m2_out[1]);
+        // D1 complete before the T pass; the region is free for GEMM2's L buffers
+        drain(&mbar1[0], pm1[0], m1_out[0]);
+        drain(&mbar1[1], pm1[1], m1_out[1]);
       }
       __syncthreads();
       if (bad) break;
@@ -559,8 +581,10 @@ __global__ void __launch_bounds__(TC_NT, 2)
   }
   // every copy and MMA of this CTA done (bounded) before TMEM is read or released
   if (tid == 0) {
-    drain(&lbar1, pl1, l1_out);
-    drain(&mbar1, pm1, m1_out);
+    for (int b = 0; b < 2; ++b) {
+      drain(&lbar1[b], pl1[b], l1_out[b]);
+      drain(&mbar1[b], pm1[b], m1_out[b]);
+    }
     for (int b = 0; b < 2; ++b) {
       drain(&lbar2[b], pl2[b], l2_out[b]);
       drain(&mbar2[b], pm2[b], m2_out[b]);
@@ -875,6 +899,7 @@ void launch_reduce_splits(CudaBackend& be, const SplitRed* reds, int nreds, cons
 void release_tc_plan(void* p);
 
 bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec, int variant, int precision) {
+  if (!be.ok()) return false;
   TcPlan* plan = (TcPlan*)d.tc;
   if (plan && (d.tc_gen != tl.gen || plan->precision != precision)) {
     cudaStreamSynchronize(be.stream());
@@ -1000,7 +1025,7 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
 void enqueue_tasks_tc(CudaBackend& be, DevList& d, const double* xv, double* yv, int nvec, long long xs,
                       long long ys, int precision, int variant) {
   TcPlan* plan = (TcPlan*)d.tc;
-  if (!plan) return;
+  if (!plan || !be.ok()) return;
   TcVariant& V = plan->var[variant];
   if (V.ntiles == 0) return;
   be.note(cudaMemsetAsync(plan->flag, 0, 8 * sizeof(int), be.stream()), "tensor-core flag");
