@@ -259,6 +259,8 @@ typedef struct tns_step_stats {
   long long length;         /* two-site wavefunction length */
   int bond_dim;             /* new dimension of bond site+1 */
   long long kernel_launches; /* launches of the engine's own CUDA kernels in the call */
+  int exact_products;       /* FP64 products among iters (reduced-precision refreshes; 0 on the FP64 path) */
+  double exact_seconds;     /* device time of those FP64 products */
 } tns_step_stats;
 
 /* One two-site step of a sweep at (site, site+1) (one "DMRG iteration cycle",

@@ -47,7 +47,8 @@ class StepStats(C.Structure):
     _fields_ = [("energy", C.c_double), ("discarded", C.c_double), ("iters", C.c_int), ("converged", C.c_int),
                 ("heff_flops", C.c_double), ("heff_seconds", C.c_double), ("env_seconds", C.c_double),
                 ("svd_seconds", C.c_double), ("seconds", C.c_double), ("length", C.c_longlong),
-                ("bond_dim", C.c_int), ("kernel_launches", C.c_longlong)]
+                ("bond_dim", C.c_int), ("kernel_launches", C.c_longlong), ("exact_products", C.c_int),
+                ("exact_seconds", C.c_double)]
 
 
 _LIBS = {}

@@ -17,7 +17,7 @@
 namespace tns {
 namespace {
 
-constexpr int SY_NT = 256;
+constexpr int SY_NT = 512;
 constexpr int SY_WARPS = SY_NT / 32;
 
 __device__ __forceinline__ double wsum(double v) {

@@ -96,6 +96,8 @@ struct Acc {
   double heff_ms = 0, env_ms = 0, svd_ms = 0;
   long long matvecs = 0;
   double flops = 0;
+  int exact_products = 0;  // FP64 products of the reduced-precision form (refreshes)
+  double exact_ms = 0;
 };
 
 int check(CudaBackend& be, std::string& err) {
@@ -159,6 +161,7 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
     get(be, h, dscal + 1, 1);
     return h[0];
   };
+  const int lowp = precision != 0;
   // nv products in one launch (the block of Davidson vectors shares every
   // operator block read)
   auto matvec = [&](const double* in, double* out, int nv, int prec) {
@@ -169,6 +172,10 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
       acc->heff_ms += ms;
       acc->matvecs += nv;
       acc->flops += st.heff.flops * nv;
+      if (lowp && prec == 0) {
+        acc->exact_products += nv;
+        acc->exact_ms += ms;
+      }
     }
   };
   auto scale_by = [&](double* v, double f) {
@@ -198,7 +205,6 @@ int davidson(Engine& E, CudaBackend& be, double* X, double tol, int max_iter, in
   int k = 0, it = 0, nnew = 1;
   double theta = 0.0, rn = 1e300;
   bool conv = false;
-  const int lowp = precision != 0;
   double fp64_res = 1e300;
   // reduced precision: the start vector's product is reduced too (the first
   // phase only has to cut the residual by 1e-3); V_0 carries an exact FP64
@@ -1029,6 +1035,8 @@ static int backend_step(tns::Engine& E, int k, bool ltr, const tns_sweep_opts* o
     stats->length = length ? length : (long long)(X.bytes / 8);
     stats->bond_dim = (int)E.bonds()[k + 1].total;
     stats->kernel_launches = be.launches - launches0;
+    stats->exact_products = acc.exact_products;
+    stats->exact_seconds = acc.exact_ms * 1e-3;
   }
   return 0;
 }

@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(TC_NT, 2)
                const TcChunk* __restrict__ chunks, const unsigned char* __restrict__ ops_hi,
                const unsigned char* __restrict__ ops_lo, const unsigned char* __restrict__ x_hi,
                const unsigned char* __restrict__ x_lo, long long x_bytes, const XBlock* __restrict__ xblocks,
-               double* yv, long long ys, int* flag, double* part_all, long long psize) {
+               double* yv, long long ys, int* flag, double* part_all, long long psize, int nv) {
   using S = TcSmem<TF32>;
   constexpr int ES = S::ES;
   constexpr int NPROD = TF32 ? 1 : 3;
@@ -339,9 +339,10 @@ __global__ void __launch_bounds__(TC_NT, 2)
   __shared__ int bad;
   __shared__ float salpha[TC_M / 16];
   const int tid = threadIdx.x;
-  const TcTile TL = tiles[blockIdx.x];
+  // the vectors of one tile piece are adjacent CTAs (they read the same operator blocks)
+  const TcTile TL = tiles[blockIdx.x / nv];
   const Group G = groups[TL.g];
-  const int vec = blockIdx.y;
+  const int vec = blockIdx.x % nv;
   const unsigned char* xh = x_hi + (long long)vec * x_bytes;
   const unsigned char* xl = TF32 ? nullptr : x_lo + (long long)vec * x_bytes;
   const int rp = (TL.ncols + 15) & ~15;  // GEMM2 N; rows of one product in the GEMM1 stack
@@ -778,6 +779,19 @@ void split_plan(const std::vector<TcTask>& tasks, std::vector<TcTile>& tiles, co
     R.nsplit = made + 1;
     reds.push_back(R);
   }
+  // costliest pieces first: CTAs are dispatched in index order, so the long
+  // pieces start in the first wave and the short ones fill in behind them
+  {
+    std::vector<double> pc(out.size(), 0.0);
+    for (size_t i = 0; i < out.size(); ++i)
+      for (int c = out[i].c0; c < out[i].c1; ++c) pc[i] += ccost(chunks[c], out[i]);
+    std::vector<int> ord(out.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return pc[a] > pc[b]; });
+    std::vector<TcTile> sorted(out.size());
+    for (size_t i = 0; i < ord.size(); ++i) sorted[i] = out[ord[i]];
+    out.swap(sorted);
+  }
   tiles.swap(out);
 }
 
@@ -1038,17 +1052,17 @@ void enqueue_tasks_tc(CudaBackend& be, DevList& d, const double* xv, double* yv,
     be.launches++;
     be.note(cudaGetLastError(), "input images");
   }
-  dim3 grid(V.ntiles, nvec);
+  const unsigned grid = (unsigned)V.ntiles * (unsigned)nvec;
   if (precision == TNS_TF32)
     k_tasks_tc<1><<<grid, TC_NT, TcSmem<1>::total, be.stream()>>>(plan->tasks, d.groups, V.tiles, plan->chunks,
                                                                    plan->ops_hi, plan->ops_lo, plan->x_hi, plan->x_lo,
                                                                    plan->x_bytes, plan->xblocks, yv, ys, plan->flag,
-                                                                   V.part, V.psize);
+                                                                   V.part, V.psize, nvec);
   else
     k_tasks_tc<0><<<grid, TC_NT, TcSmem<0>::total, be.stream()>>>(plan->tasks, d.groups, V.tiles, plan->chunks,
                                                                    plan->ops_hi, plan->ops_lo, plan->x_hi, plan->x_lo,
                                                                    plan->x_bytes, plan->xblocks, yv, ys, plan->flag,
-                                                                   V.part, V.psize);
+                                                                   V.part, V.psize, nvec);
   be.launches++;
   be.note(cudaGetLastError(), "k_tasks_tc");
   if (V.nreds > 0) launch_reduce_splits(be, V.reds, V.nreds, d.groups, V.part, V.psize, yv, ys, nvec);
