@@ -35,7 +35,8 @@ constexpr double kRounds[kNumVariants] = {1.0, 2.0, 4.0};
 struct FpVariant {
   bool planned = false;
   Tile* tiles = nullptr;
-  int ncls[3] = {0, 0, 0};   // tiles per size class (contiguous, class 0 first)
+  int ncls[4] = {0, 0, 0, 0};  // tiles per size class (contiguous, class 0 first)
+  double ccost[4] = {0, 0, 0, 0};  // estimated FMAs per class (the costliest runs on the launching stream)
   int ntiles = 0;
   SplitRed* reds = nullptr;  // split tiles to reduce after the product kernels
   int nreds = 0;
@@ -73,6 +74,11 @@ struct DevList {
   Tile* wtiles = nullptr;    // 32 x 16 warp tiles of the FP64 tensor (DMMA) kernel
   int nwtiles = 0;
   FpVariant fv[kNumVariants];
+  // FP64 output tiles per size class with their estimated FMAs (host; shared
+  // by the schedule variants, which differ only in how they cut the tiles)
+  bool fp_tiled = false;
+  std::vector<Tile> fp_tiles[4];
+  std::vector<double> fp_cost[4];
   // tensor-core form (precision != FP64)
   void* tc = nullptr;
   long long tc_gen = -1;
@@ -139,6 +145,10 @@ class CudaBackend : public Backend {
   std::vector<std::pair<void*, size_t>> scratch_ = std::vector<std::pair<void*, size_t>>(8, {nullptr, 0});
   cudaStream_t gstream_ = nullptr;  // side stream for graph capture and replay
   cudaEvent_t gev_[2] = {nullptr, nullptr};
+  // forked streams: the FP64 tile classes run side by side (fork/join events)
+  cudaStream_t fstream_[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fev_[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool fork_ready();
   void upload_list(const TaskList& tl, DevList& d);
   void plan_variant(const TaskList& tl, DevList& d, int v);
   bool ensure_part(FpVariant& f, int nvec);

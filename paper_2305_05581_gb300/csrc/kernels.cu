@@ -42,25 +42,51 @@ __device__ __forceinline__ double opR(const Task& t, int j, int k) {
 constexpr int CH = 32;  // chunk of the contracted middle dimension
 
 // tile classes: (threads, outputs per thread, max tile rows, max tile cols);
-// shared memory is sized per class so that small tiles keep many CTAs per SM
+// a group's output block is cut into tall (<= 128 x 32) or wide (<= 32 x 128)
+// tiles, whichever executes fewer FMAs for its products; tiles of at most
+// 32 x 32 (16 x 16) run in the small classes, which keep many CTAs per SM
 constexpr int C0_NT = 32, C0_ACC = 8, C0_TR = 16, C0_TC = 16;
 constexpr int C1_NT = 128, C1_ACC = 8, C1_TR = 32, C1_TC = 32;
-constexpr int C2_NT = 256, C2_ACC = 16, C2_TR = 64, C2_TC = 64;
+constexpr int C2_NT = 256, C2_ACC = 16, C2_TR = 128, C2_TC = 32;  // tall
+constexpr int C3_NT = 256, C3_ACC = 16, C3_TR = 32, C3_TC = 128;  // wide
+constexpr int kFpClasses = 4;
+constexpr int kTallR = 128, kTallC = 32, kWideR = 32, kWideC = 128;
+
+// dynamic shared memory of a class: max(SA, SB) + SR doubles (see the kernel)
+constexpr int fp64_smem(int TR, int TC) {
+  return 8 * ((CH * (TC + 1) > TR * (CH + 1) ? CH * (TC + 1) : TR * (CH + 1)) + CH * (TC + 1));
+}
+
+// FMAs of one product on an nr x nc tile of its output block.  With no
+// identity factor the kernel evaluates L (X R^T) or (L X) R^T, whichever is
+// cheaper on this tile (the intermediate is recomputed per tile: X R^T per
+// row tile, L X per column tile); *ordb tells which
+__host__ __device__ inline long long tile_fmas(const Task& t, int nr, int nc, bool* ordb) {
+  const long long a = nr, b = nc;
+  if (ordb) *ordb = false;
+  if ((t.flags & TF_LI) && (t.flags & TF_RI)) return a * b;
+  if (t.flags & TF_LI) return a * b * t.n;
+  if (t.flags & (TF_RI | TF_XI)) return a * b * t.m;
+  const long long ca = b * t.m * (t.n + a);  // L (X R^T)
+  const long long cb = a * t.n * (t.m + b);  // (L X) R^T
+  if (ordb) *ordb = cb < ca;
+  return cb < ca ? cb : ca;
+}
 
 template <int NT, int ACC, int TR, int TC>
 __global__ void __launch_bounds__(NT, NT >= 256 ? 2 : NT >= 128 ? 4 : 16) k_tasks_fp64(const Task* __restrict__ tasks, const Group* __restrict__ groups,
                                                    const Tile* __restrict__ tiles, int tile0, const double* xv,
                                                    double* yv, long long xs, long long ys, double* part,
-                                                   long long psize) {
+                                                   long long psize, int nv) {
   constexpr int SA = CH * (TC + 1);  // L (X R^T): CH rows of X R^T, TC columns
   constexpr int SB = TR * (CH + 1);  // (L X) R^T: TR rows of L X, CH columns
-  constexpr int SR = CH * (TC + 1);  // L (X R^T): a K slice of the tile's R rows, transposed
   constexpr int TE = CH * TC / NT;   // elements of X R^T per thread and chunk (upper bound)
-  __shared__ double S[(SA > SB ? SA : SB) + SR];
-  double* const Rt = S + (SA > SB ? SA : SB);
-  const Tile T = tiles[tile0 + blockIdx.x];
+  extern __shared__ double S[];      // max(SA, SB) + SR doubles, SR = CH * (TC + 1)
+  double* const Rt = S + (SA > SB ? SA : SB);  // L (X R^T): a K slice of the tile's R rows, transposed
+  // the vectors of one tile piece are adjacent CTAs (they read the same operator blocks)
+  const Tile T = tiles[tile0 + blockIdx.x / nv];
   const Group G = groups[T.g];
-  const int vec = blockIdx.y;
+  const int vec = blockIdx.x % nv;
   const double* X0 = xv ? xv + (long long)vec * xs : nullptr;
   double* Y = yv + (long long)vec * ys + G.yoff;
   const int nc = T.ncols, nr = T.nrows;
@@ -92,6 +118,8 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? 2 : NT >= 128 ? 4 : 16) k_task
     const long long sXi = (f & TF_XT) ? 1 : tk.n, sXk = (f & TF_XT) ? tk.m : 1;
     const double* pR = tk.R;
     const long long sRj = (f & TF_RT) ? 1 : tk.n, sRk = (f & TF_RT) ? tk.r : 1;
+    bool ordb;
+    tile_fmas(tk, nr, nc, &ordb);
     if ((f & TF_LI) && (f & TF_RI)) {
 #pragma unroll
       for (int u = 0; u < ACC; ++u)
@@ -126,7 +154,7 @@ __global__ void __launch_bounds__(NT, NT >= 256 ? 2 : NT >= 128 ? 4 : 16) k_task
         for (int k = 0; k < tk.m; ++k) s = fma(__ldg(lr + k * sLk), __ldg(rr + k * sRk), s);
         acc[u] = fma(a, s, acc[u]);
       }
-    } else if (!(f & TF_ORDB)) {
+    } else if (!ordb) {
       // L (X R^T): chunks of CH rows of X
       for (int m0 = 0; m0 < tk.m; m0 += CH) {
         const int mc = min(CH, tk.m - m0);
@@ -906,7 +934,32 @@ CudaBackend::~CudaBackend() {
   if (gstream_) cudaStreamDestroy(gstream_);
   for (cudaEvent_t e : gev_)
     if (e) cudaEventDestroy(e);
+  for (cudaStream_t f : fstream_)
+    if (f) cudaStreamDestroy(f);
+  for (cudaEvent_t e : fev_)
+    if (e) cudaEventDestroy(e);
   if (own_ && stream_) cudaStreamDestroy(stream_);
+}
+
+bool CudaBackend::fork_ready() {
+  if (fstream_[0]) return true;
+  bool good = true;
+  for (int i = 0; i < 3 && good; ++i) good = cudaStreamCreateWithFlags(&fstream_[i], cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < 4 && good; ++i) good = cudaEventCreateWithFlags(&fev_[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!good) {
+    cudaGetLastError();
+    for (cudaStream_t& f : fstream_)
+      if (f) {
+        cudaStreamDestroy(f);
+        f = nullptr;
+      }
+    for (cudaEvent_t& e : fev_)
+      if (e) {
+        cudaEventDestroy(e);
+        e = nullptr;
+      }
+  }
+  return good;
 }
 
 void CudaBackend::note(cudaError_t e, const char* what) {
@@ -1006,14 +1059,6 @@ void CudaBackend::free_list(DevList& d) {
   d = DevList();
 }
 
-// estimated cost of one product (flops of the cheaper chain)
-static double task_cost(const Task& t) {
-  const double q = t.q, m = t.m, n = t.n, r = t.r;
-  if ((t.flags & TF_LI) && (t.flags & TF_RI)) return m * n;
-  if (t.flags & (TF_LI | TF_RI | TF_XI)) return 2.0 * std::max(q * m * n, std::max(m * n * r, q * m * r));
-  return std::min(2.0 * m * r * (n + q), 2.0 * q * n * (m + r));
-}
-
 void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
   free_list(d);
   d.tasks = dev_copy(tl.tasks, *this);
@@ -1041,64 +1086,121 @@ void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
   note(cudaStreamSynchronize(stream_), "work list upload");
 }
 
-// schedule variant v of the FP64 kernels: tiles of at most 64 x 64 in size
-// classes; a tile whose task list is long is cut into pieces of similar cost
-// (split-K), each written to a partial tile and summed afterwards in piece
-// order, so that every class fills the GPU and no CTA walks a much longer
-// list than the rest
-void CudaBackend::plan_variant(const TaskList& tl, DevList& d, int v) {
-  FpVariant& f = d.fv[v];
-  if (f.planned) return;
-  std::vector<Tile> cls[3];
-  std::vector<double> cost[3];
-  double ctot[3] = {0, 0, 0};
-  std::vector<double> gcost(tl.groups.size(), 0.0);
-  for (int g = 0; g < (int)tl.groups.size(); ++g)
-    for (int i = tl.groups[g].t0; i < tl.groups[g].t1; ++i) gcost[g] += task_cost(tl.tasks[i]);
+// estimated fixed cost of one product on one tile (loads, barriers), in FMAs
+constexpr double kTaskOverhead = 512.0;
+
+// cut an extent into p near-equal parts of at most mx
+static std::vector<std::pair<int, int>> cut_extent(int len, int mx) {
+  std::vector<std::pair<int, int>> out;
+  const int p = (len + mx - 1) / mx;
+  for (int i = 0, o = 0; i < p; ++i) {
+    const int w = len / p + (i < len % p ? 1 : 0);
+    out.push_back({o, w});
+    o += w;
+  }
+  return out;
+}
+
+// FP64 output tiles of every group: tall or wide, whichever executes fewer
+// FMAs over the group's products (fixed overhead per product and tile
+// included), each tile in the smallest class it fits
+static void fp64_tiles(const TaskList& tl, DevList& d) {
+  for (int c = 0; c < kFpClasses; ++c) {
+    d.fp_tiles[c].clear();
+    d.fp_cost[c].clear();
+  }
   for (int g = 0; g < (int)tl.groups.size(); ++g) {
     const Group& G = tl.groups[g];
-    for (int r0 = 0; r0 < G.q; r0 += 64)
-      for (int c0 = 0; c0 < G.r; c0 += 64) {
+    if (G.q <= 0 || G.r <= 0) continue;
+    std::vector<std::pair<int, int>> rows[2] = {cut_extent(G.q, kTallR), cut_extent(G.q, kWideR)};
+    std::vector<std::pair<int, int>> cols[2] = {cut_extent(G.r, kTallC), cut_extent(G.r, kWideC)};
+    double best = -1;
+    int pick = 0;
+    for (int o = 0; o < 2; ++o) {
+      double c = 0;
+      for (auto& rr : rows[o])
+        for (auto& cc : cols[o])
+          for (int t = G.t0; t < G.t1; ++t) c += (double)tile_fmas(tl.tasks[t], rr.second, cc.second, nullptr) + kTaskOverhead;
+      if (best < 0 || c < best) {
+        best = c;
+        pick = o;
+      }
+    }
+    for (auto& rr : rows[pick])
+      for (auto& cc : cols[pick]) {
         Tile t;
         t.g = g;
-        t.row0 = r0;
-        t.col0 = c0;
-        t.nrows = std::min(64, G.q - r0);
-        t.ncols = std::min(64, G.r - c0);
+        t.row0 = rr.first;
+        t.col0 = cc.first;
+        t.nrows = rr.second;
+        t.ncols = cc.second;
         t.t0 = G.t0;
         t.t1 = G.t1;
         t.poff = -1;
-        int c = (t.nrows <= C0_TR && t.ncols <= C0_TC) ? 0 : (t.nrows <= C1_TR && t.ncols <= C1_TC) ? 1 : 2;
-        const double w = gcost[g] * (double)t.nrows * t.ncols / std::max(1.0, (double)G.q * G.r);
-        cls[c].push_back(t);
-        cost[c].push_back(w);
-        ctot[c] += w;
+        double w = 0;
+        for (int k = G.t0; k < G.t1; ++k) w += (double)tile_fmas(tl.tasks[k], t.nrows, t.ncols, nullptr) + kTaskOverhead;
+        const int c = (t.nrows <= C0_TR && t.ncols <= C0_TC)   ? 0
+                      : (t.nrows <= C1_TR && t.ncols <= C1_TC) ? 1
+                      : (t.ncols <= C2_TC)                     ? 2
+                                                               : 3;
+        d.fp_tiles[c].push_back(t);
+        d.fp_cost[c].push_back(w);
       }
   }
+  d.fp_tiled = true;
+}
+
+// schedule variant v of the FP64 kernels: the tiles of each class, a tile
+// whose task list is long cut into pieces of similar cost (split-K), each
+// written to a partial tile and summed afterwards in piece order, so that
+// every class fills the GPU and no CTA walks a much longer list than the rest
+void CudaBackend::plan_variant(const TaskList& tl, DevList& d, int v) {
+  FpVariant& f = d.fv[v];
+  if (f.planned) return;
+  // kernel attribute once, outside any stream capture: the wide class needs
+  // more than 48 KB of dynamic shared memory
+  static bool attr = false;
+  if (!attr) {
+    note(cudaFuncSetAttribute(k_tasks_fp64<C3_NT, C3_ACC, C3_TR, C3_TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              fp64_smem(C3_TR, C3_TC)),
+         "k_tasks_fp64 shared memory");
+    attr = true;
+  }
+  if (!d.fp_tiled) fp64_tiles(tl, d);
+  double ctot[kFpClasses] = {0, 0, 0, 0};
+  for (int c = 0; c < kFpClasses; ++c)
+    for (double w : d.fp_cost[c]) ctot[c] += w;
   // resident CTAs per SM of each class (registers) x SMs x rounds
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device_);
   const double rounds = kRounds[v];
-  const double slots[3] = {16.0 * sms * rounds, 4.0 * sms * rounds, 2.0 * sms * rounds};
+  const double slots[kFpClasses] = {16.0 * sms * rounds, 4.0 * sms * rounds, 2.0 * sms * rounds,
+                                    2.0 * sms * rounds};
   std::vector<Tile> all;
   std::vector<SplitRed> reds;
   long long poff = 0;
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < kFpClasses; ++c) {
     const double target = std::max(ctot[c] / slots[c], 1.0);
     int count = 0;
-    for (size_t i = 0; i < cls[c].size(); ++i) {
-      Tile t = cls[c][i];
+    const size_t first = all.size();
+    std::vector<double> pcost;  // estimated cost of each piece of this class
+    for (size_t i = 0; i < d.fp_tiles[c].size(); ++i) {
+      const Tile t = d.fp_tiles[c][i];
+      const double tc = d.fp_cost[c][i];
       const int ntask = t.t1 - t.t0;
-      int ns = (int)std::min<double>(ntask, std::ceil(cost[c][i] / target));
+      int ns = (int)std::min<double>(ntask, std::ceil(tc / target));
       ns = std::max(1, std::min(ns, 64));
       if (ns == 1) {
         all.push_back(t);
+        pcost.push_back(tc);
         ++count;
         continue;
       }
-      // cut the task range at equal shares of its cost
+      // cut the task range at equal shares of its cost on this tile
+      std::vector<double> kc(ntask);
       double tot = 0;
-      for (int k = t.t0; k < t.t1; ++k) tot += task_cost(tl.tasks[k]);
+      for (int k = t.t0; k < t.t1; ++k)
+        tot += kc[k - t.t0] = (double)tile_fmas(tl.tasks[k], t.nrows, t.ncols, nullptr) + kTaskOverhead;
       SplitRed R;
       R.g = t.g;
       R.row0 = t.row0;
@@ -1107,9 +1209,9 @@ void CudaBackend::plan_variant(const TaskList& tl, DevList& d, int v) {
       R.ncols = t.ncols;
       R.poff = poff;
       int start = t.t0, made = 0;
-      double acc = 0;
+      double acc = 0, last = 0;
       for (int k = t.t0; k < t.t1 && made < ns - 1; ++k) {
-        acc += task_cost(tl.tasks[k]);
+        acc += kc[k - t.t0];
         if (acc >= tot * (made + 1) / ns) {
           Tile p = t;
           p.t0 = start;
@@ -1117,6 +1219,8 @@ void CudaBackend::plan_variant(const TaskList& tl, DevList& d, int v) {
           p.poff = poff;
           poff += (long long)t.nrows * t.ncols;
           all.push_back(p);
+          pcost.push_back(acc - last);
+          last = acc;
           ++made;
           ++count;
           start = k + 1;
@@ -1128,11 +1232,21 @@ void CudaBackend::plan_variant(const TaskList& tl, DevList& d, int v) {
       p.poff = poff;
       poff += (long long)t.nrows * t.ncols;
       all.push_back(p);
+      pcost.push_back(tot - last);
       ++count;
       R.nsplit = made + 1;
       reds.push_back(R);
     }
+    // costliest pieces first: CTAs are dispatched in index order, so the long
+    // pieces start in the first wave and the short ones fill in behind them
+    std::vector<int> ord(pcost.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return pcost[a] > pcost[b]; });
+    std::vector<Tile> sorted(ord.size());
+    for (size_t i = 0; i < ord.size(); ++i) sorted[i] = all[first + ord[i]];
+    std::copy(sorted.begin(), sorted.end(), all.begin() + first);
     f.ncls[c] = count;
+    f.ccost[c] = ctot[c];
   }
   f.psize = poff;
   f.nreds = (int)reds.size();
@@ -1180,23 +1294,51 @@ void CudaBackend::enqueue_fp64(const DevList& d, int v, const double* xv, double
                                long long ys) {
   if (!ok()) return;
   const FpVariant& f = d.fv[v];
-  int t0 = 0;
-  for (int c = 0; c < 3; ++c) {
-    int n = f.ncls[c];
+  // the classes write disjoint tiles and partial tiles: the costliest class
+  // runs on the launching stream and the others on forked streams beside it
+  // (they fill its tail), joined before the split reduction
+  int order[kFpClasses] = {0, 1, 2, 3};
+  std::stable_sort(order, order + kFpClasses, [&](int a, int b) { return f.ccost[a] > f.ccost[b]; });
+  const int nact = (f.ncls[0] > 0) + (f.ncls[1] > 0) + (f.ncls[2] > 0) + (f.ncls[3] > 0);
+  const bool fork = nact > 1 && fork_ready();
+  if (fork) {
+    note(cudaEventRecord(fev_[0], stream_), "fork");
+    for (int i = 0; i < 3; ++i) note(cudaStreamWaitEvent(fstream_[i], fev_[0], 0), "fork");
+  }
+  int tbeg[kFpClasses];
+  for (int c = 0, t = 0; c < kFpClasses; ++c) {
+    tbeg[c] = t;
+    t += f.ncls[c];
+  }
+  int side = 0;
+  for (int oi = 0; oi < kFpClasses; ++oi) {
+    const int c = order[oi];
+    const int n = f.ncls[c];
     if (n == 0) continue;
-    dim3 grid(n, nvec);
+    const unsigned grid = (unsigned)n * (unsigned)nvec;
+    cudaStream_t s = stream_;
+    if (fork && oi > 0) s = fstream_[side++];
+    const int t0 = tbeg[c];
     if (c == 0)
-      k_tasks_fp64<C0_NT, C0_ACC, C0_TR, C0_TC><<<grid, C0_NT, 0, stream_>>>(d.tasks, d.groups, f.tiles, t0, xv, yv,
-                                                                             xs, ys, f.part, f.psize);
+      k_tasks_fp64<C0_NT, C0_ACC, C0_TR, C0_TC><<<grid, C0_NT, fp64_smem(C0_TR, C0_TC), s>>>(
+          d.tasks, d.groups, f.tiles, t0, xv, yv, xs, ys, f.part, f.psize, nvec);
     else if (c == 1)
-      k_tasks_fp64<C1_NT, C1_ACC, C1_TR, C1_TC><<<grid, C1_NT, 0, stream_>>>(d.tasks, d.groups, f.tiles, t0, xv, yv,
-                                                                             xs, ys, f.part, f.psize);
+      k_tasks_fp64<C1_NT, C1_ACC, C1_TR, C1_TC><<<grid, C1_NT, fp64_smem(C1_TR, C1_TC), s>>>(
+          d.tasks, d.groups, f.tiles, t0, xv, yv, xs, ys, f.part, f.psize, nvec);
+    else if (c == 2)
+      k_tasks_fp64<C2_NT, C2_ACC, C2_TR, C2_TC><<<grid, C2_NT, fp64_smem(C2_TR, C2_TC), s>>>(
+          d.tasks, d.groups, f.tiles, t0, xv, yv, xs, ys, f.part, f.psize, nvec);
     else
-      k_tasks_fp64<C2_NT, C2_ACC, C2_TR, C2_TC><<<grid, C2_NT, 0, stream_>>>(d.tasks, d.groups, f.tiles, t0, xv, yv,
-                                                                             xs, ys, f.part, f.psize);
+      k_tasks_fp64<C3_NT, C3_ACC, C3_TR, C3_TC><<<grid, C3_NT, fp64_smem(C3_TR, C3_TC), s>>>(
+          d.tasks, d.groups, f.tiles, t0, xv, yv, xs, ys, f.part, f.psize, nvec);
     launches++;
     note(cudaGetLastError(), "k_tasks_fp64");
-    t0 += n;
+  }
+  if (fork) {
+    for (int i = 0; i < 3; ++i) {
+      note(cudaEventRecord(fev_[1 + i], fstream_[i]), "join");
+      note(cudaStreamWaitEvent(stream_, fev_[1 + i], 0), "join");
+    }
   }
   if (f.nreds > 0) {
     dim3 grid(std::min(f.nreds, 65535), nvec);
