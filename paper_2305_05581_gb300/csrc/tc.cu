@@ -308,12 +308,11 @@ struct TcSmem {
   static constexpr int CB2 = TC_M * CH_BYTES;   // one K chunk of B2 (all 128 rows)
   static constexpr int B2 = TC_MC * ES / CH_BYTES * CB2;  // T^T of all products, K = TC_MC
   static constexpr int A2 = TC_M * CH_BYTES;    // L rows, one K chunk (two buffers)
-  // GEMM1's two operand buffers and GEMM2's two L buffers are never live at
-  // the same time (the phases of an m-step are separated by completed MMAs),
-  // so they share one region
+  // separate regions for GEMM1's two operand buffers and GEMM2's two L
+  // buffers, so that each GEMM's first copies are issued while the other GEMM
+  // (or the T pass) runs; 113 KB for split-BF16 still leaves two CTAs per SM
   static constexpr int G1 = 2 * NS * (A1 + B1), G2 = 2 * NS * A2;
-  static constexpr int R1 = G1 > G2 ? G1 : G2;
-  static constexpr int total = R1 + NS * B2 + 1024;
+  static constexpr int total = G1 + G2 + NS * B2;
 };
 
 template <int TF32>
@@ -328,12 +327,12 @@ __global__ void __launch_bounds__(TC_NT, 2)
   constexpr int NPROD = TF32 ? 1 : 3;
   constexpr int EPC = CH_BYTES / ES;              // elements per K chunk
   constexpr uint32_t SBO_FULL = (CH_BYTES / 16) * 128;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* const sR1 = smem;            // GEMM1 buffers, or GEMM2 L buffers
-  unsigned char* const sB2 = smem + S::R1;    // planes at + p * S::B2
-  unsigned char* const sA2 = sR1;             // buffer b, plane p at + (b * NS + p) * S::A2
-  auto sA1 = [&](int b) { return sR1 + b * S::NS * (S::A1 + S::B1); };          // plane p at + p * S::A1
-  auto sB1 = [&](int b) { return sR1 + b * S::NS * (S::A1 + S::B1) + S::NS * S::A1; };  // plane p at + p * S::B1
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* const sG1 = smem;                    // GEMM1 operand buffers
+  unsigned char* const sA2 = smem + S::G1;            // GEMM2 L buffers: buffer b, plane p at + (b * NS + p) * S::A2
+  unsigned char* const sB2 = smem + S::G1 + S::G2;    // planes at + p * S::B2
+  auto sA1 = [&](int b) { return sG1 + b * S::NS * (S::A1 + S::B1); };          // plane p at + p * S::A1
+  auto sB1 = [&](int b) { return sG1 + b * S::NS * (S::A1 + S::B1) + S::NS * S::A1; };  // plane p at + p * S::B1
   __shared__ uint64_t lbar1[2], mbar1[2], lbar2[2], mbar2[2];
   __shared__ uint32_t tbase;
   __shared__ int bad;
@@ -394,6 +393,60 @@ __global__ void __launch_bounds__(TC_NT, 2)
     }
   };
 
+  // thread 0's copy issue for the steps (chunk c, X rows m0..m0+63) of this
+  // piece; GEMM1 chunk kc of a step goes to G1 buffer kc & 1, GEMM2 slice st
+  // (product st / nch2, K chunk st % nch2) to G2 buffer (g2_steps + st) & 1
+  auto issue1 = [&](int c, int m0, int kc, int b) {
+    const TcChunk C = chunks[c];
+    const int pc = C.t1 - C.t0;
+    const XBlock XB = xblocks[tasks[C.t0].xb];
+    const int mc16 = (min(TC_MC, XB.m - m0) + 15) & ~15;
+    const int xg0 = m0 / 8, xng = min(mc16 / 8, XB.img.rg - xg0);
+    const uint32_t rowb = (chunk_w(XB.img, kc) / 16) * 128;  // bytes of one row group in this chunk
+    uint32_t bytes = (xng > 0 ? xng * rowb : 0) * S::NS;
+    for (int t = 0; t < pc; ++t) {
+      const int ng = min(rp / 8, tasks[C.t0 + t].R.rg - TL.col0 / 8);
+      if (ng > 0) bytes += ng * rowb * S::NS;
+    }
+    expect_tx(&lbar1[b], bytes);
+    l1_out[b] = 1;
+    if (xng > 0) {
+      const long long xo = chunk_off(XB.img, kc) + (long long)xg0 * rowb;
+      bulk_g2s(sB1(b), xh + xo, xng * rowb, &lbar1[b]);
+      if (!TF32) bulk_g2s(sB1(b) + S::B1, xl + xo, xng * rowb, &lbar1[b]);
+    }
+    for (int t = 0; t < pc; ++t) {
+      const Img R = tasks[C.t0 + t].R;
+      const int ng = min(rp / 8, R.rg - TL.col0 / 8);
+      if (ng <= 0) continue;
+      const long long ro = chunk_off(R, kc) + (long long)(TL.col0 / 8) * rowb;
+      const uint32_t dst = (uint32_t)(t * rp / 8) * rowb;
+      bulk_g2s(sA1(b) + dst, ops_hi + ro, ng * rowb, &lbar1[b]);
+      if (!TF32) bulk_g2s(sA1(b) + S::A1 + dst, ops_lo + ro, ng * rowb, &lbar1[b]);
+    }
+  };
+  auto nchunks1 = [&](int c) { return (xblocks[tasks[chunks[c].t0].xb].img.kb + CH_BYTES - 1) / CH_BYTES; };
+  // the first (up to) two GEMM1 chunks of a step, into free G1 buffers
+  auto prefetch1 = [&](int c, int m0) {
+    const int nch = nchunks1(c);
+    for (int kc = 0; kc < 2 && kc < nch; ++kc) issue1(c, m0, kc, kc);
+  };
+  auto issue2 = [&](int c, int m0, int st, int nch2, int b) {
+    const TcChunk C = chunks[c];
+    const int t = st / nch2, c2 = st % nch2;
+    const Img Lm = tasks[C.t0 + t].L;
+    const int lg0 = TL.row0 / 8, lng = min(TC_M / 8, Lm.rg - lg0);
+    const int lc = (m0 * ES) / CH_BYTES + c2;  // chunk of L's K (= X rows)
+    const uint32_t rowb = (chunk_w(Lm, lc) / 16) * 128;
+    unsigned char* a2 = sA2 + b * S::NS * S::A2;
+    expect_tx(&lbar2[b], lng * rowb * S::NS);
+    l2_out[b] = 1;
+    const long long lo_ = chunk_off(Lm, lc) + (long long)lg0 * rowb;
+    bulk_g2s(a2, ops_hi + lo_, lng * rowb, &lbar2[b]);
+    if (!TF32) bulk_g2s(a2 + S::A2, ops_lo + lo_, lng * rowb, &lbar2[b]);
+  };
+  if (tid == 0 && has_work) prefetch1(TL.c0, 0);
+
   for (int c = TL.c0; c < TL.c1 && !bad; ++c) {
     const TcChunk C = chunks[c];
     const int pc = C.t1 - C.t0;
@@ -406,47 +459,21 @@ __global__ void __launch_bounds__(TC_NT, 2)
       where_m0 = m0;
       const int mc = min(TC_MC, m - m0);
       const int mc16 = (mc + 15) & ~15;
-      // ---- GEMM1: D1[t*rp + j][i] = sum_k R_t[col0 + j][k] X[m0 + i][k] ----
-      // two operand buffers: the copies of K chunk kc+1 run while chunk kc's
-      // MMAs do; the region is shared with GEMM2's L buffers, so the previous
-      // GEMM2 MMAs (which also read B2, rewritten below) finish first
+      const int nch2 = (mc16 * ES + CH_BYTES - 1) / CH_BYTES;
+      const int nsteps = pc * nch2;
       if (tid == 0) {
-        drain(&mbar2[0], pm2[0], m2_out[0]);
-        drain(&mbar2[1], pm2[1], m2_out[1]);
+        // ---- GEMM1: D1[t*rp + j][i] = sum_k R_t[col0 + j][k] X[m0 + i][k] ----
+        // chunks 0 and 1 are in flight (issued while the previous step's
+        // GEMM2 ran); chunk kc+1 >= 2 is copied once chunk kc-1's MMAs have
+        // released its buffer
         const int nch = (XB.img.kb + CH_BYTES - 1) / CH_BYTES;
-        const int xg0 = m0 / 8, xng = min(mc16 / 8, XB.img.rg - xg0);
-        auto issue1 = [&](int kc, int b) {
-          const uint32_t rowb = (chunk_w(XB.img, kc) / 16) * 128;  // bytes of one row group in this chunk
-          uint32_t bytes = (xng > 0 ? xng * rowb : 0) * S::NS;
-          for (int t = 0; t < pc; ++t) {
-            const int ng = min(rp / 8, tasks[C.t0 + t].R.rg - TL.col0 / 8);
-            if (ng > 0) bytes += ng * rowb * S::NS;
-          }
-          expect_tx(&lbar1[b], bytes);
-          l1_out[b] = 1;
-          if (xng > 0) {
-            const long long xo = chunk_off(XB.img, kc) + (long long)xg0 * rowb;
-            bulk_g2s(sB1(b), xh + xo, xng * rowb, &lbar1[b]);
-            if (!TF32) bulk_g2s(sB1(b) + S::B1, xl + xo, xng * rowb, &lbar1[b]);
-          }
-          for (int t = 0; t < pc; ++t) {
-            const Img R = tasks[C.t0 + t].R;
-            const int ng = min(rp / 8, R.rg - TL.col0 / 8);
-            if (ng <= 0) continue;
-            const long long ro = chunk_off(R, kc) + (long long)(TL.col0 / 8) * rowb;
-            const uint32_t dst = (uint32_t)(t * rp / 8) * rowb;
-            bulk_g2s(sA1(b) + dst, ops_hi + ro, ng * rowb, &lbar1[b]);
-            if (!TF32) bulk_g2s(sA1(b) + S::A1 + dst, ops_lo + ro, ng * rowb, &lbar1[b]);
-          }
-        };
-        if (!bad && nch > 0) issue1(0, 0);
         for (int kc = 0; kc < nch && !bad; ++kc) {
           where_s = kc;
           const int b = kc & 1, bn = (kc + 1) & 1;
-          if (kc + 1 < nch) {
-            drain(&mbar1[bn], pm1[bn], m1_out[bn]);  // chunk kc-1's MMAs read buffer bn
+          if (kc + 1 < nch && kc + 1 >= 2) {
+            drain(&mbar1[bn], pm1[bn], m1_out[bn]);
             if (bad) break;
-            issue1(kc + 1, bn);
+            issue1(c, m0, kc + 1, bn);
           }
           drain(&lbar1[b], pl1[b], l1_out[b]);
           if (bad) break;
@@ -464,7 +491,13 @@ __global__ void __launch_bounds__(TC_NT, 2)
           commit(&mbar1[b]);
           m1_out[b] = 1;
         }
-        // D1 complete before the T pass; the region is free for GEMM2's L buffers
+        // the previous step's GEMM2 MMAs (they read B2 and the G2 buffers)
+        // are done before the T pass rewrites B2; this step's first two L
+        // slices are then copied while the T pass runs
+        drain(&mbar2[0], pm2[0], m2_out[0]);
+        drain(&mbar2[1], pm2[1], m2_out[1]);
+        for (int st = 0; st < 2 && st < nsteps && !bad; ++st) issue2(c, m0, st, nch2, (g2_steps + st) & 1);
+        // D1 complete before the T pass
         drain(&mbar1[0], pm1[0], m1_out[0]);
         drain(&mbar1[1], pm1[1], m1_out[1]);
       }
@@ -521,36 +554,16 @@ __global__ void __launch_bounds__(TC_NT, 2)
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int nk2 = mc16 * ES / 32;  // 32-byte MMA k-steps over this X row range
-        const int nch2 = (mc16 * ES + CH_BYTES - 1) / CH_BYTES;
         const uint32_t id = idesc(TF32 ? 2 : 1, rp);
         // two-stage pipeline over the steps s = (product t, K chunk c2): the
         // L slice of step s+1 is copied while step s's MMAs run
-        const int nsteps = pc * nch2;
-        auto issue = [&](int st, int b) {  // bulk copy of step st's L slice into buffer b
-          const int t = st / nch2, c2 = st % nch2;
-          const Img Lm = tasks[C.t0 + t].L;
-          const int lg0 = TL.row0 / 8, lng = min(TC_M / 8, Lm.rg - lg0);
-          const int lc = (m0 * ES) / CH_BYTES + c2;  // chunk of L's K (= X rows)
-          const uint32_t rowb = (chunk_w(Lm, lc) / 16) * 128;
-          unsigned char* a2 = sA2 + b * S::NS * S::A2;
-          expect_tx(&lbar2[b], lng * rowb * S::NS);
-          l2_out[b] = 1;
-          const long long lo_ = chunk_off(Lm, lc) + (long long)lg0 * rowb;
-          bulk_g2s(a2, ops_hi + lo_, lng * rowb, &lbar2[b]);
-          if (!TF32) bulk_g2s(a2 + S::A2, ops_lo + lo_, lng * rowb, &lbar2[b]);
-        };
-        if (nsteps > 0) {
-          const int b0 = g2_steps & 1;
-          drain(&mbar2[b0], pm2[b0], m2_out[b0]);  // buffer free
-          if (!bad) issue(0, b0);
-        }
         for (int st = 0; st < nsteps && !bad; ++st) {
           const int b = (g2_steps + st) & 1, bn = (g2_steps + st + 1) & 1;
           where_s = 1000 + st;
-          if (st + 1 < nsteps) {
+          if (st + 1 < nsteps && st + 1 >= 2) {
             drain(&mbar2[bn], pm2[bn], m2_out[bn]);  // the MMAs of step st-1 read buffer bn
             if (bad) break;
-            issue(st + 1, bn);
+            issue2(c, m0, st + 1, nch2, bn);
           }
           drain(&lbar2[b], pl2[b], l2_out[b]);
           if (bad) break;
@@ -576,6 +589,14 @@ __global__ void __launch_bounds__(TC_NT, 2)
           m2_out[b] = 1;
         }
         g2_steps += nsteps;
+        // the next step's first GEMM1 chunks (the G1 buffers were released
+        // when this step's D1 completed)
+        if (!bad) {
+          if (m0 + TC_MC < m)
+            prefetch1(c, m0 + TC_MC);
+          else if (c + 1 < TL.c1)
+            prefetch1(c + 1, 0);
+        }
       }
       __syncthreads();
     }
