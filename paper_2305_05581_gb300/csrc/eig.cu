@@ -1,13 +1,18 @@
 // Batched symmetric eigen-decomposition for the truncation (reduced density
-// matrix of each sector of the new bond).  One CTA per matrix:
-//   1. Householder tridiagonalisation T = Q^T A Q (Golub & Van Loan,
-//      "Matrix Computations", Sec. 8.3.1), reflectors kept in the rows of A;
-//   2. explicit Z = Q^T by backward accumulation of the reflectors;
-//   3. implicit symmetric QR steps with the Wilkinson shift and deflation
-//      (Golub & Van Loan Sec. 8.3.3-8.3.5) on (d, e); thread 0 computes the
-//      Givens rotations of a bulge chase, then every thread applies them to its
-//      own columns of Z (rows i, i+1 of Z rotate), so no barrier is needed
-//      inside a chase and the accesses are coalesced.
+// matrix of each sector of the new bond).
+//   k_tridiag, one CTA per matrix: Householder tridiagonalisation
+//      T = Q^T A Q (Golub & Van Loan, "Matrix Computations", Sec. 8.3.1);
+//      reflectors kept in the rows of A (beta on the diagonal), (d, e) to a
+//      scratch array.
+//   k_tqr, one CTA per (matrix, slice of 32 columns of Z):
+//      1. its columns of Z = Q^T, column j = H_{n-3} ... H_0 e_j;
+//      2. implicit symmetric QR steps with the Wilkinson shift and deflation
+//         (Golub & Van Loan Sec. 8.3.3-8.3.5) on its own copy of (d, e): lane 0
+//         computes the Givens rotations of a bulge chase, every lane applies
+//         them to one column (rows i, i+1 rotate).  Every slice runs the same
+//         chase on the same data, so the slices agree bit for bit and need no
+//         communication; the rotation work, which dominates, is spread over
+//         ceil(n / 32) SMs instead of one.
 // Output: eigenvalues w[woff + p] and eigenvector p as ROW p of Z
 // (Z[p * n + i], n x n row-major at off).  A is overwritten.
 #include <cuda_runtime.h>
@@ -36,24 +41,19 @@ __device__ double bsum(double v, double* red) {
   return s;
 }
 
-__global__ void __launch_bounds__(SY_NT) k_syev(double* A, double* Zall, double* w, const long long* off,
-                                                const int* nn, const int* woff, int maxn, int* status) {
+__global__ void __launch_bounds__(SY_NT) k_tridiag(double* A, double* DE, const long long* off, const int* nn,
+                                                   const int* woff, int maxn) {
   extern __shared__ double sm[];
-  double* v = sm;              // Householder vector / rotation cosines
-  double* p = sm + maxn;       // work vector / rotation sines
+  double* v = sm;              // Householder vector
+  double* p = sm + maxn;       // work vector
   double* d = sm + 2 * maxn;   // diagonal of T
   double* e = sm + 3 * maxn;   // sub-diagonal of T (e[i] couples i, i+1)
   __shared__ double red[SY_WARPS];
-  __shared__ int ctl[3];       // lo, hi, done
   const int mi = blockIdx.x;
   const int n = nn[mi];
   if (n <= 0) return;
   double* a = A + off[mi];
-  double* Z = Zall + off[mi];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const double eps = 2.220446049250313e-16;
-
-  // ---- 1. tridiagonalisation ------------------------------------------------
   for (int k = 0; k + 2 < n; ++k) {
     const long long rk = (long long)k * n;
     // x = a[k][k+1 .. n-1] (row k = column k by symmetry)
@@ -109,35 +109,77 @@ __global__ void __launch_bounds__(SY_NT) k_syev(double* A, double* Zall, double*
     }
     d[n - 1] = a[(long long)(n - 1) * n + n - 1];
   }
-  // ---- 2. Z = Q^T = H_{n-3} ... H_0 ----------------------------------------
-  for (long long t = tid; t < (long long)n * n; t += SY_NT) Z[t] = (t / n) == (t % n) ? 1.0 : 0.0;
   __syncthreads();
-  for (int k = n - 3; k >= 0; --k) {
+  // (d, e) of matrix mi at DE + 2 * woff: d[0..n), e[0..n-1)
+  double* de = DE + 2 * (long long)woff[mi];
+  for (int i = tid; i < n; i += SY_NT) {
+    de[i] = d[i];
+    de[n + i] = i + 1 < n ? e[i] : 0.0;
+  }
+}
+
+constexpr int TQ_COLS = 32;   // columns of Z per CTA (one per lane of warp 0)
+constexpr int TQ_NT = 128;    // 4 row phases x 32 columns while building Q^T
+constexpr int TQ_PH = TQ_NT / TQ_COLS;
+
+__global__ void __launch_bounds__(TQ_NT) k_tqr(const double* A, double* Zall, double* w, const double* DE,
+                                               const long long* off, const int* nn, const int* woff, int maxn,
+                                               int* status) {
+  extern __shared__ double sm[];
+  double* v = sm;              // reflector, then rotation cosines
+  double* p = sm + maxn;       // rotation sines
+  double* d = sm + 2 * maxn;
+  double* e = sm + 3 * maxn;
+  __shared__ double red[TQ_PH][TQ_COLS];
+  __shared__ int ctl[3];       // lo, hi, done
+  const int mi = blockIdx.x;
+  const int n = nn[mi];
+  const int j0 = blockIdx.y * TQ_COLS;
+  if (n <= 0 || j0 >= n) return;
+  const int cw = min(TQ_COLS, n - j0);
+  const double* a = A + off[mi];
+  double* Z = Zall + off[mi];
+  const int tid = threadIdx.x, lane = tid & 31, ph = tid / TQ_COLS;
+  const double eps = 2.220446049250313e-16;
+  const double* de = DE + 2 * (long long)woff[mi];
+  for (int i = tid; i < n; i += TQ_NT) {
+    d[i] = de[i];
+    e[i] = de[n + i];
+  }
+  // ---- 1. columns j0 .. j0+cw of Z = Q^T = H_{n-3} ... H_0 ----------------
+  const int jc = j0 + lane;  // this thread's column (lane < cw)
+  for (int r = ph; r < n; r += TQ_PH)
+    if (lane < cw) Z[(long long)r * n + jc] = r == jc ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = 0; k + 2 < n; ++k) {
     const long long rk = (long long)k * n;
     const double beta = a[rk + k];
     if (beta == 0.0) continue;  // uniform across the block
-    for (int j = k + 1 + tid; j < n; j += SY_NT) v[j] = j == k + 1 ? 1.0 : a[rk + j];
+    for (int r = k + 1 + tid; r < n; r += TQ_NT) v[r] = r == k + 1 ? 1.0 : a[rk + r];
     __syncthreads();
-    // rows r >= k+1 of Z: Z[r][k+1:] -= beta (Z[r][k+1:] . v) v
-    for (int r = k + 1 + wid; r < n; r += SY_WARPS) {
-      const long long rr = (long long)r * n;
-      double s = 0.0;
-      for (int j = k + 1 + lane; j < n; j += 32) s += Z[rr + j] * v[j];
-      s = wsum(s) * beta;
-      for (int j = k + 1 + lane; j < n; j += 32) Z[rr + j] -= s * v[j];
-    }
+    double s = 0.0;
+    if (lane < cw)
+      for (int r = k + 1 + ph; r < n; r += TQ_PH) s += v[r] * Z[(long long)r * n + jc];
+    red[ph][lane] = s;
+    __syncthreads();
+    double t = 0.0;
+    for (int q = 0; q < TQ_PH; ++q) t += red[q][lane];
+    t *= beta;
+    if (lane < cw)
+      for (int r = k + 1 + ph; r < n; r += TQ_PH) Z[(long long)r * n + jc] -= t * v[r];
     __syncthreads();
   }
-  // ---- 3. implicit symmetric QR with Wilkinson shift -------------------------
-  if (tid == 0) {
+  // ---- 2. implicit symmetric QR with Wilkinson shift (warp 0) ---------------
+  if (tid >= 32) return;  // no block-wide barrier below
+  if (lane == 0) {
     ctl[1] = n - 1;
     ctl[2] = 0;
   }
-  __syncthreads();
+  __syncwarp();
   const int max_steps = 40 * n + 40;
   int steps = 0;
   for (;;) {
-    if (tid == 0) {
+    if (lane == 0) {
       int hi = ctl[1], lo = 0, done = 0;
       // deflate from the bottom
       while (hi > 0) {
@@ -168,11 +210,13 @@ __global__ void __launch_bounds__(SY_NT) k_syev(double* A, double* Zall, double*
         const double mu = den != 0.0 ? d[hi] - bb / den : d[hi];
         double x = d[lo] - mu, z = e[lo];
         for (int i = lo; i < hi; ++i) {
-          double r = hypot(x, z);
-          double c = 1.0, s = 0.0;
-          if (r != 0.0) {
-            c = x / r;
-            s = z / r;
+          // Givens rotation zeroing z against x; rhypot avoids two divisions
+          double c = 1.0, s = 0.0, r = 0.0;
+          if (x != 0.0 || z != 0.0) {
+            const double ri = rhypot(x, z);
+            c = x * ri;
+            s = z * ri;
+            r = c * x + s * z;
           }
           if (i > lo) e[i - 1] = r;
           const double ai = d[i], aj = d[i + 1], b = e[i];
@@ -192,40 +236,41 @@ __global__ void __launch_bounds__(SY_NT) k_syev(double* A, double* Zall, double*
       ctl[1] = hi;
       ctl[2] = done;
     }
-    __syncthreads();
+    __syncwarp();
     if (ctl[2]) break;
     const int lo = ctl[0], hi = ctl[1];
-    for (int j = tid; j < n; j += SY_NT) {
-      double carry = Z[(long long)lo * n + j];
+    if (lane < cw) {
+      double carry = Z[(long long)lo * n + jc];
       int i = lo;
       // every original row is read once (as y) before its row is written, so
       // the loads of the next 8 rows are issued together ahead of the stores
       for (; i + 8 <= hi; i += 8) {
         double y[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) y[q] = Z[(long long)(i + 1 + q) * n + j];
+        for (int q = 0; q < 8; ++q) y[q] = Z[(long long)(i + 1 + q) * n + jc];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const double c = v[i + q], s = p[i + q];
-          Z[(long long)(i + q) * n + j] = c * carry + s * y[q];
+          Z[(long long)(i + q) * n + jc] = c * carry + s * y[q];
           carry = -s * carry + c * y[q];
         }
       }
       for (; i < hi; ++i) {
-        const double y = Z[(long long)(i + 1) * n + j];
+        const double y = Z[(long long)(i + 1) * n + jc];
         const double c = v[i], s = p[i];
-        Z[(long long)i * n + j] = c * carry + s * y;
+        Z[(long long)i * n + jc] = c * carry + s * y;
         carry = -s * carry + c * y;
       }
-      Z[(long long)hi * n + j] = carry;
+      Z[(long long)hi * n + jc] = carry;
     }
-    __syncthreads();
+    __syncwarp();
     if (++steps > max_steps) {
-      if (tid == 0 && status) atomicExch(status, 1);
+      if (lane == 0 && status) atomicExch(status, 1);
       break;
     }
   }
-  for (int i = tid; i < n; i += SY_NT) w[woff[mi] + i] = d[i];
+  if (blockIdx.y == 0)
+    for (int i = lane; i < n; i += 32) w[woff[mi] + i] = d[i];
 }
 
 }  // namespace
@@ -237,17 +282,26 @@ void launch_syev(CudaBackend& be, double* A, double* Z, double* w, const long lo
     be.note(cudaErrorInvalidValue, "syev: matrix too large");
     return;
   }
+  // (d, e) of every matrix: 2 * sum(n) doubles, sum(n) <= nmat * maxn
+  double* DE = (double*)be.scratch(sizeof(double) * 2 * (size_t)nmat * maxn + 64, 3);
+  if (!DE) return;
   const size_t smem = sizeof(double) * 4 * (size_t)maxn;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
       be.note(e, "syev: shared memory attribute");
       return;
     }
   }
-  k_syev<<<nmat, SY_NT, smem, be.stream()>>>(A, Z, w, off, n, woff, maxn, status);
+  k_tridiag<<<nmat, SY_NT, smem, be.stream()>>>(A, DE, off, n, woff, maxn);
   be.launches++;
-  be.note(cudaGetLastError(), "syev");
+  be.note(cudaGetLastError(), "syev tridiagonalisation");
+  dim3 grid(nmat, (maxn + TQ_COLS - 1) / TQ_COLS);
+  k_tqr<<<grid, TQ_NT, smem, be.stream()>>>(A, Z, w, DE, off, n, woff, maxn, status);
+  be.launches++;
+  be.note(cudaGetLastError(), "syev QR");
 }
 
 }  // namespace tns
