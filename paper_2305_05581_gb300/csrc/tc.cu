@@ -336,7 +336,19 @@ __global__ void __launch_bounds__(TC_NT, 2)
   __shared__ uint64_t lbar1[2], mbar1[2], lbar2[2], mbar2[2];
   __shared__ uint32_t tbase;
   __shared__ int bad;
-  __shared__ float salpha[TC_M / 16];
+  // metadata of the products of a chunk (at most TC_M / 16 share one X
+  // block), double-buffered by chunk parity: thread 0's copy and MMA issue
+  // reads it from here instead of from global memory
+  struct MetaT {
+    Img L, R;
+    float alpha;
+  };
+  struct Meta {
+    MetaT t[TC_M / 16];
+    XBlock xb;
+    int pc;
+  };
+  __shared__ Meta meta[2];
   const int tid = threadIdx.x;
   // the vectors of one tile piece are adjacent CTAs (they read the same operator blocks)
   const TcTile TL = tiles[blockIdx.x / nv];
@@ -396,16 +408,32 @@ __global__ void __launch_bounds__(TC_NT, 2)
   // thread 0's copy issue for the steps (chunk c, X rows m0..m0+63) of this
   // piece; GEMM1 chunk kc of a step goes to G1 buffer kc & 1, GEMM2 slice st
   // (product st / nch2, K chunk st % nch2) to G2 buffer (g2_steps + st) & 1
-  auto issue1 = [&](int c, int m0, int kc, int b) {
+  // all threads: metadata of chunk c into meta[c & 1]
+  auto load_meta = [&](int c) {
     const TcChunk C = chunks[c];
+    Meta& M = meta[c & 1];
     const int pc = C.t1 - C.t0;
-    const XBlock XB = xblocks[tasks[C.t0].xb];
+    if (tid < pc) {
+      const TcTask& k = tasks[C.t0 + tid];
+      M.t[tid].L = k.L;
+      M.t[tid].R = k.R;
+      M.t[tid].alpha = k.alpha;
+    }
+    if (tid == 0) {
+      M.pc = pc;
+      M.xb = xblocks[tasks[C.t0].xb];
+    }
+  };
+  auto issue1 = [&](int c, int m0, int kc, int b) {
+    const Meta& M = meta[c & 1];
+    const int pc = M.pc;
+    const XBlock& XB = M.xb;
     const int mc16 = (min(TC_MC, XB.m - m0) + 15) & ~15;
     const int xg0 = m0 / 8, xng = min(mc16 / 8, XB.img.rg - xg0);
     const uint32_t rowb = (chunk_w(XB.img, kc) / 16) * 128;  // bytes of one row group in this chunk
     uint32_t bytes = (xng > 0 ? xng * rowb : 0) * S::NS;
     for (int t = 0; t < pc; ++t) {
-      const int ng = min(rp / 8, tasks[C.t0 + t].R.rg - TL.col0 / 8);
+      const int ng = min(rp / 8, M.t[t].R.rg - TL.col0 / 8);
       if (ng > 0) bytes += ng * rowb * S::NS;
     }
     expect_tx(&lbar1[b], bytes);
@@ -416,7 +444,7 @@ __global__ void __launch_bounds__(TC_NT, 2)
       if (!TF32) bulk_g2s(sB1(b) + S::B1, xl + xo, xng * rowb, &lbar1[b]);
     }
     for (int t = 0; t < pc; ++t) {
-      const Img R = tasks[C.t0 + t].R;
+      const Img R = M.t[t].R;
       const int ng = min(rp / 8, R.rg - TL.col0 / 8);
       if (ng <= 0) continue;
       const long long ro = chunk_off(R, kc) + (long long)(TL.col0 / 8) * rowb;
@@ -425,16 +453,14 @@ __global__ void __launch_bounds__(TC_NT, 2)
       if (!TF32) bulk_g2s(sA1(b) + S::A1 + dst, ops_lo + ro, ng * rowb, &lbar1[b]);
     }
   };
-  auto nchunks1 = [&](int c) { return (xblocks[tasks[chunks[c].t0].xb].img.kb + CH_BYTES - 1) / CH_BYTES; };
   // the first (up to) two GEMM1 chunks of a step, into free G1 buffers
   auto prefetch1 = [&](int c, int m0) {
-    const int nch = nchunks1(c);
+    const int nch = (meta[c & 1].xb.img.kb + CH_BYTES - 1) / CH_BYTES;
     for (int kc = 0; kc < 2 && kc < nch; ++kc) issue1(c, m0, kc, kc);
   };
   auto issue2 = [&](int c, int m0, int st, int nch2, int b) {
-    const TcChunk C = chunks[c];
     const int t = st / nch2, c2 = st % nch2;
-    const Img Lm = tasks[C.t0 + t].L;
+    const Img Lm = meta[c & 1].t[t].L;
     const int lg0 = TL.row0 / 8, lng = min(TC_M / 8, Lm.rg - lg0);
     const int lc = (m0 * ES) / CH_BYTES + c2;  // chunk of L's K (= X rows)
     const uint32_t rowb = (chunk_w(Lm, lc) / 16) * 128;
@@ -445,15 +471,19 @@ __global__ void __launch_bounds__(TC_NT, 2)
     bulk_g2s(a2, ops_hi + lo_, lng * rowb, &lbar2[b]);
     if (!TF32) bulk_g2s(a2 + S::A2, ops_lo + lo_, lng * rowb, &lbar2[b]);
   };
+  if (has_work) load_meta(TL.c0);
+  __syncthreads();
   if (tid == 0 && has_work) prefetch1(TL.c0, 0);
 
   for (int c = TL.c0; c < TL.c1 && !bad; ++c) {
-    const TcChunk C = chunks[c];
-    const int pc = C.t1 - C.t0;
-    const TcTask t0 = tasks[C.t0];
-    const XBlock XB = xblocks[t0.xb];
-    const int m = t0.m;
-    if (tid < pc) salpha[tid] = tasks[C.t0 + tid].alpha;
+    // the next chunk's metadata goes to the other buffer, free since the last
+    // step of chunk c-1 ended (thread 0 reads it for its prefetch at the end
+    // of this chunk, after the barriers of this chunk's steps)
+    if (c + 1 < TL.c1) load_meta(c + 1);
+    const Meta& M = meta[c & 1];
+    const int pc = M.pc;
+    const XBlock XB = M.xb;
+    const int m = XB.m;
     where_c = c;
     for (int m0 = 0; m0 < m && !bad; m0 += TC_MC) {
       where_m0 = m0;
@@ -509,7 +539,7 @@ __global__ void __launch_bounds__(TC_NT, 2)
         const int warp = tid >> 5, wg = warp >> 2;
         const int row = (warp & 3) * 32 + (tid & 31);  // TMEM lane = stacked R row = B2 row
         const int t = row / rp;
-        const float al = (t < pc) ? salpha[t] : 0.f;
+        const float al = (t < pc) ? M.t[t].alpha : 0.f;
         for (int i0 = 8 * wg; i0 < mc16; i0 += 16) {
           uint32_t r[8];
           const uint32_t addr = tD1 + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)i0;
@@ -569,7 +599,7 @@ __global__ void __launch_bounds__(TC_NT, 2)
           if (bad) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
           const int t = st / nch2, c2 = st % nch2;
-          const Img Lm = tasks[C.t0 + t].L;
+          const Img Lm = M.t[t].L;
           const int lc = (m0 * ES) / CH_BYTES + c2;
           const int kcm = chunk_w(Lm, lc) / 16;
           const uint32_t rowb = kcm * 128;
@@ -1044,17 +1074,24 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
     }
     V.part_nvec = nvec;
   }
-  // kernel attributes once, outside any stream capture
-  static bool attr[2] = {false, false};
-  if (!attr[0]) {
-    cudaFuncSetAttribute(k_tasks_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<0>::total);
-    attr[0] = true;
+  // kernel attributes once, outside any stream capture: the dynamic shared
+  // memory, and the largest shared-memory carve-out (the kernel stages all
+  // operands in shared memory and does not rely on L1)
+  static bool attr = false;
+  if (!attr) {
+    be.note(cudaFuncSetAttribute(k_tasks_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<0>::total),
+            "k_tasks_tc shared memory");
+    be.note(cudaFuncSetAttribute(k_tasks_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<1>::total),
+            "k_tasks_tc shared memory");
+    be.note(cudaFuncSetAttribute(k_tasks_tc<0>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared),
+            "k_tasks_tc carve-out");
+    be.note(cudaFuncSetAttribute(k_tasks_tc<1>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared),
+            "k_tasks_tc carve-out");
+    attr = true;
   }
-  if (!attr[1]) {
-    cudaFuncSetAttribute(k_tasks_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<1>::total);
-    attr[1] = true;
-  }
-  return true;
+  return be.ok();
 }
 
 void enqueue_tasks_tc(CudaBackend& be, DevList& d, const double* xv, double* yv, int nvec, long long xs,
