@@ -34,7 +34,7 @@ UNIT = "TFLOP/s"
 # workload's middle bond, from the ncu capture summarised in
 # profiles/k_tasks_tc_bf16x3_n24_state.md (None until captured for the
 # current kernel of that precision).
-TRAFFIC_BYTES_PER_HEFF = {"fp64": None, "tf32": None, "bf16x3": 5.21e9}
+TRAFFIC_BYTES_PER_HEFF = {"fp64": None, "tf32": None, "bf16x3": 5.75e9}
 
 
 def parse():

@@ -46,13 +46,17 @@ struct FpVariant {
 };
 
 // online autotuner state of one (precision, nvec) use of a work list: the
-// first kNumVariants products run one variant each and are timed; the
-// fastest is kept for the rest of the list's life
+// first products run the variants in turn and are timed; the fastest is kept
+// for the rest of the list's life
 struct Tune {
-  int next = 0;
+  int step = 0;   // products run so far while tuning
   int best = -1;
-  float ms[kNumVariants] = {0.f, 0.f, 0.f};
+  float ms[kNumVariants] = {1e30f, 1e30f, 1e30f};  // fastest sample of each variant
 };
+// tuning sequence: one untimed product (default variant: first-use effects
+// such as cold caches land there), then kTuneRounds timed samples of every
+// variant, the fastest sample of each compared
+constexpr int kTuneRounds = 2;
 
 // captured launch sequence of one (precision, nvec) use: replayed with the
 // input copied into xbuf and the output copied out of ybuf

@@ -126,12 +126,11 @@ __global__ void __launch_bounds__(TQ_NT) k_tqr(const double* A, double* Zall, do
                                                const long long* off, const int* nn, const int* woff, int maxn,
                                                int* status) {
   extern __shared__ double sm[];
-  double* v = sm;              // reflector, then rotation cosines
-  double* p = sm + maxn;       // rotation sines
-  double* d = sm + 2 * maxn;
-  double* e = sm + 3 * maxn;
+  double* v = sm;              // reflector; then two slots of rotations (cos, sin) in sm[0, 4 maxn)
+  double* d = sm + 4 * maxn;
+  double* e = sm + 5 * maxn;
   __shared__ double red[TQ_PH][TQ_COLS];
-  __shared__ int ctl[3];       // lo, hi, done
+  __shared__ int ctl[9];       // lo, hi, done; per slot: lo, hi, done
   const int mi = blockIdx.x;
   const int n = nn[mi];
   const int j0 = blockIdx.y * TQ_COLS;
@@ -169,21 +168,22 @@ __global__ void __launch_bounds__(TQ_NT) k_tqr(const double* A, double* Zall, do
       for (int r = k + 1 + ph; r < n; r += TQ_PH) Z[(long long)r * n + jc] -= t * v[r];
     __syncthreads();
   }
-  // ---- 2. implicit symmetric QR with Wilkinson shift (warp 0) ---------------
-  if (tid >= 32) return;  // no block-wide barrier below
-  if (lane == 0) {
-    ctl[1] = n - 1;
-    ctl[2] = 0;
-  }
-  __syncwarp();
+  // ---- 2. implicit symmetric QR with Wilkinson shift -----------------------
+  // warp 1 (lane 0) computes the bulge chases, warp 0 applies them to the
+  // columns: chase t+1 is computed while chase t is applied (rotations
+  // double-buffered in cs[t & 1], one 64-thread named barrier per chase)
+  if (tid >= 64) return;  // only named barriers over warps 0 and 1 below
+  double* cs[2] = {v, v + 2 * maxn};  // cos at [i], sin at [maxn + i]
   const int max_steps = 40 * n + 40;
-  int steps = 0;
-  for (;;) {
-    if (lane == 0) {
-      int hi = ctl[1], lo = 0, done = 0;
+  int hi_state = n - 1;  // producer: bottom of the unreduced part
+  for (int t = 0;; ++t) {
+    if (tid == 32) {
+      double* cc = cs[t & 1];
+      double* ss = cc + maxn;
+      int hi = hi_state, lo = 0, done = 0;
       // deflate from the bottom
       while (hi > 0) {
-        double b = fabs(e[hi - 1]);
+        const double b = fabs(e[hi - 1]);
         if (b <= eps * (fabs(d[hi - 1]) + fabs(d[hi])) || b < 1e-300) {
           e[hi - 1] = 0.0;
           --hi;
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(TQ_NT) k_tqr(const double* A, double* Zall, do
       } else {
         lo = hi - 1;
         while (lo > 0) {
-          double b = fabs(e[lo - 1]);
+          const double b = fabs(e[lo - 1]);
           if (b <= eps * (fabs(d[lo - 1]) + fabs(d[lo])) || b < 1e-300) {
             e[lo - 1] = 0.0;
             break;
@@ -208,38 +208,67 @@ __global__ void __launch_bounds__(TQ_NT) k_tqr(const double* A, double* Zall, do
         const double bb = e[hi - 1] * e[hi - 1];
         const double den = dl + (dl >= 0.0 ? 1.0 : -1.0) * sqrt(dl * dl + bb);
         const double mu = den != 0.0 ? d[hi] - bb / den : d[hi];
-        double x = d[lo] - mu, z = e[lo];
+        // the chase with d[i], e[i] carried in registers and the next
+        // diagonal / off-diagonal entries loaded one step ahead
+        double ai = d[lo], b = e[lo];
+        double x = ai - mu, z = b;
+        double aj_n = d[lo + 1], e_n = lo + 1 < hi ? e[lo + 1] : 0.0;
         for (int i = lo; i < hi; ++i) {
-          // Givens rotation zeroing z against x; rhypot avoids two divisions
-          double c = 1.0, s = 0.0, r = 0.0;
-          if (x != 0.0 || z != 0.0) {
+          const double aj = aj_n, en = e_n;
+          if (i + 1 < hi) {
+            aj_n = d[i + 2];
+            e_n = i + 2 < hi ? e[i + 2] : 0.0;
+          }
+          // Givens rotation zeroing z against x
+          double c = 1.0, sn = 0.0, r = 0.0;
+          const double q = x * x + z * z;
+          if (q >= 1e-280 && q <= 1e280) {
+            const double ri = rsqrt(q);
+            c = x * ri;
+            sn = z * ri;
+            r = q * ri;
+          } else if (x != 0.0 || z != 0.0) {
             const double ri = rhypot(x, z);
             c = x * ri;
-            s = z * ri;
-            r = c * x + s * z;
+            sn = z * ri;
+            r = c * x + sn * z;
           }
           if (i > lo) e[i - 1] = r;
-          const double ai = d[i], aj = d[i + 1], b = e[i];
-          d[i] = c * c * ai + 2.0 * c * s * b + s * s * aj;
-          d[i + 1] = s * s * ai - 2.0 * c * s * b + c * c * aj;
-          e[i] = c * s * (aj - ai) + (c * c - s * s) * b;
+          const double cs2 = 2.0 * c * sn * b;
+          d[i] = c * c * ai + cs2 + sn * sn * aj;
+          const double dj = sn * sn * ai - cs2 + c * c * aj;
+          const double ei = c * sn * (aj - ai) + (c * c - sn * sn) * b;
+          e[i] = ei;
+          x = ei;
           if (i + 1 < hi) {
-            z = s * e[i + 1];  // bulge at (i, i+2)
-            e[i + 1] *= c;
+            z = sn * en;  // bulge at (i, i+2)
+            b = c * en;
           }
-          x = e[i];
-          v[i] = c;
-          p[i] = s;
+          ai = dj;
+          cc[i] = c;
+          ss[i] = sn;
         }
+        d[hi] = ai;
       }
+      hi_state = hi;
       ctl[0] = lo;
       ctl[1] = hi;
       ctl[2] = done;
+      ctl[3 + (t & 1)] = lo;  // slot copies for the consumer
+      ctl[5 + (t & 1)] = hi;
+      ctl[7 + (t & 1)] = done;
     }
-    __syncwarp();
-    if (ctl[2]) break;
-    const int lo = ctl[0], hi = ctl[1];
-    if (lane < cw) {
+    // chase t is in cs[t & 1]; chase t-1 has been applied
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    if (ctl[7 + (t & 1)]) break;
+    if (t > max_steps) {
+      if (tid == 0 && status) atomicExch(status, 1);
+      break;
+    }
+    if (tid < 32 && lane < cw) {
+      const int lo = ctl[3 + (t & 1)], hi = ctl[5 + (t & 1)];
+      const double* cc = cs[t & 1];
+      const double* ss = cc + maxn;
       double carry = Z[(long long)lo * n + jc];
       int i = lo;
       // every original row is read once (as y) before its row is written, so
@@ -250,26 +279,21 @@ __global__ void __launch_bounds__(TQ_NT) k_tqr(const double* A, double* Zall, do
         for (int q = 0; q < 8; ++q) y[q] = Z[(long long)(i + 1 + q) * n + jc];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const double c = v[i + q], s = p[i + q];
-          Z[(long long)(i + q) * n + jc] = c * carry + s * y[q];
-          carry = -s * carry + c * y[q];
+          const double c = cc[i + q], sn = ss[i + q];
+          Z[(long long)(i + q) * n + jc] = c * carry + sn * y[q];
+          carry = -sn * carry + c * y[q];
         }
       }
       for (; i < hi; ++i) {
         const double y = Z[(long long)(i + 1) * n + jc];
-        const double c = v[i], s = p[i];
-        Z[(long long)i * n + jc] = c * carry + s * y;
-        carry = -s * carry + c * y;
+        const double c = cc[i], sn = ss[i];
+        Z[(long long)i * n + jc] = c * carry + sn * y;
+        carry = -sn * carry + c * y;
       }
       Z[(long long)hi * n + jc] = carry;
     }
-    __syncwarp();
-    if (++steps > max_steps) {
-      if (lane == 0 && status) atomicExch(status, 1);
-      break;
-    }
   }
-  if (blockIdx.y == 0)
+  if (blockIdx.y == 0 && tid >= 32)
     for (int i = lane; i < n; i += 32) w[woff[mi] + i] = d[i];
 }
 
@@ -285,11 +309,16 @@ void launch_syev(CudaBackend& be, double* A, double* Z, double* w, const long lo
   // (d, e) of every matrix: 2 * sum(n) doubles, sum(n) <= nmat * maxn
   double* DE = (double*)be.scratch(sizeof(double) * 2 * (size_t)nmat * maxn + 64, 3);
   if (!DE) return;
-  const size_t smem = sizeof(double) * 4 * (size_t)maxn;
+  const size_t smem = sizeof(double) * 4 * (size_t)maxn, smem_q = sizeof(double) * 6 * (size_t)maxn;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_tqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+      be.note(e, "syev: shared memory attribute");
+      return;
+    }
+  }
+  if (smem_q > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_tqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q);
     if (e != cudaSuccess) {
       be.note(e, "syev: shared memory attribute");
       return;
@@ -299,7 +328,7 @@ void launch_syev(CudaBackend& be, double* A, double* Z, double* w, const long lo
   be.launches++;
   be.note(cudaGetLastError(), "syev tridiagonalisation");
   dim3 grid(nmat, (maxn + TQ_COLS - 1) / TQ_COLS);
-  k_tqr<<<grid, TQ_NT, smem, be.stream()>>>(A, Z, w, DE, off, n, woff, maxn, status);
+  k_tqr<<<grid, TQ_NT, smem_q, be.stream()>>>(A, Z, w, DE, off, n, woff, maxn, status);
   be.launches++;
   be.note(cudaGetLastError(), "syev QR");
 }

@@ -1455,13 +1455,15 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
     }
     return;
   }
-  // online autotuner: the first products of this (precision, nvec) use run
-  // one schedule variant each, timed with events; the fastest is kept
+  // online autotuner: after one untimed product, the next products of this
+  // (precision, nvec) use run the schedule variants in turn, timed with
+  // events; the variant with the fastest sample is kept
   const int key = precision * 64 + nvec;
   Tune& tu = d.tune[key];
   if (!autotune && tu.best < 0) tu.best = 1;
-  const bool timing = tu.best < 0;
-  const int v = timing ? tu.next : tu.best;
+  const bool tuning = tu.best < 0;
+  const bool timing = tuning && tu.step > 0;
+  const int v = !tuning ? tu.best : timing ? (tu.step - 1) % kNumVariants : 1;
   if (precision != 0) {
     if (!prepare_tasks_tc(*this, tl, d, nvec, v, precision)) return;
   } else {
@@ -1474,7 +1476,10 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
     else
       enqueue_fp64(d, v, x, y, nvec, xs, ys);
   };
-  if (timing) {
+  if (tuning && !timing) {
+    enqueue(xv, yv);
+    ++tu.step;
+  } else if (timing) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
@@ -1486,8 +1491,8 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
     cudaEventElapsedTime(&ms, a, b);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    tu.ms[v] = ms;
-    if (++tu.next == kNumVariants) {
+    tu.ms[v] = std::min(tu.ms[v], ms);
+    if (++tu.step == 1 + kTuneRounds * kNumVariants) {
       tu.best = 0;
       for (int i = 1; i < kNumVariants; ++i)
         if (tu.ms[i] < tu.ms[tu.best]) tu.best = i;

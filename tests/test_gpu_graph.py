@@ -74,12 +74,14 @@ def test_autotuned_graph_replays_match_fixed_schedule(prec, tol, nvec):
     ref = _apply(ref_ctx, x, nvec, prec, 1)[0]
     ctx = _ctx()
     _load(ctx)
-    ys = _apply(ctx, x, nvec, prec, 7)   # 3 tuning products, then capture and replays
+    # 7 tuning products (one untimed, then two timed samples of each of the
+    # three variants), then capture and replays of the chosen schedule
+    ys = _apply(ctx, x, nvec, prec, 11)
     scale = float(torch.linalg.norm(ref))
     for y in ys:
         assert float(torch.linalg.norm(y - ref)) <= tol * scale
-    for y in ys[4:]:
-        assert torch.equal(y, ys[3])
+    for y in ys[8:]:
+        assert torch.equal(y, ys[7])
 
 
 @pytest.mark.parametrize("prec", [TNS_FP64, TNS_BF16X3])
