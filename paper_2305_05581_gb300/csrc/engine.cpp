@@ -1114,13 +1114,6 @@ double chain_flops(const Task& t) {
   return std::min(2.0 * m * r * (n + q), 2.0 * q * n * (m + r));
 }
 
-void set_order(Task& t) {
-  bool li = t.flags & TF_LI, ri = t.flags & TF_RI;
-  if (li || ri) return;
-  double a = 2.0 * t.m * t.r * ((double)t.n + t.q);  // L (X R^T)
-  double b = 2.0 * t.q * t.n * ((double)t.m + t.r);  // (L X) R^T
-  if (b < a) t.flags |= TF_ORDB;
-}
 }  // namespace
 
 // rotate the enlarged operators of a side into the new block (renormalisation)
@@ -1191,7 +1184,6 @@ void Engine::rotation_tasks(const Side& S, const Catalogue& src, const Catalogue
             tk.r = g.r;
             tk.flags = TF_LT | TF_RT | (X.ident ? TF_XI : 0) | (X.trans ? TF_XT : 0);
             tk.pad = 0;
-            set_order(tk);
             tl.flops += chain_flops(tk);
             tl.tasks.push_back(tk);
             if (prov) prov->push_back({(int)ei, (int)di, (int)ti});
@@ -1220,7 +1212,6 @@ void Engine::rotation_tasks(const Side& S, const Catalogue& src, const Catalogue
             tk.r = g.r;
             tk.flags = (X.ident ? TF_XI : 0) | (X.trans ? TF_XT : 0);
             tk.pad = 0;
-            set_order(tk);
             tl.flops += chain_flops(tk);
             tl.tasks.push_back(tk);
             if (prov) prov->push_back({(int)ei, (int)di, (int)ti});
@@ -1389,17 +1380,22 @@ void Engine::build_heff_tasks() {
     for (int b = 0; b < nLL; ++b) pairs.push_back({eL(K_B, a, b), false, eR(K_Q, a, b), false, 1.0, 0});
 
   // per output block task buckets (and where each coefficient comes from)
+  std::vector<Operand> rres(nqr);
+  std::vector<char> rok(nqr);
+  std::vector<int> qr_of((size_t)Lb.size() * 16, -1);  // (q_l, s1, s2) -> the q_r of its psi block, or -1
+  for (int ql = 0; ql < Lb.size(); ++ql)
+    for (int s12 = 0; s12 < 16; ++s12)
+      for (int qr = 0; qr < nqr; ++qr)
+        if (st.psi_index[((size_t)ql * 16 + s12) * nqr + qr] >= 0) qr_of[(size_t)ql * 16 + s12] = qr;
   std::vector<std::vector<Task>> bucket(st.psi.size());
   std::vector<std::vector<std::array<int, 6>>> pbucket(st.psi.size());
-  static const DotBlock kIdent[4] = {{0, 0, {{1.0, -1}}}, {1, 1, {{1.0, -1}}}, {2, 2, {{1.0, -1}}}, {3, 3, {{1.0, -1}}}};
+  static const std::vector<DotBlock> kIdent = {
+      {0, 0, {{1.0, -1}}}, {1, 1, {{1.0, -1}}}, {2, 2, {{1.0, -1}}}, {3, 3, {{1.0, -1}}}};
 
   for (const Pair& pr : pairs) {
     if (pr.eL == -1 || pr.eR == -1) continue;
-    std::vector<DotBlock> dl, dr;
-    if (pr.eL == -2) dl.assign(kIdent, kIdent + 4);
-    else dl = st.L.eops[pr.eL].dots;
-    if (pr.eR == -2) dr.assign(kIdent, kIdent + 4);
-    else dr = st.R.eops[pr.eR].dots;
+    const std::vector<DotBlock>& dl = pr.eL == -2 ? kIdent : st.L.eops[pr.eL].dots;
+    const std::vector<DotBlock>& dr = pr.eR == -2 ? kIdent : st.R.eops[pr.eR].dots;
     for (size_t ai = 0; ai < dl.size(); ++ai) {
       const auto& a = dl[ai];
       int s1o = pr.trL ? a.si : a.so, s1i = pr.trL ? a.so : a.si;
@@ -1410,7 +1406,24 @@ void Engine::build_heff_tasks() {
           for (size_t tbi = 0; tbi < b.t.size(); ++tbi) {
             const auto& ta = a.t[tai];
             const auto& tb = b.t[tbi];
+            // the right operand depends on qr only: resolved once per term
+            for (int qr = 0; qr < nqr; ++qr) {
+              Operand& Ro = rres[qr];
+              if (tb.expr == -1) {
+                Ro.p = nullptr;
+                Ro.out = qr;
+                Ro.ident = true;
+                Ro.trans = false;
+                Ro.sign = 1.0;
+                rok[qr] = 1;
+              } else {
+                rok[qr] = resolve(st.R, Rc, tb.expr, pr.trR, qr, Ro) ? 1 : 0;
+              }
+            }
             for (int ql = 0; ql < Lb.size(); ++ql) {
+              // the target sector fixes q_r given (q_l, s1, s2): at most one X block
+              const int qr = qr_of[(ql * 4 + s1i) * 4 + s2i];
+              if (qr < 0 || !rok[qr]) continue;
               Operand Lo;
               if (ta.expr == -1) {
                 Lo.p = nullptr;
@@ -1422,20 +1435,11 @@ void Engine::build_heff_tasks() {
                 continue;
               }
               double pl = pr.f ? sgn_n(Lb.q[ql].n + kSiteQN[s1i].n) : 1.0;
-              for (int qr = 0; qr < nqr; ++qr) {
-                int xb = st.psi_index[((size_t)(ql * 4 + s1i) * 4 + s2i) * nqr + qr];
-                if (xb < 0) continue;
-                Operand Ro;
-                if (tb.expr == -1) {
-                  Ro.p = nullptr;
-                  Ro.out = qr;
-                  Ro.ident = true;
-                  Ro.trans = false;
-                  Ro.sign = 1.0;
-                } else if (!resolve(st.R, Rc, tb.expr, pr.trR, qr, Ro)) {
-                  continue;
-                }
-                int yb = st.psi_index[((size_t)(Lo.out * 4 + s1o) * 4 + s2o) * nqr + Ro.out];
+              const int* yrow = &st.psi_index[((size_t)(Lo.out * 4 + s1o) * 4 + s2o) * nqr];
+              {
+                const int xb = st.psi_index[((size_t)(ql * 4 + s1i) * 4 + s2i) * nqr + qr];
+                const Operand& Ro = rres[qr];
+                const int yb = yrow[Ro.out];
                 if (yb < 0) continue;
                 const PsiBlock& X = st.psi[xb];
                 const PsiBlock& Y = st.psi[yb];
@@ -1452,7 +1456,6 @@ void Engine::build_heff_tasks() {
                 tk.flags = TF_XV | (Lo.ident ? TF_LI : 0) | (Lo.trans ? TF_LT : 0) | (Ro.ident ? TF_RI : 0) |
                            (Ro.trans ? TF_RT : 0);
                 tk.pad = xb;
-                set_order(tk);
                 bucket[yb].push_back(tk);
                 pbucket[yb].push_back({pr.eL == -2 ? -1 : pr.eL, pr.eL == -2 ? -1 : (int)ai, (int)tai,
                                        pr.eR == -2 ? -1 : pr.eR, pr.eR == -2 ? -1 : (int)bi, (int)tbi});
@@ -1462,6 +1465,10 @@ void Engine::build_heff_tasks() {
       }
     }
   }
+  size_t ntot = 0;
+  for (const auto& b : bucket) ntot += b.size();
+  tl.tasks.reserve(ntot);
+  st.heff_prov.reserve(ntot);
   for (size_t yb = 0; yb < st.psi.size(); ++yb) {
     const PsiBlock& Y = st.psi[yb];
     Group g;

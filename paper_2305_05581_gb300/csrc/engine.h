@@ -259,7 +259,6 @@ enum TaskFlags {
   TF_XV = 16,     // X pointer is an element offset into the launch's X vector
   TF_RI = 32,     // R is the identity
   TF_RT = 64,     // R stored transposed (n x r)
-  TF_ORDB = 128,  // evaluate (L X) R^T instead of L (X R^T)
 };
 
 struct Task {
