@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -53,6 +54,8 @@ def parse():
                         "of a random MPS of the workload (kernel micro-benchmark, used for ncu captures); "
                         "rdm: integral gradients (1- and 2-RDM) at the middle bond of a random MPS")
     p.add_argument("--nvec", type=int, default=1)
+    p.add_argument("--clocks-dir", default=None,
+                   help="folder for the nvidia-smi samples of the timed region (default: the temp folder)")
     return p.parse_args()
 
 
@@ -148,8 +151,8 @@ def sweep_plan(N):
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
-    def __init__(self, index):
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}.csv")
+    def __init__(self, index, log_dir=None):
+        self.path = os.path.join(log_dir or tempfile.gettempdir(), f"clocks_bench_{index}.csv")
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -290,7 +293,7 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = Clocks(local)
+    clocks = Clocks(local, args.clocks_dir)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
