@@ -21,7 +21,10 @@
 // pipe stays out of the product loop.
 //
 // One CTA (256 threads) per output tile piece (128 rows x <= 64 columns);
-// thread 0 issues copies and MMAs, all threads do the T pass and the epilogue.
+// thread 0 issues copies and MMAs from the chunk's product metadata, which
+// all threads stage in shared memory one chunk ahead; GEMM1's first copies of
+// a step are issued while the previous step's GEMM2 runs, GEMM2's first
+// copies while the T pass runs; all threads do the T pass and the epilogue.
 // Every wait is bounded; a timeout sets a flag the host reads, after the CTA
 // has drained (bounded) its own copies and MMAs and released its TMEM.
 #include <cuda_bf16.h>
