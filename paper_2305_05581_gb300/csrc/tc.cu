@@ -47,7 +47,8 @@ namespace {
 constexpr int TC_NT = 256;
 constexpr int TC_M = 128;     // MMA M: output tile rows; stacked R rows of GEMM1
 constexpr int TC_NC = 64;     // output tile columns (GEMM2 N <= 64)
-constexpr int TC_MC = 64;     // X rows per GEMM1 step (GEMM1 N <= 64, GEMM2 K <= 64)
+constexpr int TC_MC = 32;     // X rows per GEMM1 step (GEMM1 N <= 32, GEMM2 K <= 32)
+constexpr int TC_CTAS = 3;    // resident CTAs per SM (shared memory and registers are sized for it)
 constexpr int CH_BYTES = 64;  // bytes of one K chunk of one row (4 core matrices)
 constexpr unsigned long long TC_WAIT_NS = 200000000ull;  // bound of one wait: 0.2 s
 
@@ -311,15 +312,17 @@ struct TcSmem {
   static constexpr int CB2 = TC_M * CH_BYTES;   // one K chunk of B2 (all 128 rows)
   static constexpr int B2 = TC_MC * ES / CH_BYTES * CB2;  // T^T of all products, K = TC_MC
   static constexpr int A2 = TC_M * CH_BYTES;    // L rows, one K chunk (two buffers)
-  // separate regions for GEMM1's two operand buffers and GEMM2's two L
-  // buffers, so that each GEMM's first copies are issued while the other GEMM
-  // (or the T pass) runs; 113 KB for split-BF16 still leaves two CTAs per SM
+  // GEMM1's two operand buffers and GEMM2's two L buffers share one region
+  // (they are never live together: GEMM2's copies start once D1 is
+  // complete, GEMM1's once the previous GEMM2's MMAs are done), which keeps
+  // a CTA at 56 KB (split-BF16) so that three fit on an SM
   static constexpr int G1 = 2 * NS * (A1 + B1), G2 = 2 * NS * A2;
-  static constexpr int total = G1 + G2 + NS * B2;
+  static constexpr int R1 = G1 > G2 ? G1 : G2;
+  static constexpr int total = R1 + NS * B2;
 };
 
 template <int TF32>
-__global__ void __launch_bounds__(TC_NT, 2)
+__global__ void __launch_bounds__(TC_NT, TC_CTAS)
     k_tasks_tc(const TcTask* __restrict__ tasks, const Group* __restrict__ groups, const TcTile* __restrict__ tiles,
                const TcChunk* __restrict__ chunks, const unsigned char* __restrict__ ops_hi,
                const unsigned char* __restrict__ ops_lo, const unsigned char* __restrict__ x_hi,
@@ -331,9 +334,9 @@ __global__ void __launch_bounds__(TC_NT, 2)
   constexpr int EPC = CH_BYTES / ES;              // elements per K chunk
   constexpr uint32_t SBO_FULL = (CH_BYTES / 16) * 128;
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* const sG1 = smem;                    // GEMM1 operand buffers
-  unsigned char* const sA2 = smem + S::G1;            // GEMM2 L buffers: buffer b, plane p at + (b * NS + p) * S::A2
-  unsigned char* const sB2 = smem + S::G1 + S::G2;    // planes at + p * S::B2
+  unsigned char* const sG1 = smem;                    // GEMM1 operand buffers, or
+  unsigned char* const sA2 = smem;                    // GEMM2 L buffers: buffer b, plane p at + (b * NS + p) * S::A2
+  unsigned char* const sB2 = smem + S::R1;            // planes at + p * S::B2
   auto sA1 = [&](int b) { return sG1 + b * S::NS * (S::A1 + S::B1); };          // plane p at + p * S::A1
   auto sB1 = [&](int b) { return sG1 + b * S::NS * (S::A1 + S::B1) + S::NS * S::A1; };  // plane p at + p * S::B1
   __shared__ uint64_t lbar1[2], mbar1[2], lbar2[2], mbar2[2];
@@ -477,6 +480,7 @@ __global__ void __launch_bounds__(TC_NT, 2)
   if (has_work) load_meta(TL.c0);
   __syncthreads();
   if (tid == 0 && has_work) prefetch1(TL.c0, 0);
+  bool first_step = true;  // thread 0: the first step's GEMM1 chunks are already in flight
 
   for (int c = TL.c0; c < TL.c1 && !bad; ++c) {
     // the next chunk's metadata goes to the other buffer, free since the last
@@ -496,9 +500,14 @@ __global__ void __launch_bounds__(TC_NT, 2)
       const int nsteps = pc * nch2;
       if (tid == 0) {
         // ---- GEMM1: D1[t*rp + j][i] = sum_k R_t[col0 + j][k] X[m0 + i][k] ----
-        // chunks 0 and 1 are in flight (issued while the previous step's
-        // GEMM2 ran); chunk kc+1 >= 2 is copied once chunk kc-1's MMAs have
-        // released its buffer
+        // the previous step's GEMM2 MMAs read the shared region and B2: done
+        // first; then chunks 0 and 1 of this step (the first step's were
+        // issued before the loop); chunk kc+1 >= 2 is copied once chunk
+        // kc-1's MMAs have released its buffer
+        drain(&mbar2[0], pm2[0], m2_out[0]);
+        drain(&mbar2[1], pm2[1], m2_out[1]);
+        if (!first_step && !bad) prefetch1(c, m0);
+        first_step = false;
         const int nch = (XB.img.kb + CH_BYTES - 1) / CH_BYTES;
         for (int kc = 0; kc < nch && !bad; ++kc) {
           where_s = kc;
@@ -524,15 +533,11 @@ __global__ void __launch_bounds__(TC_NT, 2)
           commit(&mbar1[b]);
           m1_out[b] = 1;
         }
-        // the previous step's GEMM2 MMAs (they read B2 and the G2 buffers)
-        // are done before the T pass rewrites B2; this step's first two L
-        // slices are then copied while the T pass runs
-        drain(&mbar2[0], pm2[0], m2_out[0]);
-        drain(&mbar2[1], pm2[1], m2_out[1]);
-        for (int st = 0; st < 2 && st < nsteps && !bad; ++st) issue2(c, m0, st, nch2, (g2_steps + st) & 1);
-        // D1 complete before the T pass
+        // D1 complete before the T pass; the shared region is then free and
+        // this step's first two L slices are copied while the T pass runs
         drain(&mbar1[0], pm1[0], m1_out[0]);
         drain(&mbar1[1], pm1[1], m1_out[1]);
+        for (int st = 0; st < 2 && st < nsteps && !bad; ++st) issue2(c, m0, st, nch2, (g2_steps + st) & 1);
       }
       __syncthreads();
       if (bad) break;
@@ -622,14 +627,6 @@ __global__ void __launch_bounds__(TC_NT, 2)
           m2_out[b] = 1;
         }
         g2_steps += nsteps;
-        // the next step's first GEMM1 chunks (the G1 buffers were released
-        // when this step's D1 completed)
-        if (!bad) {
-          if (m0 + TC_MC < m)
-            prefetch1(c, m0 + TC_MC);
-          else if (c + 1 < TL.c1)
-            prefetch1(c + 1, 0);
-        }
       }
       __syncthreads();
     }
@@ -789,7 +786,7 @@ void split_plan(const std::vector<TcTask>& tasks, std::vector<TcTile>& tiles, co
     for (int c = tiles[i].c0; c < tiles[i].c1; ++c) tcost[i] += ccost(chunks[c], tiles[i]);
     tot += tcost[i];
   }
-  const double target = std::max(tot / (2.0 * sms * rounds), 1.0);
+  const double target = std::max(tot / ((double)TC_CTAS * sms * rounds), 1.0);
   std::vector<TcTile> out;
   psize = 0;
   reds.clear();
