@@ -22,9 +22,10 @@
 //
 // One CTA (256 threads) per output tile piece (128 rows x <= 64 columns);
 // thread 0 issues copies and MMAs from the chunk's product metadata, which
-// all threads stage in shared memory one chunk ahead; GEMM1's first copies of
-// a step are issued while the previous step's GEMM2 runs, GEMM2's first
-// copies while the T pass runs; all threads do the T pass and the epilogue.
+// all threads stage in shared memory one chunk ahead; GEMM2's first copies
+// are issued while the T pass runs; all threads do the T pass and the
+// epilogue.  Steps of 32 X rows and one staging region shared by the two
+// GEMMs keep a CTA at 56 KB of shared memory, three per SM.
 // Every wait is bounded; a timeout sets a flag the host reads, after the CTA
 // has drained (bounded) its own copies and MMAs and released its TMEM.
 #include <cuda_bf16.h>
