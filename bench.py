@@ -33,9 +33,10 @@ UNIT = "TFLOP/s"
 
 # DRAM bytes (read + write) of the dominant kernel per H_eff*psi at this
 # workload's middle bond, from the ncu capture summarised in
-# profiles/k_tasks_tc_bf16x3_n24_state.md (None until captured for the
-# current kernel of that precision).
-TRAFFIC_BYTES_PER_HEFF = {"fp64": None, "tf32": None, "bf16x3": None}
+# profiles/k_tasks_tc_bf16x3_n24_state.md (measured on the state after one
+# sweep and scaled by useful flops to the second sweep's middle bond; None
+# until captured for the current kernel of that precision).
+TRAFFIC_BYTES_PER_HEFF = {"fp64": None, "tf32": None, "bf16x3": 3.49e9}
 
 
 def parse():
