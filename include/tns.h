@@ -104,7 +104,9 @@ int tns_mps_get_site(tns_ctx* ctx, int site, double* blocks, long long len, long
 int tns_build_env(tns_ctx* ctx, int site);
 
 /* Layout of the two-site wavefunction at step (site, site+1), valid after
- * tns_build_env(site).  *desc points to n_blocks rows of 9 int64 values
+ * tns_build_env(site): its symmetry blocks, the first level of the task
+ * hierarchy of Sec. III.A.1 (the quantum-number sectors that split the
+ * superblock vector into independent dense blocks).  *desc points to n_blocks rows of 9 int64 values
  * (n_l, two_sz_l, s1, s2, n_r, two_sz_r, m, n, offset): q_l = (n_l, two_sz_l)
  * is a bond-`site` sector (left counted), q_r = (n_r, two_sz_r) the particle
  * content of orbitals site+2..N-1, the block is m x n row-major at element
@@ -131,7 +133,9 @@ int tns_heff_diag(tns_ctx* ctx, int site, double* diag);
  * block (orbitals site+2..N-1, side 1) used by step (site, site+1) live in one
  * DEVICE arena each; tns_env_arena returns its pointer and length (doubles).
  * The arena may be modified by the caller (e.g. to perturb an operator); call
- * tns_build_env(site) afterwards so the partial sums are recomputed.
+ * tns_build_env(site) afterwards so the partial sums are recomputed.  The
+ * operators of an empty block (the left block of step 0, the right block of
+ * step N-2) are zero by definition and are never read.
  * Layout: operators in catalogue order, each operator its symmetry blocks
  * (out <- in) row-major. */
 int tns_env_arena(tns_ctx* ctx, int site, int side, double** data, long long* size);
@@ -240,7 +244,9 @@ typedef struct tns_sweep_stats {
   int max_bond;             /* largest bond dimension after the call */
 } tns_sweep_stats;
 
-/* Two-site DMRG sweeps over the current MPS (tns_mps_init or an import):
+/* Two-site DMRG sweeps over the current MPS (tns_mps_init or an import),
+ * the sweep of Sec. III / Sec. IV.A (a sweep is one left-to-right and one
+ * right-to-left pass of two-site iteration cycles; D sets the accuracy):
  * per step environment build, Davidson on H_eff, SVD truncation to at most D
  * states, renormalisation.  *energy_out receives the final energy.  stats is
  * optional (NULL). */
@@ -281,9 +287,15 @@ int tns_step(tns_ctx* ctx, int site, int left_to_right, const tns_sweep_opts* op
  * only).  Works without tns_build_env. */
 int tns_psi_guess(tns_ctx* ctx, int site, double* x_host, long long* length);
 
-/* Useful FP64-equivalent flop count of one tns_heff_apply(site) for nvec = 1:
- * sum over products of p * min(2mr(n+q), 2qn(m+r)) (best chain order, the
- * matrix-chain choice of Sec. III.B), and the number of block products. */
+/* Useful FP64-equivalent flop count of one tns_heff_apply(site) for nvec = 1
+ * (the per-product cost of Eq. (2) with the cheaper chain order of Sec. III.B):
+ * one product per operator pair of the expansion, per pair of dot blocks
+ * (s1' <- s1, s2' <- s2) and per X symmetry block, costing min(2mr(n+q),
+ * 2qn(m+r)) for the m x n X block, q x m left and r x n right operator blocks;
+ * a factor that is a multiple of the block identity costs nothing (2mnr,
+ * 2qmn, or 2mn when both are); products whose operator block is identically
+ * zero are not counted.  *nproducts receives the number of block products the
+ * kernels execute (each expression of a dot block is one product there). */
 int tns_heff_flops(tns_ctx* ctx, int site, double* flops, long long* nproducts);
 
 #ifdef __cplusplus

@@ -107,6 +107,8 @@ class CudaBackend : public Backend {
   void run(const TaskList& tl, const double* xv, double* yv, int nvec, long long xs, long long ys,
            int precision) override;
   void task_values(const TaskList& tl, const double* xv, const double* ybar, double* out) override;
+  void nonzero_blocks(const std::vector<const double*>& p, const std::vector<long long>& n,
+                      std::vector<char>& nz) override;
   void sync() override;
   std::string error() override;
 

@@ -570,6 +570,7 @@ void Engine::empty_left(Catalogue& c) {
   c = Catalogue();
   c.left = true;
   c.len = 0;
+  c.zero = true;
   c.basis.add({0, 0}, 1);
   c.add_op(K_H, -1, -1, {0, 0});
   for (int x = 0; x < 2 * N_; ++x) c.add_op(K_T, x, -1, dq_of(K_T, x, -1));
@@ -579,6 +580,7 @@ void Engine::empty_right(Catalogue& c) {
   c = Catalogue();
   c.left = false;
   c.len = N_;
+  c.zero = true;
   c.basis.add({0, 0}, 1);
   c.add_op(K_H, -1, -1, {0, 0});
   for (int a = 0; a < 2 * N_; ++a) c.add_op(K_S, a, -1, dq_of(K_S, a, -1));
@@ -605,6 +607,7 @@ struct Builder {
     return t.tr ? -d : d;
   }
   int ref(int op, bool tr = false, int par = 0) {
+    if (op >= 0 && cat.zero) return -1;  // an operator of an empty block
     auto key = std::make_tuple(op, (int)tr, par);
     auto it = refs.find(key);
     if (it != refs.end()) return it->second;
@@ -621,7 +624,7 @@ struct Builder {
   int comb(const std::vector<TermT<Sc>>& ts) {
     ExprT<Sc> e;
     for (auto& t : ts)
-      if (t.c != 0.0) e.t.push_back(t);
+      if (t.c != 0.0 && !(t.op >= 0 && cat.zero)) e.t.push_back(t);
     if (e.t.empty()) return -1;
     e.dq = term_dq(e.t[0]);
     S.exprs.push_back(e);
@@ -1391,6 +1394,39 @@ void Engine::build_heff_tasks() {
   std::vector<std::vector<std::array<int, 6>>> pbucket(st.psi.size());
   static const std::vector<DotBlock> kIdent = {
       {0, 0, {{1.0, -1}}}, {1, 1, {{1.0, -1}}}, {2, 2, {{1.0, -1}}}, {3, 3, {{1.0, -1}}}};
+  // useful flops (Eq. 2 with the cheaper chain of Sec. III.B): one product per
+  // (operator pair, left dot block, right dot block, X block), whatever the
+  // number of expressions the two dot blocks hold (their sum is one operator
+  // block); a factor counts as the identity only if its dot block is the
+  // identity expression alone.  `counted[ql]` marks the X blocks of the
+  // current dot-block pair that already have their product counted.
+  std::vector<long long> counted(Lb.size(), -1);
+  long long dot_pair = 0;
+  // a dot block is a multiple of the block's identity when every term is an
+  // identity expression (parity signs allowed) and the summed coefficient is
+  // the same nonzero number on every sector of the block basis (always so on
+  // a one-state basis)
+  auto dot_ident = [](const Side& S, const DotBlock& db, const Basis& bs) {
+    if (bs.total == 1) return true;
+    double c0 = 0.0, c1 = 0.0;  // coefficient of the plain and of the parity-signed identity
+    for (const DotTerm& dt : db.t) {
+      if (dt.expr == -1) {
+        c0 += dt.s;
+        continue;
+      }
+      for (const Term& tm : S.exprs[dt.expr].t) {
+        if (tm.op >= 0) return false;
+        (tm.par ? c1 : c0) += dt.s * tm.c;
+      }
+    }
+    const double ev = c0 + c1, od = c0 - c1;  // on sectors with even / odd particle number
+    bool has_ev = false, has_od = false;
+    for (const QN& q : bs.q) (q.n % 2 ? has_od : has_ev) = true;
+    if (has_ev && ev == 0.0) return false;
+    if (has_od && od == 0.0) return false;
+    return !(has_ev && has_od) || ev == od;
+  };
+  double useful = 0.0;
 
   for (const Pair& pr : pairs) {
     if (pr.eL == -1 || pr.eR == -1) continue;
@@ -1402,6 +1438,9 @@ void Engine::build_heff_tasks() {
       for (size_t bi = 0; bi < dr.size(); ++bi) {
         const auto& b = dr[bi];
         int s2o = pr.trR ? b.si : b.so, s2i = pr.trR ? b.so : b.si;
+        ++dot_pair;
+        const bool li_u = pr.eL == -2 || dot_ident(st.L, a, Lb);
+        const bool ri_u = pr.eR == -2 || dot_ident(st.R, b, Rc.basis);
         for (size_t tai = 0; tai < a.t.size(); ++tai)
           for (size_t tbi = 0; tbi < b.t.size(); ++tbi) {
             const auto& ta = a.t[tai];
@@ -1456,6 +1495,13 @@ void Engine::build_heff_tasks() {
                 tk.flags = TF_XV | (Lo.ident ? TF_LI : 0) | (Lo.trans ? TF_LT : 0) | (Ro.ident ? TF_RI : 0) |
                            (Ro.trans ? TF_RT : 0);
                 tk.pad = xb;
+                const bool nz = (Lo.ident || !st.zero_blk.count(Lo.p)) && (Ro.ident || !st.zero_blk.count(Ro.p));
+                if (nz && counted[ql] != dot_pair) {
+                  counted[ql] = dot_pair;
+                  Task u = tk;
+                  u.flags = TF_XV | (li_u ? TF_LI : 0) | (ri_u ? TF_RI : 0);
+                  useful += chain_flops(u);
+                }
                 bucket[yb].push_back(tk);
                 pbucket[yb].push_back({pr.eL == -2 ? -1 : pr.eL, pr.eL == -2 ? -1 : (int)ai, (int)tai,
                                        pr.eR == -2 ? -1 : pr.eR, pr.eR == -2 ? -1 : (int)bi, (int)tbi});
@@ -1479,14 +1525,12 @@ void Engine::build_heff_tasks() {
     g.nrows = Y.m;
     g.ncols = Y.n;
     g.t0 = (int)tl.tasks.size();
-    for (auto& tk : bucket[yb]) {
-      tl.flops += chain_flops(tk);
-      tl.tasks.push_back(tk);
-    }
+    for (auto& tk : bucket[yb]) tl.tasks.push_back(tk);
     for (auto& pv : pbucket[yb]) st.heff_prov.push_back(pv);
     g.t1 = (int)tl.tasks.size();
     tl.groups.push_back(g);
   }
+  tl.flops = useful;
   tl.nprod = (long long)tl.tasks.size();
   st.diag_tasks.clear();
   st.diag_rng.assign(1, 0);
@@ -1496,6 +1540,42 @@ void Engine::build_heff_tasks() {
     st.diag_rng.push_back((int)st.diag_tasks.size());
   }
   tl.persistent = true;
+}
+
+// the operand blocks of the step that are identically zero (the operators of
+// a block acting on, or into, a state they annihilate, e.g. any operator with
+// an annihilator on the vacuum sector); used by the useful-flop count only
+void Engine::find_zero_blocks() {
+  Step& st = step_;
+  std::vector<const double*> p;
+  std::vector<long long> n;
+  auto add_cat = [&](const Catalogue& c) {
+    for (const CatOp& o : c.ops) {
+      const Layout& L = c.layouts[o.layout];
+      for (size_t b = 0; b < L.in.size(); ++b) {
+        p.push_back(c.d + o.off + L.off[b]);
+        n.push_back((long long)c.basis.dim[L.out[b]] * c.basis.dim[L.in[b]]);
+      }
+    }
+  };
+  auto add_side = [&](const Side& S, const Catalogue& c) {
+    for (const Mat& m : S.mats) {
+      const Layout& L = c.layouts[m.layout];
+      for (size_t b = 0; b < L.in.size(); ++b) {
+        p.push_back(S.d + m.off + L.off[b]);
+        n.push_back((long long)c.basis.dim[L.out[b]] * c.basis.dim[L.in[b]]);
+      }
+    }
+  };
+  add_cat(Lcat_[st.k]);
+  add_cat(Rcat_[st.k + 2]);
+  add_side(st.L, Lcat_[st.k]);
+  add_side(st.R, Rcat_[st.k + 2]);
+  std::vector<char> nz;
+  be_->nonzero_blocks(p, n, nz);
+  st.zero_blk.clear();
+  for (size_t i = 0; i < nz.size(); ++i)
+    if (!nz[i]) st.zero_blk.insert(p[i]);
 }
 
 int Engine::prepare_step(int k, std::string& err) {
@@ -1511,6 +1591,7 @@ int Engine::prepare_step(int k, std::string& err) {
   compile_side(step_.R, Rcat_[k + 2], false);
   rc = materialize(step_.R, Rcat_[k + 2], err);
   if (rc) return rc;
+  find_zero_blocks();
   build_psi(k);
   build_heff_tasks();
   be_->sync();

@@ -32,6 +32,7 @@
 #include <map>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 namespace tns {
@@ -99,6 +100,9 @@ struct Catalogue {
   double* d = nullptr;  // arena (device for the CUDA backend)
   long long size = 0;
   bool valid = false;
+  // an empty block (no orbitals): every operator is zero by definition, so
+  // expressions drop its operators instead of reading them
+  bool zero = false;
   static long long key(int kind, int i, int j) {
     return ((long long)kind << 40) | ((long long)(i + 1) << 20) | (long long)(j + 1);
   }
@@ -321,6 +325,10 @@ struct Backend {
   // out[t] = < Ybar_g, op(L_t) op(X_t) op(R_t)^T > for every task t of group g
   // (alpha not included); out is backend memory of tl.tasks.size() doubles
   virtual void task_values(const TaskList& tl, const double* xv, const double* ybar, double* out) = 0;
+  // nz[i] = 1 if any element of block i (p[i], n[i] doubles in backend
+  // memory) is nonzero, else 0
+  virtual void nonzero_blocks(const std::vector<const double*>& p, const std::vector<long long>& n,
+                              std::vector<char>& nz) = 0;
   virtual void sync() = 0;
   virtual std::string error() = 0;  // "" if fine
 };
@@ -371,6 +379,9 @@ struct Step {
   // per H_eff task, where its coefficient comes from: (eop, dot block, dot
   // term) on the left side and on the right side; -1 for an identity side
   std::vector<std::array<int, 6>> heff_prov;
+  // operand blocks of the step (catalogue and partial-sum blocks) that are
+  // identically zero; products reading one are not counted as useful flops
+  std::unordered_set<const double*> zero_blk;
   std::vector<int> diag_tasks;  // tasks contributing to the diagonal, in group order
   std::vector<int> diag_rng;    // per group: range [diag_rng[g], diag_rng[g+1]) of diag_tasks
   bool valid = false;
@@ -475,6 +486,7 @@ class Engine {
                       std::vector<std::array<int, 3>>* prov);
 
   void build_psi(int k);
+  void find_zero_blocks();
   void build_heff_tasks();
 };
 

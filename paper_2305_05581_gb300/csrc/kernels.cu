@@ -1556,6 +1556,44 @@ void CudaBackend::task_values(const TaskList& tl, const double* xv, const double
     if (p) cudaFree(p);
 }
 
+// one warp per block: nz[i] = any element of block i nonzero (HBM-bound read)
+__global__ void k_nonzero(const double* const* __restrict__ p, const long long* __restrict__ n, int nb,
+                          char* __restrict__ nz) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = w0; i < nb; i += nw) {
+    const double* x = p[i];
+    const long long len = n[i];
+    int any = 0;
+    for (long long j = lane; j < len && !any; j += 32) any = x[j] != 0.0;
+    any = __any_sync(0xffffffffu, any);
+    if (lane == 0) nz[i] = (char)any;
+  }
+}
+
+void CudaBackend::nonzero_blocks(const std::vector<const double*>& p, const std::vector<long long>& n,
+                                 std::vector<char>& nz) {
+  nz.assign(p.size(), 1);  // on any failure every block counts as nonzero
+  if (!ok() || p.empty()) return;
+  const double** dp = dev_copy(p, *this);
+  long long* dn = dev_copy(n, *this);
+  char* dz = nullptr;
+  if (dp && dn && cudaMalloc(&dz, p.size()) == cudaSuccess) {
+    const int nb = (int)p.size();
+    const int grid = std::min((nb + 7) / 8, 152 * 16);
+    k_nonzero<<<grid, 256, 0, stream_>>>(dp, dn, nb, dz);
+    launches++;
+    note(cudaGetLastError(), "k_nonzero");
+    std::vector<char> h(p.size());
+    if (cudaMemcpyAsync(h.data(), dz, p.size(), cudaMemcpyDeviceToHost, stream_) == cudaSuccess &&
+        cudaStreamSynchronize(stream_) == cudaSuccess)
+      nz = h;
+  }
+  cudaStreamSynchronize(stream_);
+  for (void* q : {(void*)dp, (void*)dn, (void*)dz})
+    if (q) cudaFree(q);
+}
+
 void CudaBackend::lincomb(const LCList& l) {
   if (!ok()) return;
   if (l.blocks.empty()) return;

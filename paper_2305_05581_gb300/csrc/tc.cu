@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(TC_NT, TC_CTAS)
     }
   };
 
-  // thread 0's copy issue for the steps (chunk c, X rows m0..m0+63) of this
+  // thread 0's copy issue for the steps (chunk c, X rows m0..m0+TC_MC-1) of this
   // piece; GEMM1 chunk kc of a step goes to G1 buffer kc & 1, GEMM2 slice st
   // (product st / nch2, K chunk st % nch2) to G2 buffer (g2_steps + st) & 1
   // all threads: metadata of chunk c into meta[c & 1]

@@ -21,6 +21,12 @@ struct HostBackend : tns::Backend {
   void upload(double* d, const double* s, long long n) override { std::memcpy(d, s, (size_t)n * 8); }
   void download(double* d, const double* s, long long n) override { std::memcpy(d, s, (size_t)n * 8); }
   void zero(double* p, long long n) override { std::memset(p, 0, (size_t)n * 8); }
+  void nonzero_blocks(const std::vector<const double*>& p, const std::vector<long long>& n,
+                      std::vector<char>& nz) override {
+    nz.assign(p.size(), 0);
+    for (size_t i = 0; i < p.size(); ++i)
+      for (long long j = 0; j < n[i] && !nz[i]; ++j) nz[i] = p[i][j] != 0.0;
+  }
   void lincomb(const tns::LCList& l) override {
     for (const auto& b : l.blocks)
       for (int i = 0; i < b.rows; ++i)

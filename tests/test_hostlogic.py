@@ -99,6 +99,28 @@ def test_layout_and_flops(hostlib):
     assert f > 0 and nprod > 0
 
 
+# edge bonds (k = 0: empty left block; k = N-2: empty right block), 2S_z != 0,
+# identity factors (the enlarged blocks of the empty blocks are identities)
+FLOP_CASES = [(3, 3, 1, 4, 0), (4, 4, 0, 16, 0), (4, 4, 0, 16, 1), (5, 5, 1, 8, 0), (6, 6, 0, 12, 2),
+              (6, 5, -1, 9, 3), (6, 6, 2, 16, 4), (8, 8, 0, 40, 3), (8, 7, 1, 30, 1)]
+
+
+@pytest.mark.parametrize("N,n,s2,D,k", FLOP_CASES)
+def test_heff_flops_equal_oracle(hostlib, N, n, s2, D, k):
+    """The engine's useful-flop count (structural work list plus the identically
+    zero operator blocks it detects) equals the oracle's count over its dense
+    operators exactly: every throughput figure divides this number."""
+    h, v = synth.integrals(N, 2.0, 100 + N + k)
+    bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=k + 1)
+    ctx = _ctx(hostlib)
+    ctx.load_integrals(h, v)
+    ctx.mps_import(N, n, s2, D, bonds, sites)
+    ctx.build_env(k)
+    f, nprod = ctx.heff_flops(k)
+    ref = O3.useful_flops(O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2))
+    assert f == ref
+
+
 def test_bad_arguments(hostlib):
     from paper_2305_05581_gb300.binding import TnsError
     ctx = _ctx(hostlib)
