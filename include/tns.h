@@ -298,6 +298,41 @@ int tns_psi_guess(tns_ctx* ctx, int site, double* x_host, long long* length);
  * kernels execute (each expression of a dot block is one product there). */
 int tns_heff_flops(tns_ctx* ctx, int site, double* flops, long long* nproducts);
 
+/* Out-of-HBM environments (the tree-traversal cache of Alg. 1, Sec. "Tree-
+ * Traversal Optimized Virtual Memory Addressing", applied to the chain of
+ * left and right blocks).  The operator catalogues of all blocks of a sweep
+ * grow as D^2 N^2 each; the engine keeps on the device the two that the
+ * current step reads and moves the others off it when the device runs short:
+ * in stack order (the catalogue needed last leaves first), to pinned host
+ * memory while host_bytes last, else dropped and rebuilt from its neighbours
+ * when the sweep needs it again.  Every step first makes a memory plan (its
+ * partial sums, work list, tensor-core operand images and Davidson vectors)
+ * and fails with TNS_ERR_OOM, before it allocates or launches anything, if
+ * the plan does not fit next to its two catalogues.
+ *  - device_bytes: most device memory the library may hold on the context's
+ *    device (all contexts on that device share it); 0 = the device's size.
+ *  - host_bytes: pinned host memory for staged catalogues; 0 = no staging
+ *    (catalogues that must leave the device are dropped).
+ * Results do not depend on either setting. */
+int tns_set_memory_budget(tns_ctx* ctx, long long device_bytes, long long host_bytes);
+
+typedef struct tns_mem_stats {
+  long long device_used;   /* bytes the library holds on the device now */
+  long long device_peak;   /* high-water mark since the last reset (reset=1 below) */
+  long long device_limit;  /* the budget, else the device's size */
+  long long host_used;     /* pinned host bytes holding staged catalogues */
+  long long host_peak;
+  long long staged;        /* catalogues moved to host memory */
+  long long restored;      /* catalogues moved back to the device */
+  long long dropped;       /* catalogues freed (rebuilt when needed) */
+  long long built;         /* catalogues built by renormalisation */
+  long long last_plan;     /* bytes of the last step's memory plan (beyond its catalogues) */
+} tns_mem_stats;
+
+/* Memory statistics of the context's device; reset != 0 restarts the
+ * device high-water mark at the current use. */
+int tns_memory_stats(tns_ctx* ctx, tns_mem_stats* out, int reset);
+
 #ifdef __cplusplus
 }
 #endif

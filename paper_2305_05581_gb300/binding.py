@@ -22,7 +22,8 @@ DEFAULT_LIB = os.path.join(HERE, "libtns.so")
 SYMBOLS = ["create", "destroy", "last_error", "load_integrals", "mps_init", "mps_define",
            "mps_set_bond", "mps_set_site", "mps_get_bond", "mps_get_site", "build_env",
            "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops", "step", "psi_guess",
-           "heff_diag_noalloc", "env_arena", "heff_adjoint", "sym_eig", "rdm"]
+           "heff_diag_noalloc", "env_arena", "heff_adjoint", "sym_eig", "rdm", "set_memory_budget",
+           "memory_stats"]
 
 
 class TnsError(RuntimeError):
@@ -49,6 +50,16 @@ class StepStats(C.Structure):
                 ("svd_seconds", C.c_double), ("seconds", C.c_double), ("length", C.c_longlong),
                 ("bond_dim", C.c_int), ("kernel_launches", C.c_longlong), ("exact_products", C.c_int),
                 ("exact_seconds", C.c_double)]
+
+
+class MemStats(C.Structure):
+    _fields_ = [("device_used", C.c_longlong), ("device_peak", C.c_longlong), ("device_limit", C.c_longlong),
+                ("host_used", C.c_longlong), ("host_peak", C.c_longlong), ("staged", C.c_longlong),
+                ("restored", C.c_longlong), ("dropped", C.c_longlong), ("built", C.c_longlong),
+                ("last_plan", C.c_longlong)]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
 _LIBS = {}
@@ -89,6 +100,8 @@ def load_library(path: str = DEFAULT_LIB, prefix: str = "tns_"):
         "heff_adjoint": (C.c_int, [vp, C.c_int, vp, vp, vp, vp, vp]),
         "sym_eig": (C.c_int, [vp, C.c_int, ip, vp, vp, vp]),
         "rdm": (C.c_int, [vp, C.c_int, vp, dp, dp]),
+        "set_memory_budget": (C.c_int, [vp, C.c_longlong, C.c_longlong]),
+        "memory_stats": (C.c_int, [vp, C.POINTER(MemStats), C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = f(name)
@@ -259,6 +272,15 @@ class Context:
                                      C.c_void_p(psi_host_ptr) if psi_host_ptr else None, C.byref(st)))
         return st
 
+
+    def set_memory_budget(self, device_bytes: int = 0, host_bytes: int = 0):
+        """Device budget and pinned host memory for staged catalogues (0 = none)."""
+        self._check(self._fn("set_memory_budget")(self._h, int(device_bytes), int(host_bytes)))
+
+    def memory_stats(self, reset: bool = False) -> dict:
+        st = MemStats()
+        self._check(self._fn("memory_stats")(self._h, C.byref(st), int(reset)))
+        return st.as_dict()
 
     def psi_guess(self, site, x_host_ptr: int = 0) -> int:
         """Copy the two-site start vector to host memory at x_host_ptr (0: length only)."""

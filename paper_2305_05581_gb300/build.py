@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libtns.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["engine.cpp", "kernels.cu", "solver.cu", "tc.cu", "noalloc.cu", "eig.cu"]
+SOURCES = ["engine.cpp", "kernels.cu", "solver.cu", "tc.cu", "noalloc.cu", "eig.cu", "devmem.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

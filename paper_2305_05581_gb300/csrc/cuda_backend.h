@@ -11,6 +11,22 @@
 
 namespace tns {
 
+// device memory of the library (devmem.cu): every allocation goes through
+// dmalloc / dfree, which count the bytes in use per device and refuse,
+// before cudaMalloc, an allocation above the device budget (0: no budget)
+cudaError_t dmalloc_raw(void** p, size_t bytes);
+template <class T>
+inline cudaError_t dmalloc(T** p, size_t bytes) {
+  return dmalloc_raw((void**)p, bytes);
+}
+void dfree(void* p);
+struct DevMem {
+  long long used = 0, peak = 0, budget = 0;
+};
+DevMem dmem(int device);
+void dmem_set_budget(int device, long long bytes);
+void dmem_reset_peak(int device);
+
 struct Tile {  // an output tile of a group: rows [row0, row0+nrows), cols [col0, col0+ncols)
   int g;
   int row0, col0, nrows, ncols;
@@ -109,6 +125,14 @@ class CudaBackend : public Backend {
   void task_values(const TaskList& tl, const double* xv, const double* ybar, double* out) override;
   void nonzero_blocks(const std::vector<const double*>& p, const std::vector<long long>& n,
                       std::vector<char>& nz) override;
+  long long mem_used() override;
+  long long mem_limit() override;
+  long long mem_free() override;
+  void set_budget(long long bytes) override;
+  double* host_alloc(long long n) override;
+  void host_release(double* p) override;
+  void forget(const TaskList& tl) override { drop(tl); }
+  long long step_bytes(const TaskList& tl, long long psi_length) override;
   void sync() override;
   std::string error() override;
 

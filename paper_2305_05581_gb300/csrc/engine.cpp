@@ -15,7 +15,9 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 
@@ -140,6 +142,12 @@ Engine::~Engine() {
 void Engine::free_cat(Catalogue& c) {
   if (c.d) be_->release(c.d);
   c.d = nullptr;
+  if (c.h) {
+    be_->host_release(c.h);
+    ms_.host_used -= std::max(c.size, 1LL) * 8;
+  }
+  c.h = nullptr;
+  c.zero_off.clear();
   c.valid = false;
   c.ops.clear();
   c.index.clear();
@@ -161,11 +169,121 @@ void Engine::free_side(Side& s) {
 int Engine::alloc_cat(Catalogue& c, std::string& err) {
   c.assign_offsets();
   if (c.d) be_->release(c.d);
+  c.d = nullptr;
+  int rc = make_room(std::max(c.size, 1LL) * 8, err);
+  if (rc) return rc;
   c.d = be_->alloc(std::max(c.size, 1LL));
   if (!c.d) {
     err = "device allocation of " + std::to_string(c.size * 8) + " bytes failed (operator catalogue)";
     return -3;
   }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// out-of-HBM environments: the operator catalogues a step does not read may
+// leave the device, in stack order (the one needed last first: the farthest
+// from the current step), to pinned host memory while the host budget lasts,
+// else they are dropped and rebuilt from their neighbours when needed again
+// (the tree-traversal cache of Alg. 1 applied to the left/right block chain)
+// ---------------------------------------------------------------------------
+void Engine::set_memory_budget(long long device_bytes, long long host_bytes) {
+  be_->set_budget(device_bytes);
+  host_budget_ = host_bytes > 0 ? host_bytes : 0;
+}
+
+MemStats Engine::mem_stats() {
+  MemStats m = ms_;
+  m.device_used = be_->mem_used();
+  m.device_limit = be_->mem_limit();
+  m.host_budget = host_budget_;
+  return m;
+}
+
+bool Engine::movable(const Catalogue& c) const {
+  if (!c.valid || !c.d) return false;
+  for (const Catalogue* k : keep_)
+    if (k == &c) return false;
+  if (step_.valid && (&c == &Lcat_[step_.k] || &c == &Rcat_[step_.k + 2])) return false;
+  return true;
+}
+
+int Engine::make_room(long long bytes, std::string& err) {
+  // headroom for allocations the library does not plan (stream-ordered
+  // scratch, the caller's own buffers on the same device)
+  const long long reserve = 512LL << 20;
+  for (;;) {
+    long long avail = LLONG_MAX;
+    const long long lim = be_->mem_limit();
+    if (lim > 0) avail = lim - be_->mem_used();
+    const long long fr = be_->mem_free() - reserve;
+    if (fr < avail) avail = fr;
+    if (bytes <= avail) return 0;
+    // the movable catalogue farthest from the current step (L_j is read at
+    // step j, R_j at step j-2)
+    Catalogue* victim = nullptr;
+    long long best = -1;
+    for (int j = 0; j < (int)Lcat_.size(); ++j) {
+      for (int side = 0; side < 2; ++side) {
+        Catalogue& c = side ? Rcat_[j] : Lcat_[j];
+        if (!movable(c)) continue;
+        const long long dist = std::llabs((long long)(side ? j - 2 : j) - pos_) * 4 + side;
+        if (dist > best) {
+          best = dist;
+          victim = &c;
+        }
+      }
+    }
+    if (!victim) {
+      err = "device memory: " + std::to_string(bytes) + " more bytes needed, " +
+            std::to_string(std::max(avail, 0LL)) + " available and no catalogue left to move off the device";
+      return -3;
+    }
+    int rc = evict(*victim, err);
+    if (rc) return rc;
+  }
+}
+
+int Engine::evict(Catalogue& c, std::string& err) {
+  (void)err;
+  const long long n = std::max(c.size, 1LL);
+  if (host_budget_ > 0 && ms_.host_used + n * 8 <= host_budget_) {
+    double* h = be_->host_alloc(n);
+    if (h) {
+      be_->download(h, c.d, n);
+      be_->release(c.d);
+      c.d = nullptr;
+      c.h = h;
+      ms_.host_used += n * 8;
+      ms_.host_peak = std::max(ms_.host_peak, ms_.host_used);
+      ++ms_.staged;
+      return 0;
+    }
+  }
+  free_cat(c);  // dropped: rebuilt from its neighbours when needed again
+  ++ms_.dropped;
+  return 0;
+}
+
+int Engine::restore(Catalogue& c, std::string& err) {
+  if (c.d) return 0;
+  if (!c.valid || !c.h) {
+    err = "restore: catalogue not available";
+    return -2;
+  }
+  const long long n = std::max(c.size, 1LL);
+  int rc = make_room(n * 8, err);
+  if (rc) return rc;
+  c.d = be_->alloc(n);
+  if (!c.d) {
+    err = "device allocation of " + std::to_string(n * 8) + " bytes failed (catalogue restore)";
+    return -3;
+  }
+  be_->upload(c.d, c.h, n);
+  be_->host_release(c.h);
+  c.h = nullptr;
+  ms_.host_used -= n * 8;
+  ++ms_.restored;
   return 0;
 }
 
@@ -981,8 +1099,9 @@ void Engine::compile_side(SideT<Sc>& S, const Catalogue& cat, bool left) {
   }
 }
 
-// materialise every expression with more than one term on the side's block basis
-int Engine::materialize(Side& S, Catalogue& cat, std::string& err) {
+// the partial sums of a side: every expression with more than one term gets
+// its own operator on the side's block basis (layout and offsets only)
+void Engine::layout_mats(Side& S, Catalogue& cat) {
   S.mats.clear();
   for (size_t e = 0; e < S.exprs.size(); ++e) {
     Expr& x = S.exprs[e];
@@ -1003,10 +1122,17 @@ int Engine::materialize(Side& S, Catalogue& cat, std::string& err) {
   if (S.d) be_->release(S.d);
   S.d = nullptr;
   S.size = tot;
-  if (tot == 0) return 0;
-  S.d = be_->alloc(tot);
+}
+
+// allocate the partial-sum arena of a side and compute it (linear
+// combinations of catalogue operators, Sec. III.A.2)
+int Engine::fill_mats(Side& S, Catalogue& cat, std::string& err) {
+  if (S.size == 0) return 0;
+  int rc = make_room(S.size * 8, err);
+  if (rc) return rc;
+  S.d = be_->alloc(S.size);
   if (!S.d) {
-    err = "device allocation of " + std::to_string(tot * 8) + " bytes failed (partial sums)";
+    err = "device allocation of " + std::to_string(S.size * 8) + " bytes failed (partial sums)";
     return -3;
   }
   LCList lc;
@@ -1043,13 +1169,49 @@ int Engine::materialize(Side& S, Catalogue& cat, std::string& err) {
   return 0;
 }
 
+int Engine::materialize(Side& S, Catalogue& cat, std::string& err) {
+  layout_mats(S, cat);
+  return fill_mats(S, cat, err);
+}
+
+// element offsets (in the side's arena) of the partial-sum blocks that are
+// identically zero: every term reads a zero catalogue block or none at all
+// (an identity term makes a diagonal block nonzero)
+static void mats_zero(const Side& S, const Catalogue& cat, std::vector<long long>& out) {
+  const Basis& bs = cat.basis;
+  for (auto& m : S.mats) {
+    const Expr& x = S.exprs[m.expr];
+    const Layout& L = cat.layouts[m.layout];
+    for (size_t b = 0; b < L.in.size(); ++b) {
+      int in = L.in[b], outq = L.out[b];
+      bool nz = false;
+      for (auto& tm : x.t) {
+        if (tm.op < 0) {
+          if (in == outq) nz = true;
+          continue;
+        }
+        const CatOp& o = cat.ops[tm.op];
+        const Layout& OL = cat.layouts[o.layout];
+        int ob = tm.tr ? OL.blk_of_in[outq] : OL.blk_of_in[in];
+        if (ob < 0) continue;
+        if (tm.tr && OL.out[ob] != in) continue;
+        if (!tm.tr && OL.out[ob] != outq) continue;
+        if (!cat.zero_off.count(o.off + OL.off[ob])) nz = true;
+      }
+      (void)bs;
+      if (!nz) out.push_back(m.off + L.off[b]);
+    }
+  }
+}
+
 // operand of a product: expression `e` of side S used plain or transposed,
 // applied to in-sector `in` of the side's basis
 namespace {
 struct Operand {
-  const double* p;
+  const double* p;  // block address; for a partial sum whose arena is not allocated yet, its element offset
   int out;
   bool ident, trans;
+  bool mat = false;  // the block is a partial sum (in the side's arena)
   double sign;
 };
 bool resolve(const Side& S, const Catalogue& cat, int e, bool tr, int in, Operand& r) {
@@ -1068,9 +1230,11 @@ bool resolve(const Side& S, const Catalogue& cat, int e, bool tr, int in, Operan
       if (b < 0) return false;
       r.out = L.in[b];
     }
-    r.p = S.d + M.off + L.off[b];
+    const long long eo = M.off + L.off[b];
+    r.p = S.d ? S.d + eo : reinterpret_cast<const double*>((uintptr_t)eo);
     r.ident = false;
     r.trans = tr;
+    r.mat = true;
     r.sign = 1.0;
     return true;
   }
@@ -1078,6 +1242,7 @@ bool resolve(const Side& S, const Catalogue& cat, int e, bool tr, int in, Operan
   bool tt = tr != t.tr;
   int par = t.par;
   if (tr && par) par = 3 - par;
+  r.mat = false;
   if (t.op < 0) {
     r.out = in;
     r.ident = true;
@@ -1138,7 +1303,10 @@ int Engine::rotate(Side& S, const Catalogue& src, Catalogue& dst, int site, bool
   rotation_tasks(S, src, dst, site, left, tl, nullptr);
   tl.nprod = (long long)tl.tasks.size();
   be_->run(tl, nullptr, dst.d, 1, 0, 0, 0);
+  be_->forget(tl);
   dst.valid = true;
+  scan_zero(dst);
+  ++ms_.built;
   return 0;
 }
 
@@ -1231,60 +1399,122 @@ void Engine::rotation_tasks(const Side& S, const Catalogue& src, const Catalogue
 // ---------------------------------------------------------------------------
 // environment
 // ---------------------------------------------------------------------------
-int Engine::ensure_left(int k, std::string& err) {
-  if (Lcat_[k].valid) return 0;
-  int j = k;
-  while (j > 0 && !Lcat_[j].valid) --j;
-  if (j == 0 && !Lcat_[0].valid) {
-    empty_left(Lcat_[0]);
-    int rc = alloc_cat(Lcat_[0], err);
-    if (rc) return rc;
-    be_->zero(Lcat_[0].d, Lcat_[0].size);
-    Lcat_[0].valid = true;
+// the two catalogues of step k on the device (a previous step's partial sums
+// and work list are released first, so that they leave room)
+int Engine::ensure_step(int k, std::string& err) {
+  if (step_.valid && step_.k != k) {
+    be_->forget(step_.heff);
+    free_side(step_.L);
+    free_side(step_.R);
+    step_.heff.clear();
+    step_.valid = false;
   }
-  for (; j < k; ++j) {
-    if (!sites_[j].d) {
-      err = "site tensor " + std::to_string(j) + " not set";
-      return -2;
-    }
-    Side S;
-    build_left_eops(Lcat_[j], j, S);
-    compile_side(S, Lcat_[j], true);
-    int rc = materialize(S, Lcat_[j], err);
-    if (!rc) rc = rotate(S, Lcat_[j], Lcat_[j + 1], j, true, err);
-    be_->sync();
-    free_side(S);
-    if (rc) return rc;
+  pos_ = k;
+  keep_.clear();
+  if (step_.valid) return 0;  // this step's catalogues are on the device and pinned
+  int rc = ensure_left(k, err);
+  if (rc) return rc;
+  keep_.push_back(&Lcat_[k]);
+  rc = ensure_right(k + 2, err);
+  if (rc) return rc;
+  keep_.push_back(&Rcat_[k + 2]);
+  if (!Lcat_[k].d || !Rcat_[k + 2].d) {
+    err = "step " + std::to_string(k) + ": its two catalogues do not fit on the device together";
+    return -3;
   }
   return 0;
 }
 
+// L_k resident on the device: restored from host memory, or rebuilt from the
+// nearest catalogue below it that still exists (on the device or the host)
+int Engine::ensure_left(int k, std::string& err) {
+  if (Lcat_[k].valid) {
+    if (Lcat_[k].d) return 0;
+    std::vector<const Catalogue*> saved = keep_;
+    int rc = restore(Lcat_[k], err);
+    keep_ = saved;
+    return rc;
+  }
+  int j = k;
+  while (j > 0 && !Lcat_[j].valid) --j;
+  const std::vector<const Catalogue*> saved = keep_;
+  int rc = 0;
+  if (j == 0 && !Lcat_[0].valid) {
+    empty_left(Lcat_[0]);
+    rc = alloc_cat(Lcat_[0], err);
+    if (rc) return rc;
+    be_->zero(Lcat_[0].d, Lcat_[0].size);
+    Lcat_[0].valid = true;
+  }
+  rc = restore(Lcat_[j], err);
+  if (rc) return rc;
+  for (; j < k; ++j) {
+    if (!sites_[j].d) {
+      err = "site tensor " + std::to_string(j) + " not set";
+      keep_ = saved;
+      return -2;
+    }
+    keep_ = saved;
+    keep_.push_back(&Lcat_[j]);
+    const int pos_saved = pos_;
+    pos_ = j;
+    Side S;
+    build_left_eops(Lcat_[j], j, S);
+    compile_side(S, Lcat_[j], true);
+    rc = materialize(S, Lcat_[j], err);
+    if (!rc) rc = rotate(S, Lcat_[j], Lcat_[j + 1], j, true, err);
+    be_->sync();
+    free_side(S);
+    pos_ = pos_saved;
+    if (rc) break;
+  }
+  keep_ = saved;
+  return rc;
+}
+
 int Engine::ensure_right(int k, std::string& err) {
-  if (Rcat_[k].valid) return 0;
+  if (Rcat_[k].valid) {
+    if (Rcat_[k].d) return 0;
+    std::vector<const Catalogue*> saved = keep_;
+    int rc = restore(Rcat_[k], err);
+    keep_ = saved;
+    return rc;
+  }
   int j = k;
   while (j < N_ && !Rcat_[j].valid) ++j;
+  const std::vector<const Catalogue*> saved = keep_;
+  int rc = 0;
   if (j == N_ && !Rcat_[N_].valid) {
     empty_right(Rcat_[N_]);
-    int rc = alloc_cat(Rcat_[N_], err);
+    rc = alloc_cat(Rcat_[N_], err);
     if (rc) return rc;
     be_->zero(Rcat_[N_].d, Rcat_[N_].size);
     Rcat_[N_].valid = true;
   }
+  rc = restore(Rcat_[j], err);
+  if (rc) return rc;
   for (; j > k; --j) {
     if (!sites_[j - 1].d) {
       err = "site tensor " + std::to_string(j - 1) + " not set";
+      keep_ = saved;
       return -2;
     }
+    keep_ = saved;
+    keep_.push_back(&Rcat_[j]);
+    const int pos_saved = pos_;
+    pos_ = j - 2;
     Side S;
     build_right_eops(Rcat_[j], j - 1, S);
     compile_side(S, Rcat_[j], false);
-    int rc = materialize(S, Rcat_[j], err);
+    rc = materialize(S, Rcat_[j], err);
     if (!rc) rc = rotate(S, Rcat_[j], Rcat_[j - 1], j - 1, false, err);
     be_->sync();
     free_side(S);
-    if (rc) return rc;
+    pos_ = pos_saved;
+    if (rc) break;
   }
-  return 0;
+  keep_ = saved;
+  return rc;
 }
 
 void psi_layout_of(const Basis& L, const Basis& R, QN target, std::vector<PsiBlock>& psi, std::vector<int>& index,
@@ -1493,9 +1723,9 @@ void Engine::build_heff_tasks() {
                 tk.n = X.n;
                 tk.r = Y.n;
                 tk.flags = TF_XV | (Lo.ident ? TF_LI : 0) | (Lo.trans ? TF_LT : 0) | (Ro.ident ? TF_RI : 0) |
-                           (Ro.trans ? TF_RT : 0);
+                           (Ro.trans ? TF_RT : 0) | (Lo.mat ? TF_LM : 0) | (Ro.mat ? TF_RM : 0);
                 tk.pad = xb;
-                const bool nz = (Lo.ident || !st.zero_blk.count(Lo.p)) && (Ro.ident || !st.zero_blk.count(Ro.p));
+                const bool nz = (Lo.ident || !st.zero_L.count(Lo.p)) && (Ro.ident || !st.zero_R.count(Ro.p));
                 if (nz && counted[ql] != dot_pair) {
                   counted[ql] = dot_pair;
                   Task u = tk;
@@ -1542,58 +1772,103 @@ void Engine::build_heff_tasks() {
   tl.persistent = true;
 }
 
-// the operand blocks of the step that are identically zero (the operators of
-// a block acting on, or into, a state they annihilate, e.g. any operator with
-// an annihilator on the vacuum sector); used by the useful-flop count only
-void Engine::find_zero_blocks() {
-  Step& st = step_;
+// the operator blocks of a catalogue that are identically zero (an operator
+// acting on, or into, a state it annihilates: e.g. any operator with an
+// annihilator on the vacuum sector); kept as element offsets
+void Engine::scan_zero(Catalogue& c) {
+  c.zero_off.clear();
+  if (!c.d) return;
   std::vector<const double*> p;
-  std::vector<long long> n;
-  auto add_cat = [&](const Catalogue& c) {
-    for (const CatOp& o : c.ops) {
-      const Layout& L = c.layouts[o.layout];
-      for (size_t b = 0; b < L.in.size(); ++b) {
-        p.push_back(c.d + o.off + L.off[b]);
-        n.push_back((long long)c.basis.dim[L.out[b]] * c.basis.dim[L.in[b]]);
-      }
+  std::vector<long long> n, off;
+  for (const CatOp& o : c.ops) {
+    const Layout& L = c.layouts[o.layout];
+    for (size_t b = 0; b < L.in.size(); ++b) {
+      off.push_back(o.off + L.off[b]);
+      p.push_back(c.d + o.off + L.off[b]);
+      n.push_back((long long)c.basis.dim[L.out[b]] * c.basis.dim[L.in[b]]);
     }
-  };
-  auto add_side = [&](const Side& S, const Catalogue& c) {
-    for (const Mat& m : S.mats) {
-      const Layout& L = c.layouts[m.layout];
-      for (size_t b = 0; b < L.in.size(); ++b) {
-        p.push_back(S.d + m.off + L.off[b]);
-        n.push_back((long long)c.basis.dim[L.out[b]] * c.basis.dim[L.in[b]]);
-      }
-    }
-  };
-  add_cat(Lcat_[st.k]);
-  add_cat(Rcat_[st.k + 2]);
-  add_side(st.L, Lcat_[st.k]);
-  add_side(st.R, Rcat_[st.k + 2]);
+  }
   std::vector<char> nz;
   be_->nonzero_blocks(p, n, nz);
-  st.zero_blk.clear();
   for (size_t i = 0; i < nz.size(); ++i)
-    if (!nz[i]) st.zero_blk.insert(p[i]);
+    if (!nz[i]) c.zero_off.insert(off[i]);
+}
+
+int Engine::refresh_step(std::string& err) {
+  if (!step_.valid) return -2;
+  // the caller may have changed the arenas: their zero blocks are found again
+  scan_zero(Lcat_[step_.k]);
+  scan_zero(Rcat_[step_.k + 2]);
+  return prepare_step(step_.k, err);
 }
 
 int Engine::prepare_step(int k, std::string& err) {
+  be_->forget(step_.heff);  // the device copy of the previous step's work list
   free_side(step_.L);
   free_side(step_.R);
   step_.valid = false;
   step_.k = k;
-  build_left_eops(Lcat_[k], k, step_.L);
-  compile_side(step_.L, Lcat_[k], true);
-  int rc = materialize(step_.L, Lcat_[k], err);
-  if (rc) return rc;
-  build_right_eops(Rcat_[k + 2], k + 1, step_.R);
-  compile_side(step_.R, Rcat_[k + 2], false);
-  rc = materialize(step_.R, Rcat_[k + 2], err);
-  if (rc) return rc;
-  find_zero_blocks();
+  pos_ = k;
+  Catalogue& Lc = Lcat_[k];
+  Catalogue& Rc = Rcat_[k + 2];
+  keep_ = {&Lc, &Rc};
+  // host: enlarged operators, partial-sum layouts, psi blocks and the work
+  // list (partial-sum operands as arena offsets); nothing is allocated yet
+  build_left_eops(Lc, k, step_.L);
+  compile_side(step_.L, Lc, true);
+  layout_mats(step_.L, Lc);
+  build_right_eops(Rc, k + 1, step_.R);
+  compile_side(step_.R, Rc, false);
+  layout_mats(step_.R, Rc);
+  step_.zero_L.clear();
+  step_.zero_R.clear();
+  for (long long o : Lc.zero_off) step_.zero_L.insert(Lc.d + o);
+  for (long long o : Rc.zero_off) step_.zero_R.insert(Rc.d + o);
+  {
+    std::vector<long long> zo;
+    mats_zero(step_.L, Lc, zo);
+    for (long long o : zo) step_.zero_L.insert(reinterpret_cast<const double*>((uintptr_t)o));
+    zo.clear();
+    mats_zero(step_.R, Rc, zo);
+    for (long long o : zo) step_.zero_R.insert(reinterpret_cast<const double*>((uintptr_t)o));
+  }
   build_psi(k);
   build_heff_tasks();
+  // memory plan: partial sums + work list + images + Davidson vectors must fit
+  // next to the step's two catalogues once every other catalogue has left the
+  // device; refused before the step allocates anything
+  const long long need = (step_.L.size + step_.R.size) * 8 + be_->step_bytes(step_.heff, step_.length);
+  step_.plan_bytes = need;
+  ms_.last_plan = need;
+  {
+    const long long lim = be_->mem_limit();
+    const long long fixed = (long long)(std::max(Lc.size, 1LL) + std::max(Rc.size, 1LL)) * 8;
+    if (lim > 0 && need + fixed > lim) {
+      err = "memory plan: step " + std::to_string(k) + " needs " + std::to_string(need + fixed) +
+            " device bytes (catalogues " + std::to_string(fixed) + ", partial sums " +
+            std::to_string((step_.L.size + step_.R.size) * 8) + ", work list, images and vectors " +
+            std::to_string(need - (step_.L.size + step_.R.size) * 8) + "), above the limit " + std::to_string(lim);
+      step_.heff.clear();
+      return -3;
+    }
+  }
+  int rc = make_room(need, err);
+  if (rc) {
+    err = "memory plan: " + err;
+    step_.heff.clear();
+    return rc;
+  }
+  rc = fill_mats(step_.L, Lc, err);
+  if (!rc) rc = fill_mats(step_.R, Rc, err);
+  if (rc) {
+    step_.heff.clear();
+    return rc;
+  }
+  for (Task& t : step_.heff.tasks) {
+    if (t.flags & TF_LM) t.L = step_.L.d + (long long)(uintptr_t)t.L;
+    if (t.flags & TF_RM) t.R = step_.R.d + (long long)(uintptr_t)t.R;
+    t.flags &= ~(TF_LM | TF_RM);
+  }
   be_->sync();
   std::string e = be_->error();
   if (!e.empty()) {
@@ -1613,8 +1888,7 @@ int Engine::build_env(int k, std::string& err) {
     err = "build_env: site out of range";
     return -1;
   }
-  int rc = ensure_left(k, err);
-  if (!rc) rc = ensure_right(k + 2, err);
+  int rc = ensure_step(k, err);
   if (!rc) rc = prepare_step(k, err);
   if (!rc) {
     std::string e = be_->error();
@@ -2168,8 +2442,24 @@ int Engine::integral_gradient(const double* psi, std::vector<double>& g, std::st
   gfree(GmR);
   // ---- renormalisation chain: block l+1 = U^T (block l (x) dot l) U ----
   auto level = [&](int site, bool left, double* Gnext, double*& Gout) -> int {
+    // both blocks of this level must exist (staged ones come back, dropped
+    // ones are rebuilt); the source's arena is read on the device
+    {
+      int rc0 = left ? ensure_left(site + 1, err) : ensure_right(site, err);
+      if (!rc0) rc0 = left ? ensure_left(site, err) : ensure_right(site + 1, err);
+      if (rc0) return rc0;
+    }
     Catalogue& src = left ? Lcat_[site] : Rcat_[site + 1];
     Catalogue& dst = left ? Lcat_[site + 1] : Rcat_[site];
+    struct Keep {
+      std::vector<const Catalogue*>& k;
+      std::vector<const Catalogue*> saved;
+      Keep(std::vector<const Catalogue*>& kk, const Catalogue* a, const Catalogue* b) : k(kk), saved(kk) {
+        k.push_back(a);
+        k.push_back(b);
+      }
+      ~Keep() { k = saved; }
+    } keep(keep_, &src, &dst);
     Side S;
     SideT<Lin> SL;
     if (left) {

@@ -103,6 +103,11 @@ struct Catalogue {
   // an empty block (no orbitals): every operator is zero by definition, so
   // expressions drop its operators instead of reading them
   bool zero = false;
+  // pinned host copy while the catalogue is staged off the device (d == nullptr)
+  double* h = nullptr;
+  // element offsets of the operator blocks that are identically zero (found
+  // when the catalogue is built; used by the useful-flop count)
+  std::unordered_set<long long> zero_off;
   static long long key(int kind, int i, int j) {
     return ((long long)kind << 40) | ((long long)(i + 1) << 20) | (long long)(j + 1);
   }
@@ -263,6 +268,8 @@ enum TaskFlags {
   TF_XV = 16,     // X pointer is an element offset into the launch's X vector
   TF_RI = 32,     // R is the identity
   TF_RT = 64,     // R stored transposed (n x r)
+  TF_LM = 128,    // while a step is planned: L is an element offset into the left partial-sum arena
+  TF_RM = 256,    // the same for R and the right partial-sum arena
 };
 
 struct Task {
@@ -329,6 +336,21 @@ struct Backend {
   // memory) is nonzero, else 0
   virtual void nonzero_blocks(const std::vector<const double*>& p, const std::vector<long long>& n,
                               std::vector<char>& nz) = 0;
+  // memory of the backend's device: bytes in use by the library, the most it
+  // may hold (the budget, else the device's size; 0 = no limit known) and the
+  // bytes the device reports free
+  virtual long long mem_used() = 0;
+  virtual long long mem_limit() = 0;
+  virtual long long mem_free() = 0;
+  virtual void set_budget(long long bytes) = 0;  // 0: no budget
+  // pinned host memory for catalogues staged off the device (nullptr on failure)
+  virtual double* host_alloc(long long n) = 0;
+  virtual void host_release(double* p) = 0;
+  // release the device copy of a work list (if any)
+  virtual void forget(const TaskList& tl) = 0;
+  // device bytes the backend will allocate to run a step's H_eff work list on
+  // vectors of psi_length (work-list copy, operand images, solver vectors)
+  virtual long long step_bytes(const TaskList& tl, long long psi_length) = 0;
   virtual void sync() = 0;
   virtual std::string error() = 0;  // "" if fine
 };
@@ -379,9 +401,11 @@ struct Step {
   // per H_eff task, where its coefficient comes from: (eop, dot block, dot
   // term) on the left side and on the right side; -1 for an identity side
   std::vector<std::array<int, 6>> heff_prov;
-  // operand blocks of the step (catalogue and partial-sum blocks) that are
-  // identically zero; products reading one are not counted as useful flops
-  std::unordered_set<const double*> zero_blk;
+  // operand blocks of the step that are identically zero, per side (catalogue
+  // blocks by address, partial-sum blocks by their arena offset while the
+  // step is planned); products reading one are not counted as useful flops
+  std::unordered_set<const double*> zero_L, zero_R;
+  long long plan_bytes = 0;  // device bytes the memory plan reserved for the step
   std::vector<int> diag_tasks;  // tasks contributing to the diagonal, in group order
   std::vector<int> diag_rng;    // per group: range [diag_rng[g], diag_rng[g+1]) of diag_tasks
   bool valid = false;
@@ -390,6 +414,14 @@ struct Step {
 // two-site wavefunction layout: blocks (ql, s1, s2, qr) ordered by (ql, s1, s2, qr)
 void psi_layout_of(const Basis& L, const Basis& R, QN target, std::vector<PsiBlock>& psi, std::vector<int>& index,
                    std::vector<long long>& desc, long long& length);
+
+// memory management of the operator catalogues (out-of-HBM environments)
+struct MemStats {
+  long long device_used = 0, device_peak = 0, device_limit = 0;
+  long long host_used = 0, host_peak = 0, host_budget = 0;
+  long long staged = 0, restored = 0, dropped = 0, built = 0;  // catalogue moves and renormalisations
+  long long last_plan = 0;  // bytes of the last step's memory plan
+};
 
 class Engine {
  public:
@@ -415,7 +447,12 @@ class Engine {
   // renormalisation chain of both blocks.  psi: backend memory, step layout.
   int integral_gradient(const double* psi, std::vector<double>& g, std::string& err);
   // refresh the step's partial sums after the catalogue arenas were changed
-  int refresh_step(std::string& err) { return step_.valid ? prepare_step(step_.k, err) : -2; }
+  int refresh_step(std::string& err);
+  // device budget (bytes; 0 = none) and pinned host memory for staged
+  // catalogues (bytes; 0 = none: catalogues that must leave the device are
+  // dropped and rebuilt when needed)
+  void set_memory_budget(long long device_bytes, long long host_bytes);
+  MemStats mem_stats();
   double e_core() const { return e_core_; }
 
   // accessors for the API layer
@@ -430,6 +467,7 @@ class Engine {
   Catalogue& right(int k) { return Rcat_[k]; }
 
   // pieces used by the sweep driver
+  int ensure_step(int k, std::string& err);  // L_k and R_{k+2} on the device
   int ensure_left(int k, std::string& err);
   int ensure_right(int k, std::string& err);
   int prepare_step(int k, std::string& err);
@@ -466,6 +504,21 @@ class Engine {
   std::vector<Catalogue> Lcat_;  // Lcat_[k]: orbitals 0..k-1
   std::vector<Catalogue> Rcat_;  // Rcat_[k]: orbitals k..N-1
   Step step_;
+  // catalogue staging: the position of the current work (eviction order is
+  // the distance from it: the catalogue needed last leaves first), the
+  // catalogues in use (never moved), pinned host memory in use and budget
+  int pos_ = 0;
+  std::vector<const Catalogue*> keep_;
+  long long host_budget_ = 0;
+  MemStats ms_;
+
+  int make_room(long long bytes, std::string& err);
+  int evict(Catalogue& c, std::string& err);
+  int restore(Catalogue& c, std::string& err);
+  bool movable(const Catalogue& c) const;
+  void scan_zero(Catalogue& c);
+  void layout_mats(Side& S, Catalogue& cat);
+  int fill_mats(Side& S, Catalogue& cat, std::string& err);
 
   void free_cat(Catalogue& c);
   void free_side(Side& s);

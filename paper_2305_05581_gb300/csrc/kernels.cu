@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
+#include <unordered_set>
 
 #include "cuda_backend.h"
 
@@ -930,7 +931,7 @@ CudaBackend::CudaBackend(int device, cudaStream_t s, bool own) : device_(device)
 CudaBackend::~CudaBackend() {
   for (auto& kv : lists_) free_list(kv.second);
   for (auto& s : scratch_)
-    if (s.first) cudaFree(s.first);
+    if (s.first) dfree(s.first);
   if (gstream_) cudaStreamDestroy(gstream_);
   for (cudaEvent_t e : gev_)
     if (e) cudaEventDestroy(e);
@@ -974,7 +975,7 @@ std::string CudaBackend::error() {
 
 double* CudaBackend::alloc(long long n) {
   void* p = nullptr;
-  if (cudaMalloc(&p, (size_t)n * sizeof(double)) != cudaSuccess) {
+  if (dmalloc(&p, (size_t)n * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -984,7 +985,64 @@ double* CudaBackend::alloc(long long n) {
 void CudaBackend::release(double* p) {
   if (p) {
     cudaStreamSynchronize(stream_);
-    cudaFree(p);
+    dfree(p);
+  }
+}
+
+// the device memory of a step beyond its catalogues and partial sums: the
+// work list with its schedules, the tensor-core operand images (every distinct
+// operator block, rows padded to 8 and K to 32 bytes, 4 bytes per element)
+// and the vectors of a block Davidson (subspace, products, X images, graph
+// buffers: about 120 vectors)
+long long CudaBackend::step_bytes(const TaskList& tl, long long psi_length) {
+  long long b = (long long)tl.tasks.size() * (long long)sizeof(Task) * 3 / 2 +
+                (long long)tl.groups.size() * (long long)sizeof(Group) * 4;
+  std::unordered_set<const double*> seenL, seenR;
+  auto pad = [](long long rows, long long cols) { return ((rows + 7) / 8 * 8) * ((cols * 4 + 31) / 32 * 32); };
+  for (const Task& t : tl.tasks) {
+    if (!(t.flags & TF_LI) && seenL.insert(t.L).second) b += pad(t.q, t.m);
+    if (!(t.flags & TF_RI) && seenR.insert(t.R).second) b += pad(t.r, t.n);
+  }
+  return b + psi_length * 8LL * 120;
+}
+
+long long CudaBackend::mem_used() { return dmem(device_).used; }
+
+long long CudaBackend::mem_limit() {
+  const long long b = dmem(device_).budget;
+  if (b > 0) return b;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (long long)tot;
+}
+
+long long CudaBackend::mem_free() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (long long)fr;
+}
+
+void CudaBackend::set_budget(long long bytes) { dmem_set_budget(device_, bytes); }
+
+double* CudaBackend::host_alloc(long long n) {
+  void* p = nullptr;
+  if (cudaMallocHost(&p, (size_t)n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (double*)p;
+}
+
+void CudaBackend::host_release(double* p) {
+  if (p) {
+    cudaStreamSynchronize(stream_);
+    cudaFreeHost(p);
   }
 }
 
@@ -1007,11 +1065,11 @@ void* CudaBackend::scratch(size_t bytes, int slot) {
   if (s.second < bytes) {
     if (s.first) {
       cudaStreamSynchronize(stream_);
-      cudaFree(s.first);
+      dfree(s.first);
     }
     s.first = nullptr;
     s.second = 0;
-    if (cudaMalloc(&s.first, bytes) != cudaSuccess) {
+    if (dmalloc(&s.first, bytes) != cudaSuccess) {
       cudaGetLastError();
       note(cudaErrorMemoryAllocation, "scratch");
       return nullptr;
@@ -1025,7 +1083,7 @@ template <typename T>
 static T* dev_copy(const std::vector<T>& v, CudaBackend& be) {
   if (v.empty()) return nullptr;
   void* p = nullptr;
-  if (cudaMalloc(&p, v.size() * sizeof(T)) != cudaSuccess) {
+  if (dmalloc(&p, v.size() * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
     be.note(cudaErrorMemoryAllocation, "work list upload");
     return nullptr;
@@ -1037,8 +1095,8 @@ static T* dev_copy(const std::vector<T>& v, CudaBackend& be) {
 void CudaBackend::free_graphs(DevList& d) {
   for (auto& kv : d.graphs) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-    if (kv.second.xbuf) cudaFree(kv.second.xbuf);
-    if (kv.second.ybuf) cudaFree(kv.second.ybuf);
+    if (kv.second.xbuf) dfree(kv.second.xbuf);
+    if (kv.second.ybuf) dfree(kv.second.ybuf);
   }
   d.graphs.clear();
 }
@@ -1047,13 +1105,13 @@ void CudaBackend::free_list(DevList& d) {
   cudaStreamSynchronize(stream_);
   if (gstream_) cudaStreamSynchronize(gstream_);
   free_graphs(d);
-  if (d.tasks) cudaFree(d.tasks);
-  if (d.groups) cudaFree(d.groups);
-  if (d.wtiles) cudaFree(d.wtiles);
+  if (d.tasks) dfree(d.tasks);
+  if (d.groups) dfree(d.groups);
+  if (d.wtiles) dfree(d.wtiles);
   for (FpVariant& f : d.fv) {
-    if (f.tiles) cudaFree(f.tiles);
-    if (f.reds) cudaFree(f.reds);
-    if (f.part) cudaFree(f.part);
+    if (f.tiles) dfree(f.tiles);
+    if (f.reds) dfree(f.reds);
+    if (f.part) dfree(f.part);
   }
   if (d.tc) release_tc_plan(d.tc);
   d = DevList();
@@ -1262,11 +1320,11 @@ bool CudaBackend::ensure_part(FpVariant& f, int nvec) {
   if (f.part) {
     cudaStreamSynchronize(stream_);
     if (gstream_) cudaStreamSynchronize(gstream_);
-    cudaFree(f.part);
+    dfree(f.part);
   }
   f.part = nullptr;
   f.part_nvec = 0;
-  if (cudaMalloc(&f.part, sizeof(double) * f.psize * nvec) != cudaSuccess) {
+  if (dmalloc(&f.part, sizeof(double) * f.psize * nvec) != cudaSuccess) {
     cudaGetLastError();
     note(cudaErrorMemoryAllocation, "split partial tiles");
     f.part = nullptr;
@@ -1373,8 +1431,8 @@ void CudaBackend::launch_graphed(DevList& d, int key, const double* xv, double* 
     }
   }
   if (!gs.exec) {
-    if (cudaMalloc(&gs.xbuf, sizeof(double) * elems) != cudaSuccess ||
-        cudaMalloc(&gs.ybuf, sizeof(double) * elems) != cudaSuccess) {
+    if (dmalloc(&gs.xbuf, sizeof(double) * elems) != cudaSuccess ||
+        dmalloc(&gs.ybuf, sizeof(double) * elems) != cudaSuccess) {
       cudaGetLastError();
       gs.failed = true;
       enqueue(xv, yv);
@@ -1553,7 +1611,7 @@ void CudaBackend::task_values(const TaskList& tl, const double* xv, const double
   }
   cudaStreamSynchronize(stream_);
   for (void* p : {(void*)dt, (void*)dg, (void*)dtg})
-    if (p) cudaFree(p);
+    if (p) dfree(p);
 }
 
 // one warp per block: nz[i] = any element of block i nonzero (HBM-bound read)
@@ -1578,7 +1636,7 @@ void CudaBackend::nonzero_blocks(const std::vector<const double*>& p, const std:
   const double** dp = dev_copy(p, *this);
   long long* dn = dev_copy(n, *this);
   char* dz = nullptr;
-  if (dp && dn && cudaMalloc(&dz, p.size()) == cudaSuccess) {
+  if (dp && dn && dmalloc(&dz, p.size()) == cudaSuccess) {
     const int nb = (int)p.size();
     const int grid = std::min((nb + 7) / 8, 152 * 16);
     k_nonzero<<<grid, 256, 0, stream_>>>(dp, dn, nb, dz);
@@ -1591,7 +1649,7 @@ void CudaBackend::nonzero_blocks(const std::vector<const double*>& p, const std:
   }
   cudaStreamSynchronize(stream_);
   for (void* q : {(void*)dp, (void*)dn, (void*)dz})
-    if (q) cudaFree(q);
+    if (q) dfree(q);
 }
 
 void CudaBackend::lincomb(const LCList& l) {
@@ -1605,8 +1663,8 @@ void CudaBackend::lincomb(const LCList& l) {
   launches++;
   note(cudaGetLastError(), "k_lincomb");
   cudaStreamSynchronize(stream_);
-  cudaFree(b);
-  if (t) cudaFree(t);
+  dfree(b);
+  if (t) dfree(t);
 }
 
 }  // namespace tns

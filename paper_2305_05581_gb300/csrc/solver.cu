@@ -33,12 +33,12 @@ struct DBuf {  // owned device buffer
   void alloc(size_t n) {
     if (p) {
       cudaStreamSynchronize(be->stream());
-      cudaFree(p);
+      dfree(p);
     }
     p = nullptr;
     bytes = 0;
     if (n == 0) n = 8;
-    if (cudaMalloc(&p, n) != cudaSuccess) {
+    if (dmalloc(&p, n) != cudaSuccess) {
       cudaGetLastError();
       be->note(cudaErrorMemoryAllocation, "solver buffer");
       p = nullptr;
@@ -49,7 +49,7 @@ struct DBuf {  // owned device buffer
   ~DBuf() {
     if (p) {
       cudaStreamSynchronize(be->stream());
-      cudaFree(p);
+      dfree(p);
     }
   }
   double* d() const { return (double*)p; }
@@ -912,6 +912,13 @@ static int backend_diag_noalloc(tns::Engine& E, double* diag, std::string& err) 
   return tns::heff_diag_noalloc(be, E.step(), diag, err);
 }
 
+static long long backend_mem_peak(tns::Engine& E, bool reset) {
+  tns::CudaBackend& be = *static_cast<tns::CudaBackend*>(E.be());
+  const long long p = tns::dmem(be.device()).peak;
+  if (reset) tns::dmem_reset_peak(be.device());
+  return p;
+}
+
 static int backend_diag(tns::Engine& E, double* diag, std::string& err) {
   tns::CudaBackend& be = *static_cast<tns::CudaBackend*>(E.be());
   cudaSetDevice(be.device());
@@ -939,8 +946,7 @@ int one_step(Engine& E, CudaBackend& be, int k, bool ltr, const tns_sweep_opts* 
              double* psi_host, DBuf& X, Acc& acc, double* e, int* its, double* disc, bool* conv, std::string& err) {
   {
     Timer tm(be.stream());
-    int rc = E.ensure_left(k, err);
-    if (!rc) rc = E.ensure_right(k + 2, err);
+    int rc = E.ensure_step(k, err);
     if (!rc && !(E.step().valid && E.step().k == k)) rc = E.prepare_step(k, err);
     acc.env_ms += tm.stop();
     if (rc) return rc;

@@ -948,7 +948,7 @@ bool check_plan(const TcPlan& P, const std::vector<TcTile>& tiles, const std::ve
 template <class T>
 T* upload_vec(CudaBackend& be, const std::vector<T>& v, bool& ok) {
   T* p = nullptr;
-  if (cudaMalloc(&p, sizeof(T) * std::max<size_t>(v.size(), 1)) != cudaSuccess) {
+  if (dmalloc(&p, sizeof(T) * std::max<size_t>(v.size(), 1)) != cudaSuccess) {
     cudaGetLastError();
     ok = false;
     return nullptr;
@@ -993,14 +993,14 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
     plan->nxb = (int)xbs.size();
     plan->xbs_h = xbs;
     ImgJob* djobs = upload_vec(be, jobs, ok);
-    ok = ok && cudaMalloc(&plan->flag, 8 * sizeof(int)) == cudaSuccess;
-    ok = ok && cudaMalloc(&plan->ops_hi, std::max<long long>(plan->ops_bytes, 16)) == cudaSuccess;
-    if (es == 2) ok = ok && cudaMalloc(&plan->ops_lo, std::max<long long>(plan->ops_bytes, 16)) == cudaSuccess;
+    ok = ok && dmalloc(&plan->flag, 8 * sizeof(int)) == cudaSuccess;
+    ok = ok && dmalloc(&plan->ops_hi, std::max<long long>(plan->ops_bytes, 16)) == cudaSuccess;
+    if (es == 2) ok = ok && dmalloc(&plan->ops_lo, std::max<long long>(plan->ops_bytes, 16)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       if (djobs) {
         cudaStreamSynchronize(be.stream());
-        cudaFree(djobs);
+        dfree(djobs);
       }
       be.note(cudaErrorMemoryAllocation, "tensor-core plan / operand images");
       release_tc_plan(plan);
@@ -1015,21 +1015,21 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
       be.note(cudaGetLastError(), "operand images");
     }
     be.note(cudaStreamSynchronize(be.stream()), "operand images");
-    cudaFree(djobs);
+    dfree(djobs);
     d.tc = plan;
     d.tc_gen = tl.gen;
   }
   if (plan->x_nvec < nvec) {
     if (plan->x_hi) {
       cudaStreamSynchronize(be.stream());
-      cudaFree(plan->x_hi);
-      if (plan->x_lo) cudaFree(plan->x_lo);
+      dfree(plan->x_hi);
+      if (plan->x_lo) dfree(plan->x_lo);
     }
     plan->x_hi = plan->x_lo = nullptr;
     plan->x_nvec = 0;
     const size_t xb = (size_t)std::max<long long>(plan->x_bytes, 16) * nvec;
-    bool ok = cudaMalloc(&plan->x_hi, xb) == cudaSuccess;
-    if (es == 2) ok = ok && cudaMalloc(&plan->x_lo, xb) == cudaSuccess;
+    bool ok = dmalloc(&plan->x_hi, xb) == cudaSuccess;
+    if (es == 2) ok = ok && dmalloc(&plan->x_lo, xb) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       be.note(cudaErrorMemoryAllocation, "tensor-core input images");
@@ -1064,11 +1064,11 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
   if (V.psize > 0 && V.part_nvec < nvec) {
     if (V.part) {
       cudaStreamSynchronize(be.stream());
-      cudaFree(V.part);
+      dfree(V.part);
     }
     V.part = nullptr;
     V.part_nvec = 0;
-    if (cudaMalloc(&V.part, sizeof(double) * V.psize * nvec) != cudaSuccess) {
+    if (dmalloc(&V.part, sizeof(double) * V.psize * nvec) != cudaSuccess) {
       cudaGetLastError();
       be.note(cudaErrorMemoryAllocation, "tensor-core partial tiles");
       return false;
@@ -1146,18 +1146,18 @@ void release_tc_plan(void* p) {
   TcPlan* plan = (TcPlan*)p;
   if (!plan) return;
   for (TcVariant& V : plan->var) {
-    if (V.tiles) cudaFree(V.tiles);
-    if (V.reds) cudaFree(V.reds);
-    if (V.part) cudaFree(V.part);
+    if (V.tiles) dfree(V.tiles);
+    if (V.reds) dfree(V.reds);
+    if (V.part) dfree(V.part);
   }
-  if (plan->tasks) cudaFree(plan->tasks);
-  if (plan->chunks) cudaFree(plan->chunks);
-  if (plan->xblocks) cudaFree(plan->xblocks);
-  if (plan->flag) cudaFree(plan->flag);
-  if (plan->ops_hi) cudaFree(plan->ops_hi);
-  if (plan->ops_lo) cudaFree(plan->ops_lo);
-  if (plan->x_hi) cudaFree(plan->x_hi);
-  if (plan->x_lo) cudaFree(plan->x_lo);
+  if (plan->tasks) dfree(plan->tasks);
+  if (plan->chunks) dfree(plan->chunks);
+  if (plan->xblocks) dfree(plan->xblocks);
+  if (plan->flag) dfree(plan->flag);
+  if (plan->ops_hi) dfree(plan->ops_hi);
+  if (plan->ops_lo) dfree(plan->ops_lo);
+  if (plan->x_hi) dfree(plan->x_hi);
+  if (plan->x_lo) dfree(plan->x_lo);
   delete plan;
 }
 

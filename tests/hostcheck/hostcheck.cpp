@@ -7,6 +7,7 @@
 // tnshc_*); the product library never contains or loads it, and it is not a
 // fallback for anything: it has no Davidson, truncation or sweep.
 #include <cstdlib>
+#include <map>
 #include <cstring>
 #include <stdexcept>
 #include <string>
@@ -16,8 +17,37 @@
 
 namespace {
 struct HostBackend : tns::Backend {
-  double* alloc(long long n) override { return (double*)std::calloc((size_t)n, sizeof(double)); }
-  void release(double* p) override { std::free(p); }
+  // allocation accounting with an optional budget, standing in for a device
+  std::map<void*, long long> live;
+  long long used = 0, peak = 0, budget = 0;
+  double* alloc(long long n) override {
+    const long long b = n * 8;
+    if (budget > 0 && used + b > budget) return nullptr;
+    double* p = (double*)std::calloc((size_t)n, sizeof(double));
+    if (p) {
+      live[p] = b;
+      used += b;
+      if (used > peak) peak = used;
+    }
+    return p;
+  }
+  void release(double* p) override {
+    auto it = live.find(p);
+    if (it != live.end()) {
+      used -= it->second;
+      live.erase(it);
+    }
+    std::free(p);
+  }
+  long long mem_used() override { return used; }
+  long long mem_limit() override { return budget; }
+  long long mem_free() override { return 1LL << 60; }
+  void set_budget(long long bytes) override { budget = bytes > 0 ? bytes : 0; }
+  double* host_alloc(long long n) override { return (double*)std::malloc((size_t)n * sizeof(double)); }
+  void host_release(double* p) override { std::free(p); }
+  void forget(const tns::TaskList&) override {}
+  // the plain-loop executor allocates nothing to run a work list
+  long long step_bytes(const tns::TaskList&, long long) override { return 0; }
   void upload(double* d, const double* s, long long n) override { std::memcpy(d, s, (size_t)n * 8); }
   void download(double* d, const double* s, long long n) override { std::memcpy(d, s, (size_t)n * 8); }
   void zero(double* p, long long n) override { std::memset(p, 0, (size_t)n * 8); }
@@ -127,6 +157,13 @@ static int backend_sweep(tns::Engine&, const tns_sweep_opts*, double*, tns_sweep
   err = "not available in the host-logic check library";
   return -2;
 }
+static long long backend_mem_peak(tns::Engine& e, bool reset) {
+  HostBackend& b = *static_cast<HostBackend*>(e.be());
+  const long long p = b.peak;
+  if (reset) b.peak = b.used;
+  return p;
+}
+
 static int backend_diag(tns::Engine& e, double* diag, std::string&) {
   tns::Step& st = e.step();
   std::memset(diag, 0, (size_t)st.length * 8);
