@@ -2,14 +2,19 @@
 
 A step is one two-site DMRG step (one "iteration cycle" of a sweep) at the
 middle of the chain: partial sums and work lists, device Davidson with the
-H_eff*psi grouped products, SVD truncation to D and renormalisation.
-Workload: 24 orbitals, 24 electrons, S_z = 0, random integrals with decay
-length 5 (seed 1), D = 512 -- synthetic stand-ins for the paper's molecular
-integrals.  Sector products in split-BF16 on the tensor cores by default
-(--precision), Davidson/truncation in FP64; the energy of the next step's
-H_eff is checked against an FP64 Davidson (energy_check).  Untimed set-up: one
-full sweep (bond dimension D on both sides of the middle), then the second
-sweep up to the warm-up steps; W warm-up and K timed steps follow.
+H_eff*psi grouped products, SVD truncation to D and renormalisation.  The
+steps cycle over the five bonds around the middle (left to right, then right
+to left), so --steps only changes the number of samples.
+Workload (--workload, default n24): 24 orbitals, 24 electrons, S_z = 0, random
+integrals with decay length 5 (seed 1), D = 512 -- synthetic stand-ins for the
+paper's molecular integrals.  Sector products in split-BF16 on the tensor
+cores by default (--precision), Davidson/truncation in FP64.  At the step
+after the timed ones, Davidson with FP64 products runs beside the precision
+form on the same H_eff from the same start vector: the FP64 GPU arm (time,
+products, TFLOP/s) and the energy check.  Untimed set-up: one full sweep from
+the initial MPS (systems up to 40 orbitals) or the initial MPS itself (larger
+ones, under a device budget with host staging of the catalogues), then W
+warm-up and K timed steps.
 
 Output: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 (oracle/dmrg.py) on a bounded sample of the same workload instead.
@@ -31,12 +36,10 @@ sys.path.insert(0, ROOT)
 METRIC = "H_eff\u00b7\u03c8 useful TFLOP/s and s per two-site step at \u0394E\u22641e-8 Ha vs FP64 GPU path"
 UNIT = "TFLOP/s"
 
-# DRAM bytes (read + write) of the dominant kernel per H_eff*psi at this
-# workload's middle bond, from the ncu capture summarised in
-# profiles/k_tasks_tc_bf16x3_n24_state.md (measured on the state after one
-# sweep and scaled by useful flops to the second sweep's middle bond; None
-# until captured for the current kernel of that precision).
-TRAFFIC_BYTES_PER_HEFF = {"fp64": None, "tf32": None, "bf16x3": 3.49e9}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
+# kernel per H_eff*psi launch at a workload's middle bond, from one ncu capture
+# of the current kernel; None when no capture of the current kernel exists.
+TRAFFIC_BYTES_PER_HEFF = {}
 
 
 def parse():
@@ -59,6 +62,15 @@ def parse():
                    help="--case heff: a random MPS, or the state after one sweep from the initial MPS")
     p.add_argument("--clocks-dir", default=None,
                    help="folder for the nvidia-smi samples of the timed region (default: the temp folder)")
+    p.add_argument("--setup", default=None, choices=["sweep", "init"],
+                   help="state of the timed steps: 'sweep' = one full warm-up sweep from the initial MPS "
+                        "(default up to 40 orbitals), 'init' = the initial MPS itself, environments built "
+                        "straight to the window (default for larger systems)")
+    p.add_argument("--block", type=int, default=1, help="Davidson block size (vectors per batched product)")
+    p.add_argument("--device-budget-gb", type=float, default=None,
+                   help="device memory budget of the engine (default: device size - 24 GB for n76, none otherwise)")
+    p.add_argument("--host-gb", type=float, default=None,
+                   help="pinned host memory for staged catalogues (default: 120 GB for n76, none otherwise)")
     return p.parse_args()
 
 
@@ -161,6 +173,16 @@ def sweep_plan(N):
     return plan
 
 
+def window_cycle(N, half=2):
+    """The timed steps bounce over the bonds around the middle: left to right
+    over sites mid-half..mid+half-1, then right to left over mid+half..mid-half+1
+    (each step renormalises one block and every block the next step reads is
+    current), so the workload does not depend on the number of steps."""
+    mid = N // 2 - 1
+    a, b = mid - half, mid + half
+    return [(k, True) for k in range(a, b)] + [(k, False) for k in range(b, a, -1)]
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -233,26 +255,67 @@ def combine_ranks(dist, elapsed, flops, device):
     return float(t), float(f)
 
 
-def workload_config(args, c):
+def workload_config(args, c, setup):
     N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
+    mid = N // 2 - 1
+    state = ("one warm-up sweep from the initial MPS" if setup == "sweep" else
+             "the initial MPS (all reachable sectors, 0/1 isometries), environments built straight to the window")
     return {"workload": f"{args.workload}: N={N} n_elec={n} 2Sz={s2} D={D} lambda={c['lam']} seed={c['seed']}; "
-                        f"one warm-up sweep, then two-site steps around the middle bond",
-            "precision": args.precision, "davidson_tol": args.tol,
+                        f"{state}; two-site steps cycling over sites {mid - 2}..{mid + 2} "
+                        f"(left to right {mid - 2}..{mid + 1}, right to left {mid + 2}..{mid - 1})",
+            "precision": args.precision, "davidson_tol": args.tol, "davidson_block": args.block,
             "l2": "inputs larger than L2 (operator arenas are GBs)"}
 
 
-def peak_for(args, torch):
+def tf32_gemm_peak(torch):
+    """torch.matmul FP32 with TF32 tensor cores (TFLOP/s): the measured TF32 denominator."""
+    n = 8192
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        a = torch.randn(n, n, device="cuda", dtype=torch.float32)
+        b = torch.randn_like(a)
+        for _ in range(2):
+            a @ b
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 1e30
+        for _ in range(5):
+            e0.record()
+            a @ b
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        del a, b
+        return 2.0 * n ** 3 / best / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def measured_peaks(torch):
+    """The denominators: bf16 and HBM from MEASURED_PEAKS.json (driver-measured
+    on this pool), FP64 DGEMM and TF32 GEMM measured here with torch.matmul."""
+    mp = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+    except OSError:
+        pass
+    return {"bf16_tflops_sustained": mp.get("bf16_tflops_sustained", 1700.0),
+            "bf16_source": "MEASURED_PEAKS.json" if mp else "fallback 1.7 PFLOP/s sustained",
+            "hbm_gbs": mp.get("hbm_gbs", 6800.0),
+            "fp64_dgemm_tflops": fp64_gemm_peak(torch),
+            "tf32_gemm_tflops": tf32_gemm_peak(torch)}
+
+
+def peak_for(args, peaks):
     """(peak TFLOP/s, bound, source) for the dominant kernel of the chosen precision."""
     if args.precision == "fp64":
-        return (fp64_gemm_peak(torch), "alu",
-                "cuBLAS DGEMM 4096^3 measured in this run (MEASURED_PEAKS.json has no FP64 entry)")
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-        mp = json.load(f)
-    bf16 = mp["bf16_tflops_sustained"]
+        return peaks["fp64_dgemm_tflops"], "alu", "cuBLAS DGEMM 4096^3 measured in this run"
     if args.precision == "bf16x3":
-        return bf16, "tensor", "MEASURED_PEAKS.json bf16_tflops_sustained (dense bf16, timed inside a long step)"
-    return (bf16 * 1.1 / 2.25, "tensor",
-            "MEASURED_PEAKS.json bf16_tflops_sustained x nominal TF32/BF16 ratio 1.1/2.25")
+        return (peaks["bf16_tflops_sustained"], "tensor",
+                f"{peaks['bf16_source']} bf16_tflops_sustained (dense bf16, timed inside a long step)")
+    return peaks["tf32_gemm_tflops"], "tensor", "torch.matmul TF32 8192^3 measured in this run"
 
 
 def main():
@@ -263,7 +326,6 @@ def main():
     if args.impl == "reference":
         return run_reference_full(args, rank, world)
 
-    import numpy as np
     import torch
     import synth
     from paper_2305_05581_gb300 import Context, TNS_FP64, TNS_TF32, TNS_BF16X3
@@ -283,29 +345,36 @@ def main():
     prec = P[args.precision]
     c = synth.WORKLOADS[args.workload]
     N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
-    peak, bound, peak_source = peak_for(args, torch)
+    setup = args.setup or ("sweep" if N <= 40 else "init")
+    peaks = measured_peaks(torch)
+    peak, bound, peak_source = peak_for(args, peaks)
     h, v = synth.integrals(N, c["lam"], c["seed"])
     stream = torch.cuda.current_stream()
     ctx = Context(device=local, stream=stream.cuda_stream)
+    big = N > 40
+    budget_gb = args.device_budget_gb if args.device_budget_gb is not None else (
+        torch.cuda.mem_get_info()[1] / 2 ** 30 - 24 if big else 0)
+    host_gb = args.host_gb if args.host_gb is not None else (120 if big else 0)
+    ctx.set_memory_budget(int(budget_gb * 2 ** 30), int(host_gb * 2 ** 30))
     ctx.load_integrals(h, v)
     ctx.mps_init(N, n, s2, D, seed=c["seed"])
-    plan = sweep_plan(N)
-    mid = N // 2 - 1
-    # untimed set-up: one full sweep to reach bond dimension D on both sides,
-    # then the second sweep up to the warm-up steps
-    start = max(0, mid - args.warmup - args.steps // 2)
-    setup = plan + [(k, True) for k in range(0, start)]
-    for k, ltr in setup:
-        ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec)
-    second = [(k, True) for k in range(start, N - 2)] + plan[N - 2:]
+    cycle = window_cycle(N)
+    step = lambda k, ltr, **kw: ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec,
+                                          block=args.block, **kw)
+    # untimed set-up: the state of the timed steps, positioned at the window
+    # (its first step runs left to right at site cycle[0])
+    if setup == "sweep":
+        for k, ltr in sweep_plan(N) + [(k, True) for k in range(0, cycle[0][0])]:
+            step(k, ltr)
     i = 0
     for _ in range(args.warmup):
-        k, ltr = second[i % len(second)]
-        ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec)
+        k, ltr = cycle[i % len(cycle)]
+        step(k, ltr)
         i += 1
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    ctx.memory_stats(reset=True)
     clocks = Clocks(local, args.clocks_dir)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -316,8 +385,8 @@ def main():
     launches = 0
     stats = []
     for _ in range(args.steps):
-        k, ltr = second[i % len(second)]
-        st = ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec)
+        k, ltr = cycle[i % len(cycle)]
+        st = step(k, ltr)
         flops += st.heff_flops
         heff_s += st.heff_seconds
         if st.iters > 0:
@@ -325,42 +394,61 @@ def main():
         red_s += st.heff_seconds - st.exact_seconds
         iters += st.iters
         launches += st.kernel_launches
-        stats.append((k, st.energy, st.iters, st.bond_dim, st.seconds, st.length, st.heff_seconds,
-                      st.env_seconds, st.svd_seconds, st.exact_products, st.exact_seconds))
+        stats.append(st)
         i += 1
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    mem = ctx.memory_stats()
     elapsed = e0.elapsed_time(e1) * 1e-3
     elapsed, flops_all = combine_ranks(dist, elapsed, flops, "cuda")
     value = flops_all / elapsed / 1e12
 
-    # energy check at the next step's H_eff: Davidson in this precision (FP64
-    # residual correction) against Davidson in FP64, from the same start vector
-    k, ltr = second[i % len(second)]
+    # FP64 GPU arm and energy check at the next step's H_eff: Davidson in this
+    # precision (FP64 residual correction) against Davidson with FP64 products,
+    # from the same start vector, each timed with CUDA events
+    k, ltr = cycle[i % len(cycle)]
     ctx.build_env(k)
+    fl_k, _ = ctx.heff_flops(k)
     L = ctx.psi_guess(k)
     x0 = torch.empty(L, dtype=torch.float64, pin_memory=True)
     ctx.psi_guess(k, x0.data_ptr())
     xa = x0.to("cuda")
     xb = x0.to("cuda")
-    e64, _, _ = ctx.davidson_ptr(k, xa.data_ptr(), tol=args.tol, max_iter=200, precision=TNS_FP64)
-    ep, _, _ = ctx.davidson_ptr(k, xb.data_ptr(), tol=args.tol, max_iter=200, precision=prec)
-    echeck = {"site": k, "E_fp64_Ha": e64, "E_precision_Ha": ep, "delta_E_Ha": abs(ep - e64)}
+
+    def timed_davidson(x, p):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e, its, _ = ctx.davidson_ptr(k, x.data_ptr(), tol=args.tol, max_iter=200, precision=p)
+        b.record(stream)
+        b.synchronize()
+        return e, its, a.elapsed_time(b) * 1e-3
+
+    e64, it64, t64 = timed_davidson(xa, TNS_FP64)
+    ep, itp, tp = timed_davidson(xb, prec)
+    echeck = {"site": k, "E_fp64_Ha": e64, "E_precision_Ha": ep, "delta_E_Ha": abs(ep - e64),
+              "fp64_products": it64, "precision_products": itp}
+    env_med = statistics.median([st.env_seconds for st in stats])
+    svd_med = statistics.median([st.svd_seconds for st in stats])
+    fp64_arm = {"site": k, "davidson_s": t64, "products": it64, "heff_tflops": fl_k * it64 / t64 / 1e12,
+                "s_per_step": t64 + env_med + svd_med,
+                "note": "FP64 Davidson on the step's H_eff (all products FP64, DFMA) plus the timed steps' median "
+                        "environment and truncation time"}
+    prec_arm = {"davidson_s": tp, "products": itp, "s_per_step": tp + env_med + svd_med}
+    speedup = {"per_step": fp64_arm["s_per_step"] / prec_arm["s_per_step"], "davidson": t64 / tp}
 
     # end to end through the public API with host buffers: each step uploads
     # its start vector from pinned host memory and reads the converged psi back
     e2e_steps = max(1, min(args.steps, 3))
     lens = []
     for _ in range(e2e_steps):
-        k, ltr = second[i % len(second)]
+        k, ltr = cycle[i % len(cycle)]
         L = ctx.psi_guess(k)
         xh = torch.empty(L, dtype=torch.float64, pin_memory=True)
         ph = torch.empty(L, dtype=torch.float64, pin_memory=True)
         ctx.psi_guess(k, xh.data_ptr())
         t1 = time.perf_counter()
-        st = ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec, x0_host_ptr=xh.data_ptr(),
-                      psi_host_ptr=ph.data_ptr())
+        st = step(k, ltr, x0_host_ptr=xh.data_ptr(), psi_host_ptr=ph.data_ptr())
         lens.append((time.perf_counter() - t1, st.heff_flops, L))
         i += 1
     e2e_time = sum(x[0] for x in lens)
@@ -382,9 +470,20 @@ def main():
               f"+ split reduction")
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None,
-                "traffic": TRAFFIC_BYTES_PER_HEFF.get(args.precision),
+                "traffic": TRAFFIC_BYTES_PER_HEFF.get((args.workload, args.precision)),
                 "kernel": kernel, "peak_source": peak_source,
                 "achieved_is": achieved_is}
+    env_s = sum(st.env_seconds for st in stats)
+    env_b = sum(st.env_bytes for st in stats)
+    env_f = sum(st.env_flops for st in stats)
+    env = {"seconds_per_step": env_s / len(stats), "bytes_per_step": env_b / len(stats),
+           "gbs": env_b / env_s / 1e9 if env_s > 0 else None,
+           "hbm_frac": env_b / env_s / 1e9 / peaks["hbm_gbs"] if env_s > 0 else None,
+           "flops_per_step": env_f / len(stats), "tflops": env_f / env_s / 1e12 if env_s > 0 else None,
+           "fp64_frac": env_f / env_s / 1e12 / peaks["fp64_dgemm_tflops"] if env_s > 0 else None,
+           "note": "partial sums and renormalisation of the timed steps (host work-list build included): "
+                   "algorithmic bytes (operands read once, results written once) and FP64 flops / time, "
+                   "against the measured HBM copy rate and DGEMM rate"}
     if rank == 0:
         cpu = None
         try:
@@ -392,10 +491,12 @@ def main():
         except Exception as ex:  # the baseline is reported, never required
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {ex}"}
-        cfg = workload_config(args, c)
-        cfg["steps_detail"] = [{"site": s[0], "energy": s[1], "matvecs": s[2], "bond": s[3], "seconds": s[4],
-                                "psi_length": s[5], "heff_s": s[6], "env_s": s[7], "svd_s": s[8],
-                                "fp64_products": s[9], "fp64_s": s[10]} for s in stats]
+        cfg = workload_config(args, c, setup)
+        cfg["steps_detail"] = [{"site": cycle[(args.warmup + j) % len(cycle)][0], "energy": st.energy,
+                                "matvecs": st.iters, "bond": st.bond_dim, "seconds": st.seconds,
+                                "psi_length": st.length, "heff_s": st.heff_seconds, "env_s": st.env_seconds,
+                                "svd_s": st.svd_seconds, "fp64_products": st.exact_products,
+                                "fp64_s": st.exact_seconds} for j, st in enumerate(stats)]
         cfg["energy_check"] = echeck
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
@@ -403,6 +504,10 @@ def main():
                 "data": "synthetic", "config": cfg,
                 "s_per_step": elapsed / args.steps,
                 "heff_matvecs_per_step": iters / args.steps,
+                "fp64_arm": fp64_arm, "precision_arm": prec_arm, "speedup_vs_fp64": speedup,
+                "env": env, "memory": {k2: mem[k2] for k2 in ("device_peak", "device_limit", "host_peak", "staged",
+                                                              "restored", "dropped", "built")},
+                "peaks": peaks,
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
@@ -463,11 +568,15 @@ def run_reference_full(args, rank, world):
     val = flops * args.steps / dt / 1e12
     sample = (f"oracle dense-operator H_eff*psi at the middle bond of the {N}-orbital workload with D={Ds} "
               f"(not {c['D']}); env build excluded; useful flops {flops:.3e} per product")
+    cfg = workload_config(args, c, "init")
+    cfg["workload"] = (f"{args.workload}: N={N} n_elec={n} 2Sz={s2} lambda={c['lam']} seed={c['seed']}, "
+                       f"bond dimension D={Ds} (a bounded sample: the workload's D={c['D']} does not fit the "
+                       f"dense-operator oracle); one H_eff*psi at the middle bond of a random MPS per step")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": workload_config(args, c),
+            "config": cfg,
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

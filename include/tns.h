@@ -124,6 +124,20 @@ int tns_psi_layout(tns_ctx* ctx, int site, int* n_blocks, const long long** desc
  * tns_build_env(site).  Runs on the context stream and synchronises it. */
 int tns_heff_apply(tns_ctx* ctx, int site, const double* X, double* Y, int nvec, int precision);
 
+/* One part of an operator-row split of tns_heff_apply (Sec. "Independent
+ * operational tasks": the rows of the operator table -- the pairs of normal
+ * and complementary operators -- are distributed over devices, every device
+ * accumulates the output blocks of its rows, and one sum over the devices
+ * gives H_eff X).  The rows are assigned to nparts parts by their flop cost
+ * (longest first onto the least loaded part); the assignment depends only on
+ * the step, so every caller with the same MPS and integrals gets the same
+ * split.  Y (DEVICE, nvec vectors of `length`) is overwritten with the sum over
+ * the rows of part `part` (0 <= part < nparts); summing Y over all parts (e.g.
+ * an all-reduce across ranks) gives tns_heff_apply's result up to rounding
+ * order.  Same arguments, layout and precisions as tns_heff_apply. */
+int tns_heff_apply_part(tns_ctx* ctx, int site, const double* X, double* Y, int nvec, int precision, int part,
+                        int nparts);
+
 /* Diagonal of H_eff at step (site, site+1) into the DEVICE vector diag
  * (length doubles).  Used as the Davidson preconditioner. */
 int tns_heff_diag(tns_ctx* ctx, int site, double* diag);
@@ -169,8 +183,8 @@ int tns_heff_adjoint(tns_ctx* ctx, int site, const double* X, const double* Ybar
  *  - TNS_ERR_ARG if the step's diagonal work list needs more than
  *    TNS_NOALLOC_DIAG_MAX index entries.
  *  - The first call on a device looks up the array's device address (once
- *    per device, with that device current); make that first call before any
- *    stream capture.
+ *    per device and CUDA context, with that device current: again after a
+ *    device reset); make that first call before any stream capture.
  *  - All calls share the array and each call rewrites the part it uses, so
  *    nothing carries over between calls; calls that overlap on the GPU (from
  *    several contexts or threads) race on it and must be serialised. */
@@ -267,6 +281,9 @@ typedef struct tns_step_stats {
   long long kernel_launches; /* launches of the engine's own CUDA kernels in the call */
   int exact_products;       /* FP64 products among iters (reduced-precision refreshes; 0 on the FP64 path) */
   double exact_seconds;     /* device time of those FP64 products */
+  double env_flops;         /* FP64 flops of the step's renormalisation products */
+  double env_bytes;         /* algorithmic bytes of the step's partial sums and renormalisation
+                               (operands read once, results written once) */
 } tns_step_stats;
 
 /* One two-site step of a sweep at (site, site+1) (one "DMRG iteration cycle",
@@ -297,6 +314,19 @@ int tns_psi_guess(tns_ctx* ctx, int site, double* x_host, long long* length);
  * zero are not counted.  *nproducts receives the number of block products the
  * kernels execute (each expression of a dot block is one product there). */
 int tns_heff_flops(tns_ctx* ctx, int site, double* flops, long long* nproducts);
+
+/* Checkpoint / restart of a sweep (the long FeMoco runs of Sec. "Model
+ * systems" restart from a stored MPS).  tns_checkpoint_save writes the
+ * integrals, the MPS (bond sectors and site tensors) and a sweep position
+ * (the next step's site and direction, stored as given) to the file `path`
+ * (binary, little-endian, versioned, ended by a 64-bit FNV-1a hash of its
+ * contents).  tns_checkpoint_load reads such a file into the context,
+ * replacing its integrals and MPS (environments are rebuilt on demand), and
+ * returns the position (site, left_to_right may be NULL).  A file that is
+ * not a checkpoint, truncated or altered is refused with TNS_ERR_ARG before
+ * the context changes.  Synchronous. */
+int tns_checkpoint_save(tns_ctx* ctx, const char* path, int site, int left_to_right);
+int tns_checkpoint_load(tns_ctx* ctx, const char* path, int* site, int* left_to_right);
 
 /* Out-of-HBM environments (the tree-traversal cache of Alg. 1, Sec. "Tree-
  * Traversal Optimized Virtual Memory Addressing", applied to the chain of

@@ -345,6 +345,29 @@ def heff_apply(LL: Block, RR: Block, Psi: np.ndarray) -> np.ndarray:
     return Y
 
 
+def heff_apply_abs(LL: Block, RR: Block, Psi: np.ndarray) -> np.ndarray:
+    """Error-bound helper (not the method): the term sum of ``heff_apply`` with
+    every operator and Psi replaced by its elementwise absolute value,
+    sum_a |O_a^LL| |Psi| |O_a^RR|^T.  The forward error of a sum of matrix
+    products whose operands and partial results carry a relative rounding u is
+    bounded elementwise by a small multiple of u times this sum."""
+    A = np.abs
+    Pa = A(Psi)
+    Y = A(LL.ops["H"]) @ Pa + Pa @ A(RR.ops["H"]).T
+    for k in _keys(LL, "c"):
+        X, S = A(LL.ops[k]), A(RR.ops[("S", k[1])])
+        Y += X @ Pa @ S.T + X.T @ Pa @ S
+    for k in _keys(RR, "c"):
+        T, cx = A(LL.ops[("T", k[1])]), A(RR.ops[k])
+        Y += T @ Pa @ cx + T.T @ Pa @ cx.T
+    for k in _keys(LL, "A"):
+        X, P = A(LL.ops[k]), A(RR.ops[("P", k[1], k[2])])
+        Y += X @ Pa @ P.T + X.T @ Pa @ P
+    for k in _keys(LL, "B"):
+        Y += A(LL.ops[k]) @ Pa @ A(RR.ops[("Q", k[1], k[2])]).T
+    return Y
+
+
 # ---------------------------------------------------------------------------
 # block-sparse MPS <-> dense helpers
 # ---------------------------------------------------------------------------
@@ -437,6 +460,11 @@ class DenseHeff:
 
     def apply_matrix(self, Psi):
         return heff_apply(self.LL, self.RR, Psi)
+
+    def apply_abs(self, X: dict) -> dict:
+        """sum_a |O_a^LL| |X| |O_a^RR|^T (error-bound helper, see heff_apply_abs)."""
+        keys = [(key, blk.shape) for key, blk in X.items()]
+        return self.from_matrix(heff_apply_abs(self.LL, self.RR, self.to_matrix(X)), keys)
 
     def sector_mask(self):
         n = (self.LL.n[:, None] + self.RR.n[None, :])

@@ -23,7 +23,8 @@ SYMBOLS = ["create", "destroy", "last_error", "load_integrals", "mps_init", "mps
            "mps_set_bond", "mps_set_site", "mps_get_bond", "mps_get_site", "build_env",
            "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops", "step", "psi_guess",
            "heff_diag_noalloc", "env_arena", "heff_adjoint", "sym_eig", "rdm", "set_memory_budget",
-           "memory_stats"]
+           "memory_stats", "heff_apply_part",
+           "checkpoint_save", "checkpoint_load"]
 
 
 class TnsError(RuntimeError):
@@ -49,7 +50,7 @@ class StepStats(C.Structure):
                 ("heff_flops", C.c_double), ("heff_seconds", C.c_double), ("env_seconds", C.c_double),
                 ("svd_seconds", C.c_double), ("seconds", C.c_double), ("length", C.c_longlong),
                 ("bond_dim", C.c_int), ("kernel_launches", C.c_longlong), ("exact_products", C.c_int),
-                ("exact_seconds", C.c_double)]
+                ("exact_seconds", C.c_double), ("env_flops", C.c_double), ("env_bytes", C.c_double)]
 
 
 class MemStats(C.Structure):
@@ -90,6 +91,7 @@ def load_library(path: str = DEFAULT_LIB, prefix: str = "tns_"):
         "psi_layout": (C.c_int, [vp, C.c_int, ip, C.POINTER(llp), llp]),
         "heff_apply": (C.c_int, [vp, C.c_int, vp, vp, C.c_int, C.c_int]),
         "heff_diag": (C.c_int, [vp, C.c_int, vp]),
+        "heff_apply_part": (C.c_int, [vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int]),
         "davidson": (C.c_int, [vp, C.c_int, vp, C.c_double, C.c_int, C.c_int, dp, ip]),
         "sweep": (C.c_int, [vp, C.POINTER(SweepOpts), dp, C.POINTER(SweepStats)]),
         "heff_flops": (C.c_int, [vp, C.c_int, dp, llp]),
@@ -101,6 +103,8 @@ def load_library(path: str = DEFAULT_LIB, prefix: str = "tns_"):
         "sym_eig": (C.c_int, [vp, C.c_int, ip, vp, vp, vp]),
         "rdm": (C.c_int, [vp, C.c_int, vp, dp, dp]),
         "set_memory_budget": (C.c_int, [vp, C.c_longlong, C.c_longlong]),
+        "checkpoint_save": (C.c_int, [vp, C.c_char_p, C.c_int, C.c_int]),
+        "checkpoint_load": (C.c_int, [vp, C.c_char_p, ip, ip]),
         "memory_stats": (C.c_int, [vp, C.POINTER(MemStats), C.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -207,6 +211,12 @@ class Context:
     def heff_apply_ptr(self, site, x_ptr: int, y_ptr: int, nvec: int = 1, precision: int = TNS_FP64):
         self._check(self._fn("heff_apply")(self._h, site, C.c_void_p(x_ptr), C.c_void_p(y_ptr), nvec, precision))
 
+    def heff_apply_part_ptr(self, site, x_ptr: int, y_ptr: int, part: int, nparts: int, nvec: int = 1,
+                            precision: int = TNS_FP64):
+        """Part `part` of an nparts-way operator-row split of H_eff X (tns_heff_apply_part)."""
+        self._check(self._fn("heff_apply_part")(self._h, site, C.c_void_p(x_ptr), C.c_void_p(y_ptr), nvec, precision,
+                                                part, nparts))
+
     def heff_diag_ptr(self, site, d_ptr: int):
         self._check(self._fn("heff_diag")(self._h, site, C.c_void_p(d_ptr)))
 
@@ -272,6 +282,16 @@ class Context:
                                      C.c_void_p(psi_host_ptr) if psi_host_ptr else None, C.byref(st)))
         return st
 
+
+    def checkpoint_save(self, path: str, site: int = 0, left_to_right: bool = True):
+        """Write integrals, MPS and the sweep position to `path` (tns_checkpoint_save)."""
+        self._check(self._fn("checkpoint_save")(self._h, os.fsencode(path), site, int(left_to_right)))
+
+    def checkpoint_load(self, path: str):
+        """Read a checkpoint into this context; returns (site, left_to_right)."""
+        s, d = C.c_int(), C.c_int()
+        self._check(self._fn("checkpoint_load")(self._h, os.fsencode(path), C.byref(s), C.byref(d)))
+        return s.value, bool(d.value)
 
     def set_memory_budget(self, device_bytes: int = 0, host_bytes: int = 0):
         """Device budget and pinned host memory for staged catalogues (0 = none)."""

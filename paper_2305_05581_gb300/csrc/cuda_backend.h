@@ -113,6 +113,11 @@ class CudaBackend : public Backend {
   // peak at ~1.0 TFLOP/s alike and the DFMA kernel measured faster), 1 DMMA
   // (mma.sync m8n8k4 f64); environment TNS_FP64_KERNEL=dfma|dmma
   int fp64_kernel = 0;
+  // bound of one wait inside the tensor-core product loop (ns); the
+  // environment variable TNS_TC_WAIT_NS overrides the default 0.2 s when the
+  // backend is created (a test makes the waits run out with it and checks the
+  // reported error and that the context stays usable)
+  unsigned long long tc_wait_ns = 200000000ull;
   ~CudaBackend() override;
   double* alloc(long long n) override;
   void release(double* p) override;

@@ -15,6 +15,7 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstdlib>
@@ -370,6 +371,10 @@ Lin operator*(const Lin& a, const Lin& b) {
 }
 
 int Engine::load_integrals(int N, const double* h, const double* v, double e_core, std::string& err) {
+  {
+    const char* ve = std::getenv("TNS_VERBOSE_ENV");
+    verbose_env_ = ve && *ve && *ve != '0';
+  }
   if (N < 2 || N > 128 || !h || !v) {
     err = "load_integrals: need 2 <= N <= 128 and non-null h, v";
     return -1;
@@ -535,6 +540,176 @@ int Engine::mps_get_site(int b, double* x, long long len, long long* len_out, st
   }
   be_->download(x, sites_[b].d, len);
   be_->sync();
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint / restart: integrals, MPS and sweep position in one binary file
+//   "TNSCKPT1", int32 version, N, n_elec, two_sz, D, site, left_to_right,
+//   double e_core, h (N^2), v (N^4), per bond: int32 nsec + nsec x (n, two_sz,
+//   dim), per site: int64 len + len doubles, then the 64-bit FNV-1a hash of
+//   every byte before it.  Little-endian hosts (x86-64, Arm64) only.
+// ---------------------------------------------------------------------------
+namespace {
+struct Fnv {
+  unsigned long long h = 1469598103934665603ULL;
+  void add(const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ULL;
+  }
+};
+struct Writer {
+  FILE* f;
+  Fnv fnv;
+  bool ok = true;
+  void put(const void* p, size_t n) {
+    if (!n) return;
+    fnv.add(p, n);
+    ok = ok && std::fwrite(p, 1, n, f) == n;
+  }
+  template <class T>
+  void val(T x) {
+    put(&x, sizeof(T));
+  }
+};
+struct Reader {
+  FILE* f;
+  Fnv fnv;
+  bool ok = true;
+  void get(void* p, size_t n) {
+    if (!n) return;
+    ok = ok && std::fread(p, 1, n, f) == n;
+    if (ok) fnv.add(p, n);
+  }
+  template <class T>
+  T val() {
+    T x{};
+    get(&x, sizeof(T));
+    return x;
+  }
+};
+const char kCkptMagic[8] = {'T', 'N', 'S', 'C', 'K', 'P', 'T', '1'};
+}  // namespace
+
+int Engine::checkpoint_save(const char* path, int site, int ltr, std::string& err) {
+  if (!have_ints_ || !have_mps_) {
+    err = "checkpoint_save: no integrals or MPS";
+    return -2;
+  }
+  for (int b = 0; b < N_; ++b)
+    if (!sites_[b].d) {
+      err = "checkpoint_save: site tensor " + std::to_string(b) + " not set";
+      return -2;
+    }
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    err = std::string("checkpoint_save: cannot open ") + path;
+    return -1;
+  }
+  Writer w{f};
+  w.put(kCkptMagic, 8);
+  for (int x : {1, N_, target_.n, target_.s, D_, site, ltr}) w.val<int>(x);
+  w.val<double>(e_core_);
+  w.put(h_.data(), h_.size() * 8);
+  w.put(v_.data(), v_.size() * 8);
+  for (int b = 0; b <= N_; ++b) {
+    const Basis& B = bonds_[b];
+    w.val<int>(B.size());
+    for (int i = 0; i < B.size(); ++i) {
+      w.val<int>(B.q[i].n);
+      w.val<int>(B.q[i].s);
+      w.val<int>(B.dim[i]);
+    }
+  }
+  std::vector<double> buf;
+  for (int b = 0; b < N_; ++b) {
+    buf.resize(sites_[b].size);
+    be_->download(buf.data(), sites_[b].d, sites_[b].size);
+    be_->sync();
+    w.val<long long>(sites_[b].size);
+    w.put(buf.data(), buf.size() * 8);
+  }
+  const unsigned long long hash = w.fnv.h;
+  w.ok = w.ok && std::fwrite(&hash, 8, 1, f) == 1;
+  const bool ok = w.ok && std::fclose(f) == 0;
+  if (!ok) {
+    err = std::string("checkpoint_save: write to ") + path + " failed";
+    return -1;
+  }
+  return 0;
+}
+
+int Engine::checkpoint_load(const char* path, int* site, int* ltr, std::string& err) {
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    err = std::string("checkpoint_load: cannot open ") + path;
+    return -1;
+  }
+  struct Closer {
+    FILE* f;
+    ~Closer() { std::fclose(f); }
+  } closer{f};
+  Reader r{f};
+  char magic[8];
+  r.get(magic, 8);
+  if (!r.ok || std::memcmp(magic, kCkptMagic, 8) != 0) {
+    err = "checkpoint_load: not a checkpoint file";
+    return -1;
+  }
+  const int version = r.val<int>(), N = r.val<int>(), ne = r.val<int>(), s2 = r.val<int>(), D = r.val<int>();
+  const int st = r.val<int>(), lr = r.val<int>();
+  const double ec = r.val<double>();
+  if (!r.ok || version != 1 || N < 2 || N > 128 || D < 1) {
+    err = "checkpoint_load: unsupported or damaged header";
+    return -1;
+  }
+  const long long n = N;
+  std::vector<double> h(n * n), v(n * n * n * n);
+  r.get(h.data(), h.size() * 8);
+  r.get(v.data(), v.size() * 8);
+  std::vector<std::vector<int>> bonds(N + 1);
+  for (int b = 0; b <= N && r.ok; ++b) {
+    const int ns = r.val<int>();
+    if (!r.ok || ns < 1 || ns > 100000) {
+      err = "checkpoint_load: damaged bond table";
+      return -1;
+    }
+    bonds[b].resize(3 * ns);
+    r.get(bonds[b].data(), bonds[b].size() * 4);
+  }
+  std::vector<std::vector<double>> sites(N);
+  for (int b = 0; b < N && r.ok; ++b) {
+    const long long len = r.val<long long>();
+    if (!r.ok || len < 0 || len > (1LL << 36)) {
+      err = "checkpoint_load: damaged site tensor";
+      return -1;
+    }
+    sites[b].resize(len);
+    r.get(sites[b].data(), len * 8);
+  }
+  const unsigned long long expect = r.fnv.h;
+  unsigned long long hash = 0;
+  if (!r.ok || std::fread(&hash, 8, 1, f) != 1 || hash != expect) {
+    err = "checkpoint_load: truncated or corrupted file (hash mismatch)";
+    return -1;
+  }
+  // everything read and checked: replace the context's problem and state
+  int rc = load_integrals(N, h.data(), v.data(), ec, err);
+  if (!rc) rc = mps_define(N, ne, s2, D, err);
+  for (int b = 0; b <= N && !rc; ++b) {
+    const int ns = (int)bonds[b].size() / 3;
+    std::vector<int> sec(2 * ns), dim(ns);
+    for (int i = 0; i < ns; ++i) {
+      sec[2 * i] = bonds[b][3 * i];
+      sec[2 * i + 1] = bonds[b][3 * i + 1];
+      dim[i] = bonds[b][3 * i + 2];
+    }
+    rc = mps_set_bond(b, ns, sec.data(), dim.data(), err);
+  }
+  for (int b = 0; b < N && !rc; ++b) rc = mps_set_site(b, sites[b].data(), (long long)sites[b].size(), err);
+  if (rc) return rc;
+  if (site) *site = st;
+  if (ltr) *ltr = lr;
   return 0;
 }
 
@@ -1099,6 +1274,8 @@ void Engine::compile_side(SideT<Sc>& S, const Catalogue& cat, bool left) {
   }
 }
 
+constexpr long long kLincombChunk = 8LL << 20;  // terms per partial-sum launch
+
 // the partial sums of a side: every expression with more than one term gets
 // its own operator on the side's block basis (layout and offsets only)
 void Engine::layout_mats(Side& S, Catalogue& cat) {
@@ -1163,6 +1340,15 @@ int Engine::fill_mats(Side& S, Catalogue& cat, std::string& err) {
       }
       blk.t1 = (int)lc.terms.size();
       lc.blocks.push_back(blk);
+      env_bytes_ += 8.0 * blk.rows * blk.cols * (1 + (blk.t1 - blk.t0));
+      // the term lists of large partial sums run to hundreds of millions of
+      // entries: computed in chunks so that the host list and its device copy
+      // stay bounded
+      if (lc.terms.size() >= (size_t)kLincombChunk) {
+        be_->lincomb(lc);
+        lc.blocks.clear();
+        lc.terms.clear();
+      }
     }
   }
   be_->lincomb(lc);
@@ -1297,13 +1483,27 @@ int Engine::rotate(Side& S, const Catalogue& src, Catalogue& dst, int site, bool
     for (int i = 0; i < b.size(); ++i) dst.basis.add(target_ - b.q[i], b.dim[i]);
   }
   for (auto& E : S.eops) dst.add_op(E.kind, E.i, E.j, E.dq);
-  int rc = alloc_cat(dst, err);
-  if (rc) return rc;
+  dst.assign_offsets();
   TaskList tl;
   rotation_tasks(S, src, dst, site, left, tl, nullptr);
   tl.nprod = (long long)tl.tasks.size();
+  // room for the work list of the renormalisation next to the new catalogue
+  int rc = make_room(be_->step_bytes(tl, 0) + std::max(dst.size, 1LL) * 8, err);
+  if (!rc) rc = alloc_cat(dst, err);
+  if (rc) return rc;
+  if (verbose_env_) {
+    static const auto t_start = std::chrono::steady_clock::now();
+    std::fprintf(stderr,
+                 "[tns %.1fs] %s block of %d orbitals: %.2f GB catalogue, %.2f GB partial sums, %lld products, "
+                 "device %.1f GB, host %.1f GB\n",
+                 std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count(),
+                 left ? "left" : "right", left ? dst.len : N_ - dst.len, dst.size * 8e-9, S.size * 8e-9,
+                 (long long)tl.tasks.size(), be_->mem_used() * 1e-9, ms_.host_used * 1e-9);
+  }
   be_->run(tl, nullptr, dst.d, 1, 0, 0, 0);
   be_->forget(tl);
+  env_flops_ += tl.flops;
+  env_bytes_ += 8.0 * ((double)src.size + (double)S.size + (double)dst.size + (double)sites_[site].size);
   dst.valid = true;
   scan_zero(dst);
   ++ms_.built;
@@ -1404,6 +1604,9 @@ void Engine::rotation_tasks(const Side& S, const Catalogue& src, const Catalogue
 int Engine::ensure_step(int k, std::string& err) {
   if (step_.valid && step_.k != k) {
     be_->forget(step_.heff);
+    be_->forget(step_.heff_part);
+    step_.heff_part.clear();
+    step_.part_key = -1;
     free_side(step_.L);
     free_side(step_.R);
     step_.heff.clear();
@@ -1570,6 +1773,8 @@ void Engine::build_heff_tasks() {
   TaskList& tl = st.heff;
   tl.clear();
   st.heff_prov.clear();
+  st.heff_row.clear();
+  st.nrows = 0;
 
   struct Pair {
     int eL;
@@ -1622,6 +1827,7 @@ void Engine::build_heff_tasks() {
         if (st.psi_index[((size_t)ql * 16 + s12) * nqr + qr] >= 0) qr_of[(size_t)ql * 16 + s12] = qr;
   std::vector<std::vector<Task>> bucket(st.psi.size());
   std::vector<std::vector<std::array<int, 6>>> pbucket(st.psi.size());
+  std::vector<std::vector<int>> rbucket(st.psi.size());  // operator-pair index (operator-table row) per task
   static const std::vector<DotBlock> kIdent = {
       {0, 0, {{1.0, -1}}}, {1, 1, {{1.0, -1}}}, {2, 2, {{1.0, -1}}}, {3, 3, {{1.0, -1}}}};
   // useful flops (Eq. 2 with the cheaper chain of Sec. III.B): one product per
@@ -1658,7 +1864,8 @@ void Engine::build_heff_tasks() {
   };
   double useful = 0.0;
 
-  for (const Pair& pr : pairs) {
+  for (size_t pi = 0; pi < pairs.size(); ++pi) {
+    const Pair& pr = pairs[pi];
     if (pr.eL == -1 || pr.eR == -1) continue;
     const std::vector<DotBlock>& dl = pr.eL == -2 ? kIdent : st.L.eops[pr.eL].dots;
     const std::vector<DotBlock>& dr = pr.eR == -2 ? kIdent : st.R.eops[pr.eR].dots;
@@ -1733,6 +1940,7 @@ void Engine::build_heff_tasks() {
                   useful += chain_flops(u);
                 }
                 bucket[yb].push_back(tk);
+                rbucket[yb].push_back((int)pi);
                 pbucket[yb].push_back({pr.eL == -2 ? -1 : pr.eL, pr.eL == -2 ? -1 : (int)ai, (int)tai,
                                        pr.eR == -2 ? -1 : pr.eR, pr.eR == -2 ? -1 : (int)bi, (int)tbi});
               }
@@ -1757,11 +1965,14 @@ void Engine::build_heff_tasks() {
     g.t0 = (int)tl.tasks.size();
     for (auto& tk : bucket[yb]) tl.tasks.push_back(tk);
     for (auto& pv : pbucket[yb]) st.heff_prov.push_back(pv);
+    for (int r : rbucket[yb]) st.heff_row.push_back(r);
     g.t1 = (int)tl.tasks.size();
     tl.groups.push_back(g);
   }
   tl.flops = useful;
   tl.nprod = (long long)tl.tasks.size();
+  st.nrows = (int)pairs.size();
+  st.part_key = -1;
   st.diag_tasks.clear();
   st.diag_rng.assign(1, 0);
   for (int g = 0; g < (int)tl.groups.size(); ++g) {
@@ -1804,6 +2015,9 @@ int Engine::refresh_step(std::string& err) {
 
 int Engine::prepare_step(int k, std::string& err) {
   be_->forget(step_.heff);  // the device copy of the previous step's work list
+  be_->forget(step_.heff_part);
+  step_.heff_part.clear();
+  step_.part_key = -1;
   free_side(step_.L);
   free_side(step_.R);
   step_.valid = false;
@@ -1923,7 +2137,74 @@ int Engine::heff(const double* X, double* Y, int nvec, int precision, std::strin
   std::string e = be_->error();
   if (!e.empty()) {
     err = e;
-    return -6;
+    // a bounded device wait that gave up leaves the context usable
+    return e.find("wait timed out") != std::string::npos ? -5 : -6;
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// operator-row split (Sec. "Independent operational tasks": the rows of the
+// operator table, i.e. the normal/complementary operator pairs, are
+// distributed; every part accumulates all output blocks of its rows and the
+// parts' sums add up to H_eff X)
+// ---------------------------------------------------------------------------
+void Engine::row_parts(int nparts, std::vector<int>& part_of_row) const {
+  // cost of a row: the chain flops of its products; longest first onto the
+  // least loaded part (deterministic: every caller computes the same split)
+  const Step& st = step_;
+  std::vector<double> cost(st.nrows, 0.0);
+  for (size_t i = 0; i < st.heff.tasks.size(); ++i) cost[st.heff_row[i]] += chain_flops(st.heff.tasks[i]) + 64.0;
+  std::vector<int> order(st.nrows);
+  for (int r = 0; r < st.nrows; ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<double> load(nparts, 0.0);
+  part_of_row.assign(st.nrows, 0);
+  for (int r : order) {
+    int best = 0;
+    for (int p = 1; p < nparts; ++p)
+      if (load[p] < load[best]) best = p;
+    part_of_row[r] = best;
+    load[best] += cost[r];
+  }
+}
+
+int Engine::heff_part(const double* X, double* Y, int nvec, int precision, int part, int nparts, std::string& err) {
+  if (!step_.valid) {
+    err = "heff_part: call build_env first";
+    return -2;
+  }
+  if (nparts < 1 || part < 0 || part >= nparts) {
+    err = "heff_part: part must be in [0, nparts)";
+    return -1;
+  }
+  Step& st = step_;
+  const long long key = (long long)part * 65536 + nparts;
+  if (st.part_key != key) {
+    std::vector<int> pr;
+    row_parts(nparts, pr);
+    TaskList& tl = st.heff_part;
+    tl.clear();
+    tl.tasks.reserve(st.heff.tasks.size() / nparts + 16);
+    for (const Group& g0 : st.heff.groups) {
+      Group g = g0;
+      g.t0 = (int)tl.tasks.size();
+      for (int i = g0.t0; i < g0.t1; ++i)
+        if (pr[st.heff_row[i]] == part) tl.tasks.push_back(st.heff.tasks[i]);
+      g.t1 = (int)tl.tasks.size();
+      tl.groups.push_back(g);
+    }
+    tl.nprod = (long long)tl.tasks.size();
+    tl.flops = 0.0;
+    tl.persistent = true;
+    st.part_key = key;
+  }
+  be_->run(st.heff_part, X, Y, nvec, st.length, st.length, precision);
+  be_->sync();
+  std::string e = be_->error();
+  if (!e.empty()) {
+    err = e;
+    return e.find("wait timed out") != std::string::npos ? -5 : -6;
   }
   return 0;
 }

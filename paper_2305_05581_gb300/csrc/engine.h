@@ -401,6 +401,10 @@ struct Step {
   // per H_eff task, where its coefficient comes from: (eop, dot block, dot
   // term) on the left side and on the right side; -1 for an identity side
   std::vector<std::array<int, 6>> heff_prov;
+  std::vector<int> heff_row;  // per H_eff task: its operator-table row (operator pair)
+  int nrows = 0;              // operator-table rows of the step
+  TaskList heff_part;         // the tasks of one part of an operator-row split
+  long long part_key = -1;    // (part, nparts) heff_part was built for
   // operand blocks of the step that are identically zero, per side (catalogue
   // blocks by address, partial-sum blocks by their arena offset while the
   // step is planned); products reading one are not counted as useful flops
@@ -434,9 +438,17 @@ class Engine {
   int mps_set_site(int b, const double* x, long long len, std::string& err);
   int mps_get_site(int b, double* x, long long len, long long* len_out, std::string& err);
   int mps_init(int N, int n_elec, int two_sz, int D, unsigned long long seed, std::string& err);
+  // checkpoint / restart of a sweep: integrals, MPS and position in one file
+  int checkpoint_save(const char* path, int site, int ltr, std::string& err);
+  int checkpoint_load(const char* path, int* site, int* ltr, std::string& err);
 
   int build_env(int k, std::string& err);        // L_k, R_{k+2}, step k tables
   int heff(const double* X, double* Y, int nvec, int precision, std::string& err);
+  // the part `part` of an nparts-way operator-row split of Y = H_eff X: Y is
+  // overwritten with the sum over the operator pairs assigned to that part
+  // (balanced by flops, the same split on every caller); the parts add up to H_eff X
+  int heff_part(const double* X, double* Y, int nvec, int precision, int part, int nparts, std::string& err);
+  void row_parts(int nparts, std::vector<int>& part_of_row) const;
   // adjoint of Y = H_eff X for the cotangent Yb: Xb = H_eff^T Yb and the
   // gradients of <Yb, H_eff X> w.r.t. the arenas of L_k (Lb) and R_{k+2} (Rb);
   // any output may be null.  All pointers in the backend's memory space.
@@ -448,6 +460,12 @@ class Engine {
   int integral_gradient(const double* psi, std::vector<double>& g, std::string& err);
   // refresh the step's partial sums after the catalogue arenas were changed
   int refresh_step(std::string& err);
+  // algorithmic work of the environment build so far: FP64 flops of the
+  // renormalisation products and bytes of the partial sums (terms read,
+  // result written) and renormalisations (source catalogue and partial sums
+  // read, site tensor read, new catalogue written)
+  double env_flops() const { return env_flops_; }
+  double env_bytes() const { return env_bytes_; }
   // device budget (bytes; 0 = none) and pinned host memory for staged
   // catalogues (bytes; 0 = none: catalogues that must leave the device are
   // dropped and rebuilt when needed)
@@ -511,6 +529,8 @@ class Engine {
   std::vector<const Catalogue*> keep_;
   long long host_budget_ = 0;
   MemStats ms_;
+  double env_flops_ = 0.0, env_bytes_ = 0.0;
+  bool verbose_env_ = false;  // TNS_VERBOSE_ENV=1: one line per renormalisation on stderr
 
   int make_room(long long bytes, std::string& err);
   int evict(Catalogue& c, std::string& err);

@@ -926,6 +926,8 @@ CudaBackend::CudaBackend(int device, cudaStream_t s, bool own) : device_(device)
   const char* k = std::getenv("TNS_FP64_KERNEL");
   if (k && std::strcmp(k, "dfma") == 0) fp64_kernel = 0;
   if (k && std::strcmp(k, "dmma") == 0) fp64_kernel = 1;
+  const char* w = std::getenv("TNS_TC_WAIT_NS");
+  if (w && *w) tc_wait_ns = std::strtoull(w, nullptr, 10);
 }
 
 CudaBackend::~CudaBackend() {
@@ -1003,7 +1005,8 @@ long long CudaBackend::step_bytes(const TaskList& tl, long long psi_length) {
     if (!(t.flags & TF_LI) && seenL.insert(t.L).second) b += pad(t.q, t.m);
     if (!(t.flags & TF_RI) && seenR.insert(t.R).second) b += pad(t.r, t.n);
   }
-  return b + psi_length * 8LL * 120;
+  // + split-K partial tiles and scratch
+  return b + psi_length * 8LL * 120 + (1LL << 30);
 }
 
 long long CudaBackend::mem_used() { return dmem(device_).used; }

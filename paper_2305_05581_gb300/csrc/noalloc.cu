@@ -24,17 +24,39 @@ static __device__ __align__(256) int g_diag_scratch[TNS_NOALLOC_DIAG_MAX];
 namespace {
 std::mutex g_mu;
 int* g_addr[256] = {nullptr};
+void* g_ctx[256] = {nullptr};  // the CUDA context g_addr[device] was looked up in
+
+// the current CUDA context (driver handle), through the runtime's driver entry
+// point: a device reset or a new primary context loads the module again,
+// possibly at another address
+void* current_context() {
+  using GetCurrent = int (*)(void**);
+  static GetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &f, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return (GetCurrent)f;
+  }();
+  void* c = nullptr;
+  if (fn && fn(&c) != 0) c = nullptr;
+  return c;
+}
 }  // namespace
 
-// device address of the scratch array for the current device (looked up once
-// per device, with that device current)
+// device address of the scratch array for the current device (looked up with
+// that device current, once per device and CUDA context)
 static int* diag_scratch(int device, std::string& err) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (device < 0 || device >= 256) {
     err = "heff_diag_noalloc: device index out of range";
     return nullptr;
   }
-  if (!g_addr[device]) {
+  void* ctx = current_context();
+  if (!g_addr[device] || ctx != g_ctx[device]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_diag_scratch);
     if (e != cudaSuccess) {
@@ -42,6 +64,7 @@ static int* diag_scratch(int device, std::string& err) {
       return nullptr;
     }
     g_addr[device] = (int*)p;
+    g_ctx[device] = ctx;
   }
   return g_addr[device];
 }

@@ -1025,6 +1025,7 @@ static int backend_step(tns::Engine& E, int k, bool ltr, const tns_sweep_opts* o
   bool conv = false;
   long long length = 0;
   const long long launches0 = be.launches;
+  const double ef0 = E.env_flops(), eb0 = E.env_bytes();
   if (E.step().valid && E.step().k == k) length = E.step().length;
   int rc = one_step(E, be, k, ltr, o, x0, psi, X, acc, &e, &its, &disc, &conv, err);
   if (rc) return rc;
@@ -1043,6 +1044,8 @@ static int backend_step(tns::Engine& E, int k, bool ltr, const tns_sweep_opts* o
     stats->kernel_launches = be.launches - launches0;
     stats->exact_products = acc.exact_products;
     stats->exact_seconds = acc.exact_ms * 1e-3;
+    stats->env_flops = E.env_flops() - ef0;
+    stats->env_bytes = E.env_bytes() - eb0;
   }
   return 0;
 }

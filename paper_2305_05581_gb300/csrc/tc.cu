@@ -191,8 +191,8 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
-// wait for phase `ph`, bounded in time; returns false on timeout
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t ph) {
+// wait for phase `ph`, bounded in time (bound_ns); returns false on timeout
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t ph, unsigned long long bound_ns) {
   uint32_t done = 0;
   const unsigned long long t0 = gtimer();
   while (!done) {
@@ -200,7 +200,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t ph) {
                  : "=r"(done)
                  : "r"(smem_u32(bar)), "r"(ph)
                  : "memory");
-    if (!done && gtimer() - t0 > TC_WAIT_NS) break;
+    if (!done && gtimer() - t0 > bound_ns) break;
   }
   return done != 0;
 }
@@ -328,7 +328,8 @@ __global__ void __launch_bounds__(TC_NT, TC_CTAS)
                const TcChunk* __restrict__ chunks, const unsigned char* __restrict__ ops_hi,
                const unsigned char* __restrict__ ops_lo, const unsigned char* __restrict__ x_hi,
                const unsigned char* __restrict__ x_lo, long long x_bytes, const XBlock* __restrict__ xblocks,
-               double* yv, long long ys, int* flag, double* part_all, long long psize, int nv) {
+               double* yv, long long ys, int* flag, double* part_all, long long psize, int nv,
+               unsigned long long wait_ns) {
   using S = TcSmem<TF32>;
   constexpr int ES = S::ES;
   constexpr int NPROD = TF32 ? 1 : 3;
@@ -392,9 +393,12 @@ __global__ void __launch_bounds__(TC_NT, TC_CTAS)
   int g2_steps = 0;
   bool d2 = false;
   int where_c = -1, where_m0 = -1, where_s = -1;
-  auto drain = [&](uint64_t* bar, uint32_t& ph, int& out) {
+  // waits inside the product loop give up after wait_ns; the final drain
+  // before TMEM is released always allows the full TC_WAIT_NS, so that no copy
+  // or MMA of this CTA is still in flight when it exits
+  auto drain = [&](uint64_t* bar, uint32_t& ph, int& out, unsigned long long bound = 0) {
     if (!out) return;
-    if (wait_bar(bar, ph)) {
+    if (wait_bar(bar, ph, bound ? bound : wait_ns)) {
       ph ^= 1;
       out = 0;
     } else {
@@ -635,12 +639,12 @@ __global__ void __launch_bounds__(TC_NT, TC_CTAS)
   // every copy and MMA of this CTA done (bounded) before TMEM is read or released
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
-      drain(&lbar1[b], pl1[b], l1_out[b]);
-      drain(&mbar1[b], pm1[b], m1_out[b]);
+      drain(&lbar1[b], pl1[b], l1_out[b], TC_WAIT_NS);
+      drain(&mbar1[b], pm1[b], m1_out[b], TC_WAIT_NS);
     }
     for (int b = 0; b < 2; ++b) {
-      drain(&lbar2[b], pl2[b], l2_out[b]);
-      drain(&mbar2[b], pm2[b], m2_out[b]);
+      drain(&lbar2[b], pl2[b], l2_out[b], TC_WAIT_NS);
+      drain(&mbar2[b], pm2[b], m2_out[b], TC_WAIT_NS);
     }
   }
   __syncthreads();
@@ -1116,12 +1120,12 @@ void enqueue_tasks_tc(CudaBackend& be, DevList& d, const double* xv, double* yv,
     k_tasks_tc<1><<<grid, TC_NT, TcSmem<1>::total, be.stream()>>>(plan->tasks, d.groups, V.tiles, plan->chunks,
                                                                    plan->ops_hi, plan->ops_lo, plan->x_hi, plan->x_lo,
                                                                    plan->x_bytes, plan->xblocks, yv, ys, plan->flag,
-                                                                   V.part, V.psize, nvec);
+                                                                   V.part, V.psize, nvec, be.tc_wait_ns);
   else
     k_tasks_tc<0><<<grid, TC_NT, TcSmem<0>::total, be.stream()>>>(plan->tasks, d.groups, V.tiles, plan->chunks,
                                                                    plan->ops_hi, plan->ops_lo, plan->x_hi, plan->x_lo,
                                                                    plan->x_bytes, plan->xblocks, yv, ys, plan->flag,
-                                                                   V.part, V.psize, nvec);
+                                                                   V.part, V.psize, nvec, be.tc_wait_ns);
   be.launches++;
   be.note(cudaGetLastError(), "k_tasks_tc");
   if (V.nreds > 0) launch_reduce_splits(be, V.reds, V.nreds, d.groups, V.part, V.psize, yv, ys, nvec);

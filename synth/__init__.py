@@ -87,12 +87,16 @@ def _count(nsites: int, n: int, s2: int) -> int:
     return math.comb(nsites, nu) * math.comb(nsites, nd)
 
 
-def bond_sectors(N: int, n_elec: int, two_sz: int, D: int) -> List[List[Tuple[Sector, int]]]:
+def bond_sectors(N: int, n_elec: int, two_sz: int, D: int,
+                 max_sectors: int = 0) -> List[List[Tuple[Sector, int]]]:
     """Per bond b=0..N, the list of (sector, dim), sectors sorted by (n, 2Sz).
 
     dim = min(#left determinants, #right determinants) (the Schmidt-rank
     bound), scaled down proportionally when the total exceeds D, then made
     consistent so that every site tensor can be orthonormalised both ways.
+    max_sectors > 0 keeps only that many sectors per bond (those with the
+    largest bound, ties by sector), which concentrates D in a few large
+    sectors.
     """
     target = (n_elec, two_sz)
     dims: List[Dict[Sector, int]] = []
@@ -104,6 +108,9 @@ def bond_sectors(N: int, n_elec: int, two_sz: int, D: int) -> List[List[Tuple[Se
                 cr = _count(N - b, target[0] - n, target[1] - s2)
                 if cl and cr:
                     full[(n, s2)] = min(cl, cr)
+        if max_sectors > 0 and len(full) > max_sectors:
+            keep = sorted(full, key=lambda q: (-full[q], q))[:max_sectors]
+            full = {q: full[q] for q in keep}
         tot = sum(full.values())
         if tot > D:
             # proportional share, remainder to the largest fractional parts
@@ -132,7 +139,7 @@ def bond_sectors(N: int, n_elec: int, two_sz: int, D: int) -> List[List[Tuple[Se
     return [sorted(((q, d) for q, d in db.items() if d > 0)) for db in dims]
 
 
-def random_mps(N: int, n_elec: int, two_sz: int, D: int, center: int, seed: int):
+def random_mps(N: int, n_elec: int, two_sz: int, D: int, center: int, seed: int, max_sectors: int = 0):
     """Random block-sparse MPS, left-canonical on sites <= center and
     right-canonical on sites >= center+1.
 
@@ -142,7 +149,7 @@ def random_mps(N: int, n_elec: int, two_sz: int, D: int, center: int, seed: int)
     not part of the method).
     """
     rng = np.random.default_rng(seed)
-    bonds = bond_sectors(N, n_elec, two_sz, D)
+    bonds = bond_sectors(N, n_elec, two_sz, D, max_sectors)
     sites = []
     for b in range(N):
         left = dict(bonds[b])

@@ -17,8 +17,11 @@ from paper_2305_05581_gb300 import (Context, TNS_FP64, TNS_TF32, TNS_BF16X3,  # 
                                     blocks_to_vector, vector_to_blocks, DEFAULT_LIB)
 
 # error bounds of one H_eff*psi relative to its 2-norm: split-BF16 keeps ~16
-# significant bits per operand (hi + lo), TF32 11; both accumulate in FP32
-TOL = {TNS_BF16X3: 2e-4, TNS_TF32: 1e-2}
+# significant bits per operand (hi + lo), TF32 11 (unit roundoff 2^-11 = 4.9e-4
+# per rounding; measured 2.3e-4 at the 24-orbital middle bond); both
+# accumulate in FP32.  An operand rounded to bf16 (8 bits) instead of TF32
+# would give ~2e-3 and fail the TF32 bound.
+TOL = {TNS_BF16X3: 2e-4, TNS_TF32: 1e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -163,4 +166,6 @@ def test_block_davidson_step_matches_single_vector(prec):
         st = ctx.step(k, True, D, tol=1e-8, max_iter=600, precision=prec, block=block)
         assert st.converged
         out.append(st.energy)
-    assert abs(out[0] - out[1]) < 1e-9
+    # both runs stop at an FP64 residual <= 1e-8 (the operating tolerance); the
+    # eigenvalue error of each is then <= |r|^2 / gap, far below this bound
+    assert abs(out[0] - out[1]) < 1e-10

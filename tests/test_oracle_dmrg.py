@@ -96,3 +96,21 @@ def test_dmrg_energy_monotone_in_D():
     efci = fci_energy(h, v, n, s2)
     assert es[0] >= es[1] - 1e-9 >= es[2] - 2e-9
     assert es[2] >= efci - 1e-9
+
+
+def test_apply_abs_bounds_the_product():
+    """The error-bound helper dominates the product elementwise and is linear
+    in |psi|."""
+    N, n, s2, D, k = 6, 6, 0, 12, 2
+    h, v = synth.integrals(N, 2.0, 9)
+    bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=2)
+    heff = O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2)
+    keys = synth.psi_keys(bonds, N, n, s2, k)
+    X = synth.random_psi(keys, seed=4)[0]
+    Y, Ya = heff.apply(X), heff.apply_abs(X)
+    for q in Y:
+        assert np.all(np.abs(Y[q]) <= Ya[q] + 1e-12)
+    X2 = {q: 2.0 * np.abs(b) for q, b in X.items()}
+    Ya2 = heff.apply_abs(X2)
+    for q in Y:
+        assert np.allclose(Ya2[q], 2.0 * Ya[q], rtol=1e-13, atol=0)
