@@ -62,10 +62,12 @@ def parse():
                    help="--case heff: a random MPS, or the state after one sweep from the initial MPS")
     p.add_argument("--clocks-dir", default=None,
                    help="folder for the nvidia-smi samples of the timed region (default: the temp folder)")
-    p.add_argument("--setup", default=None, choices=["sweep", "init"],
+    p.add_argument("--setup", default=None, choices=["sweep", "random", "init"],
                    help="state of the timed steps: 'sweep' = one full warm-up sweep from the initial MPS "
-                        "(default up to 40 orbitals), 'init' = the initial MPS itself, environments built "
-                        "straight to the window (default for larger systems)")
+                        "(default up to 40 orbitals); 'random' = a seeded random MPS with bond dimension D at "
+                        "every bond (synth.random_mps, canonical around the window; default for larger systems); "
+                        "'init' = the initial MPS of tns_mps_init (0/1 isometries: its two-site states have low "
+                        "Schmidt rank, so the bond dimension collapses in the first steps)")
     p.add_argument("--block", type=int, default=1, help="Davidson block size (vectors per batched product)")
     p.add_argument("--device-budget-gb", type=float, default=None,
                    help="device memory budget of the engine (default: device size - 24 GB for n76, none otherwise)")
@@ -258,8 +260,11 @@ def combine_ranks(dist, elapsed, flops, device):
 def workload_config(args, c, setup):
     N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
     mid = N // 2 - 1
-    state = ("one warm-up sweep from the initial MPS" if setup == "sweep" else
-             "the initial MPS (all reachable sectors, 0/1 isometries), environments built straight to the window")
+    state = {"sweep": "one warm-up sweep from the initial MPS",
+             "random": "a seeded random MPS (synth.random_mps, bond dimension D at every bond, canonical around "
+                       "the window), environments built straight to the window",
+             "init": "the initial MPS (all reachable sectors, 0/1 isometries), environments built straight to the "
+                     "window"}[setup]
     return {"workload": f"{args.workload}: N={N} n_elec={n} 2Sz={s2} D={D} lambda={c['lam']} seed={c['seed']}; "
                         f"{state}; two-site steps cycling over sites {mid - 2}..{mid + 2} "
                         f"(left to right {mid - 2}..{mid + 1}, right to left {mid + 2}..{mid - 1})",
@@ -345,7 +350,7 @@ def main():
     prec = P[args.precision]
     c = synth.WORKLOADS[args.workload]
     N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
-    setup = args.setup or ("sweep" if N <= 40 else "init")
+    setup = args.setup or ("sweep" if N <= 40 else "random")
     peaks = measured_peaks(torch)
     peak, bound, peak_source = peak_for(args, peaks)
     h, v = synth.integrals(N, c["lam"], c["seed"])
@@ -357,8 +362,12 @@ def main():
     host_gb = args.host_gb if args.host_gb is not None else (120 if big else 0)
     ctx.set_memory_budget(int(budget_gb * 2 ** 30), int(host_gb * 2 ** 30))
     ctx.load_integrals(h, v)
-    ctx.mps_init(N, n, s2, D, seed=c["seed"])
     cycle = window_cycle(N)
+    if setup == "random":
+        bonds, sites = synth.random_mps(N, n, s2, D, center=cycle[0][0], seed=c["seed"])
+        ctx.mps_import(N, n, s2, D, bonds, sites)
+    else:
+        ctx.mps_init(N, n, s2, D, seed=c["seed"])
     step = lambda k, ltr, **kw: ctx.step(k, ltr, D, tol=args.tol, max_iter=60, precision=prec,
                                           block=args.block, **kw)
     # untimed set-up: the state of the timed steps, positioned at the window

@@ -1604,8 +1604,10 @@ void Engine::rotation_tasks(const Side& S, const Catalogue& src, const Catalogue
 int Engine::ensure_step(int k, std::string& err) {
   if (step_.valid && step_.k != k) {
     be_->forget(step_.heff);
+    be_->forget(step_.heff_full);
     be_->forget(step_.heff_part);
     step_.heff_part.clear();
+    step_.heff_full.clear();
     step_.part_key = -1;
     free_side(step_.L);
     free_side(step_.R);
@@ -1828,6 +1830,7 @@ void Engine::build_heff_tasks() {
   std::vector<std::vector<Task>> bucket(st.psi.size());
   std::vector<std::vector<std::array<int, 6>>> pbucket(st.psi.size());
   std::vector<std::vector<int>> rbucket(st.psi.size());  // operator-pair index (operator-table row) per task
+  std::vector<std::vector<char>> zbucket(st.psi.size());  // 0: the task reads an identically zero block
   static const std::vector<DotBlock> kIdent = {
       {0, 0, {{1.0, -1}}}, {1, 1, {{1.0, -1}}}, {2, 2, {{1.0, -1}}}, {3, 3, {{1.0, -1}}}};
   // useful flops (Eq. 2 with the cheaper chain of Sec. III.B): one product per
@@ -1940,6 +1943,7 @@ void Engine::build_heff_tasks() {
                   useful += chain_flops(u);
                 }
                 bucket[yb].push_back(tk);
+                zbucket[yb].push_back(nz ? 1 : 0);
                 rbucket[yb].push_back((int)pi);
                 pbucket[yb].push_back({pr.eL == -2 ? -1 : pr.eL, pr.eL == -2 ? -1 : (int)ai, (int)tai,
                                        pr.eR == -2 ? -1 : pr.eR, pr.eR == -2 ? -1 : (int)bi, (int)tbi});
@@ -1949,10 +1953,21 @@ void Engine::build_heff_tasks() {
       }
     }
   }
-  size_t ntot = 0;
-  for (const auto& b : bucket) ntot += b.size();
-  tl.tasks.reserve(ntot);
+  // two lists over the same output blocks: every product (the adjoint and the
+  // integral gradients differentiate with respect to every operator entry,
+  // zero blocks included), and the products whose operator blocks are not
+  // identically zero (the forward product: the others add exact zeros)
+  TaskList& full = st.heff_full;
+  full.clear();
+  size_t ntot = 0, nnz = 0;
+  for (size_t yb = 0; yb < bucket.size(); ++yb) {
+    ntot += bucket[yb].size();
+    for (char z : zbucket[yb]) nnz += z;
+  }
+  full.tasks.reserve(ntot);
+  tl.tasks.reserve(nnz);
   st.heff_prov.reserve(ntot);
+  st.heff_row.reserve(nnz);
   for (size_t yb = 0; yb < st.psi.size(); ++yb) {
     const PsiBlock& Y = st.psi[yb];
     Group g;
@@ -1962,13 +1977,24 @@ void Engine::build_heff_tasks() {
     g.row0 = g.col0 = 0;
     g.nrows = Y.m;
     g.ncols = Y.n;
+    Group gf = g;
     g.t0 = (int)tl.tasks.size();
-    for (auto& tk : bucket[yb]) tl.tasks.push_back(tk);
+    gf.t0 = (int)full.tasks.size();
+    for (size_t i = 0; i < bucket[yb].size(); ++i) {
+      full.tasks.push_back(bucket[yb][i]);
+      if (zbucket[yb][i]) {
+        tl.tasks.push_back(bucket[yb][i]);
+        st.heff_row.push_back(rbucket[yb][i]);
+      }
+    }
     for (auto& pv : pbucket[yb]) st.heff_prov.push_back(pv);
-    for (int r : rbucket[yb]) st.heff_row.push_back(r);
     g.t1 = (int)tl.tasks.size();
+    gf.t1 = (int)full.tasks.size();
     tl.groups.push_back(g);
+    full.groups.push_back(gf);
   }
+  full.flops = useful;
+  full.nprod = (long long)full.tasks.size();
   tl.flops = useful;
   tl.nprod = (long long)tl.tasks.size();
   st.nrows = (int)pairs.size();
@@ -2015,6 +2041,7 @@ int Engine::refresh_step(std::string& err) {
 
 int Engine::prepare_step(int k, std::string& err) {
   be_->forget(step_.heff);  // the device copy of the previous step's work list
+  be_->forget(step_.heff_full);
   be_->forget(step_.heff_part);
   step_.heff_part.clear();
   step_.part_key = -1;
@@ -2063,6 +2090,7 @@ int Engine::prepare_step(int k, std::string& err) {
             std::to_string((step_.L.size + step_.R.size) * 8) + ", work list, images and vectors " +
             std::to_string(need - (step_.L.size + step_.R.size) * 8) + "), above the limit " + std::to_string(lim);
       step_.heff.clear();
+      step_.heff_full.clear();
       return -3;
     }
   }
@@ -2070,19 +2098,22 @@ int Engine::prepare_step(int k, std::string& err) {
   if (rc) {
     err = "memory plan: " + err;
     step_.heff.clear();
+    step_.heff_full.clear();
     return rc;
   }
   rc = fill_mats(step_.L, Lc, err);
   if (!rc) rc = fill_mats(step_.R, Rc, err);
   if (rc) {
     step_.heff.clear();
+    step_.heff_full.clear();
     return rc;
   }
-  for (Task& t : step_.heff.tasks) {
-    if (t.flags & TF_LM) t.L = step_.L.d + (long long)(uintptr_t)t.L;
-    if (t.flags & TF_RM) t.R = step_.R.d + (long long)(uintptr_t)t.R;
-    t.flags &= ~(TF_LM | TF_RM);
-  }
+  for (TaskList* l : {&step_.heff, &step_.heff_full})
+    for (Task& t : l->tasks) {
+      if (t.flags & TF_LM) t.L = step_.L.d + (long long)(uintptr_t)t.L;
+      if (t.flags & TF_RM) t.R = step_.R.d + (long long)(uintptr_t)t.R;
+      t.flags &= ~(TF_LM | TF_RM);
+    }
   be_->sync();
   std::string e = be_->error();
   if (!e.empty()) {
@@ -2103,7 +2134,13 @@ int Engine::build_env(int k, std::string& err) {
     return -1;
   }
   int rc = ensure_step(k, err);
-  if (!rc) rc = prepare_step(k, err);
+  if (!rc) {
+    // the caller may have changed the two arenas (tns_env_arena): their zero
+    // blocks are found again before the work list is built
+    scan_zero(Lcat_[k]);
+    scan_zero(Rcat_[k + 2]);
+    rc = prepare_step(k, err);
+  }
   if (!rc) {
     std::string e = be_->error();
     if (!e.empty()) {
@@ -2253,7 +2290,7 @@ int Engine::heff_adjoint(const double* X, const double* Yb, double* Xb, double* 
   const int k = st.k;
   Catalogue& Lc = Lcat_[k];
   Catalogue& Rc = Rcat_[k + 2];
-  const TaskList& fw = st.heff;
+  const TaskList& fw = st.heff_full;
   const long long nL = Lc.size, nR = Rc.size, nML = st.L.size, nMR = st.R.size;
   // temporaries: direct gradients of catalogue blocks and of materialised blocks
   double* GL = Lb ? be_->alloc(std::max(nL, 1LL)) : nullptr;
@@ -2677,7 +2714,7 @@ int Engine::integral_gradient(const double* psi, std::vector<double>& g, std::st
   }
   // ---- H_eff*psi: coefficients and operand adjoints ----
   {
-    const TaskList& tl = st.heff;
+    const TaskList& tl = st.heff_full;
     const std::vector<double> v = values(tl, psi, Yb);
     for (size_t i = 0; i < tl.tasks.size(); ++i) {
       const auto& pv = st.heff_prov[i];
@@ -2704,8 +2741,8 @@ int Engine::integral_gradient(const double* psi, std::vector<double>& g, std::st
     if (st.L.size) sink.region(st.L.d, st.L.size, GmL);
     sink.region(Rk.d, Rk.size, GdR);
     if (st.R.size) sink.region(st.R.d, st.R.size, GmR);
-    for (const Group& gr : st.heff.groups)
-      for (int i = gr.t0; i < gr.t1; ++i) sink.adjoint(st.heff.tasks[i], psi, Yb + gr.yoff);
+    for (const Group& gr : st.heff_full.groups)
+      for (int i = gr.t0; i < gr.t1; ++i) sink.adjoint(st.heff_full.tasks[i], psi, Yb + gr.yoff);
     sink.flush(be_);
   }
   double* GL = galloc(Lk.size);

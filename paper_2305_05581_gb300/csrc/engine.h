@@ -397,11 +397,12 @@ struct Step {
   std::vector<int> psi_index;  // ((ql*4+s1)*4+s2)*nqr+qr -> block
   std::vector<long long> desc;
   long long length = 0;
-  TaskList heff;
+  TaskList heff;       // products whose operator blocks are not identically zero (the forward product)
+  TaskList heff_full;  // every product (adjoint and integral gradients; heff_prov is aligned with it)
   // per H_eff task, where its coefficient comes from: (eop, dot block, dot
   // term) on the left side and on the right side; -1 for an identity side
   std::vector<std::array<int, 6>> heff_prov;
-  std::vector<int> heff_row;  // per H_eff task: its operator-table row (operator pair)
+  std::vector<int> heff_row;  // per forward H_eff task: its operator-table row (operator pair)
   int nrows = 0;              // operator-table rows of the step
   TaskList heff_part;         // the tasks of one part of an operator-row split
   long long part_key = -1;    // (part, nparts) heff_part was built for
