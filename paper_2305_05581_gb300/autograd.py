@@ -51,3 +51,40 @@ class HeffFunction(torch.autograd.Function):
 
 def heff(x, larena, rarena, ctx, site):
     return HeffFunction.apply(x, larena, rarena, ctx, site)
+
+
+class IntegralEnergy(torch.autograd.Function):
+    """E(h, v) = <psi| H_eff(h, v) |psi> / <psi|psi> at one two-site step with
+    the MPS isometries fixed (the differentiation form's energy functional).
+
+    forward loads (h, v) into the context, builds the step's environment and
+    applies H_eff; backward returns dE/dh and dE/dv from tns_rdm (reverse mode
+    through H_eff*psi and the whole renormalisation chain of both blocks,
+    done natively by the library): dE/dh = gamma (symmetrised) and
+    dE/dv = Gamma / 2 averaged over the eight index permutations of (ij|kl),
+    the only part of dE/dv defined for integrals with that symmetry.  h and v
+    are CPU float64 tensors (copied into the library); psi is a CUDA tensor
+    in the step's layout."""
+
+    @staticmethod
+    def forward(fctx, h, v, psi, ctx, site):
+        ctx.load_integrals(h.detach().cpu().numpy(), v.detach().cpu().numpy())
+        ctx.build_env(site)
+        y = torch.empty_like(psi)
+        ctx.heff_apply_ptr(site, psi.data_ptr(), y.data_ptr(), 1, TNS_FP64)
+        e = torch.dot(psi, y) / torch.dot(psi, psi)
+        fctx.tns = (ctx, site, h.shape[0])
+        fctx.save_for_backward(psi)
+        return e.detach().cpu()
+
+    @staticmethod
+    def backward(fctx, ge):
+        (psi,) = fctx.saved_tensors
+        ctx, site, N = fctx.tns
+        gamma, Gamma = ctx.rdm_ptr(site, psi.data_ptr(), N)
+        g = float(ge)
+        return (torch.from_numpy(g * gamma), torch.from_numpy(0.5 * g * Gamma), None, None, None)
+
+
+def integral_energy(h, v, psi, ctx, site):
+    return IntegralEnergy.apply(h, v, psi, ctx, site)

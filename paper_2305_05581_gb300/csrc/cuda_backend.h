@@ -42,9 +42,14 @@ struct SplitRed {  // a split tile: sum of nsplit partial tiles (fixed order) ->
 };
 
 // schedule variants tried by the online autotuner: the split-K target is
-// (total cost) / (resident CTAs x SMs x rounds) with rounds = kRounds[v]
-constexpr int kNumVariants = 3;
-constexpr double kRounds[kNumVariants] = {1.0, 2.0, 4.0};
+// (total cost) / (resident CTAs x SMs x rounds) with rounds = kRounds[v];
+// for the tensor-core form variant kWsVariant runs the persistent
+// warp-specialised kernel (its own split, rounds 2) instead of one CTA per
+// piece; the FP64 form tries the first kFp64Variants
+constexpr int kNumVariants = 4;
+constexpr double kRounds[kNumVariants] = {1.0, 2.0, 4.0, 2.0};
+constexpr int kWsVariant = 3;
+constexpr int kFp64Variants = 3;
 
 // one schedule of a work list for the FP64 kernels: tiles split into size
 // classes, long task lists cut into partial tiles summed in fixed order
@@ -67,7 +72,7 @@ struct FpVariant {
 struct Tune {
   int step = 0;   // products run so far while tuning
   int best = -1;
-  float ms[kNumVariants] = {1e30f, 1e30f, 1e30f};  // fastest sample of each variant
+  float ms[kNumVariants] = {1e30f, 1e30f, 1e30f, 1e30f};  // fastest sample of each variant
 };
 // tuning sequence: one untimed product (default variant: first-use effects
 // such as cold caches land there), then kTuneRounds timed samples of every
@@ -118,6 +123,9 @@ class CudaBackend : public Backend {
   // backend is created (a test makes the waits run out with it and checks the
   // reported error and that the context stays usable)
   unsigned long long tc_wait_ns = 200000000ull;
+  // TNS_TC_VARIANT=v (0..kNumVariants-1) fixes the tensor-core schedule
+  // variant instead of tuning it (tests run each kernel this way)
+  int forced_tc_variant = -1;
   ~CudaBackend() override;
   double* alloc(long long n) override;
   void release(double* p) override;

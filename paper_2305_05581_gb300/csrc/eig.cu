@@ -17,6 +17,8 @@
 // (Z[p * n + i], n x n row-major at off).  A is overwritten.
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "cuda_backend.h"
 
 namespace tns {
@@ -302,6 +304,15 @@ __global__ void __launch_bounds__(TQ_NT) k_tqr(const double* A, double* Zall, do
 void launch_syev(CudaBackend& be, double* A, double* Z, double* w, const long long* off, const int* n,
                  const int* woff, int nmat, int maxn, int* status) {
   if (nmat <= 0 || maxn <= 0 || !be.ok()) return;
+  {
+    // an error left pending by an earlier call would otherwise be reported
+    // as this launch's
+    const cudaError_t pending = cudaGetLastError();
+    if (pending != cudaSuccess) {
+      be.note(pending, "pending CUDA error before the truncation eigensolver");
+      return;
+    }
+  }
   if (maxn > SYEV_MAXN) {
     be.note(cudaErrorInvalidValue, "syev: matrix too large");
     return;
@@ -330,7 +341,14 @@ void launch_syev(CudaBackend& be, double* A, double* Z, double* w, const long lo
   dim3 grid(nmat, (maxn + TQ_COLS - 1) / TQ_COLS);
   k_tqr<<<grid, TQ_NT, smem_q, be.stream()>>>(A, Z, w, DE, off, n, woff, maxn, status);
   be.launches++;
-  be.note(cudaGetLastError(), "syev QR");
+  {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      const std::string what = "syev QR (" + std::to_string(nmat) + " matrices, largest " + std::to_string(maxn) +
+                               ", " + std::to_string(smem_q) + " bytes of shared memory)";
+      be.note(e, what.c_str());
+    }
+  }
 }
 
 }  // namespace tns

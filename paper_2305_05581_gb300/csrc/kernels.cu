@@ -928,6 +928,11 @@ CudaBackend::CudaBackend(int device, cudaStream_t s, bool own) : device_(device)
   if (k && std::strcmp(k, "dmma") == 0) fp64_kernel = 1;
   const char* w = std::getenv("TNS_TC_WAIT_NS");
   if (w && *w) tc_wait_ns = std::strtoull(w, nullptr, 10);
+  const char* tv = std::getenv("TNS_TC_VARIANT");
+  if (tv && *tv) {
+    const int x = std::atoi(tv);
+    if (x >= 0 && x < kNumVariants) forced_tc_variant = x;
+  }
 }
 
 CudaBackend::~CudaBackend() {
@@ -1522,9 +1527,11 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
   const int key = precision * 64 + nvec;
   Tune& tu = d.tune[key];
   if (!autotune && tu.best < 0) tu.best = 1;
+  const int nvar = precision != 0 ? kNumVariants : kFp64Variants;
+  if (precision != 0 && forced_tc_variant >= 0) tu.best = forced_tc_variant;
   const bool tuning = tu.best < 0;
   const bool timing = tuning && tu.step > 0;
-  const int v = !tuning ? tu.best : timing ? (tu.step - 1) % kNumVariants : 1;
+  const int v = !tuning ? tu.best : timing ? (tu.step - 1) % nvar : 1;
   if (precision != 0) {
     if (!prepare_tasks_tc(*this, tl, d, nvec, v, precision)) return;
   } else {
@@ -1553,9 +1560,9 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     tu.ms[v] = std::min(tu.ms[v], ms);
-    if (++tu.step == 1 + kTuneRounds * kNumVariants) {
+    if (++tu.step == 1 + kTuneRounds * nvar) {
       tu.best = 0;
-      for (int i = 1; i < kNumVariants; ++i)
+      for (int i = 1; i < nvar; ++i)
         if (tu.ms[i] < tu.ms[tu.best]) tu.best = i;
     }
   } else {

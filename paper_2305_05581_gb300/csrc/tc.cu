@@ -681,6 +681,436 @@ __global__ void __launch_bounds__(TC_NT, TC_CTAS)
 }
 
 // ---------------------------------------------------------------------------
+// the same product, warp-specialised and persistent
+//
+// One CTA per SM walks its share of the tile pieces (static stride over the
+// costliest-first list).  The steps (chunk c, X rows m0..m0+TC_MC-1) of all
+// its pieces form one stream that three roles pipeline through mbarriers:
+//   warp 0 (one lane)  copies: GEMM1 operand chunks into a ring of WS_S1
+//                      slots, the L slices of GEMM2 into a ring of WS_S2 slots;
+//   warp 1 (one lane)  MMAs: GEMM1 of step s into TMEM buffer D1[s & 1], then
+//                      GEMM2 of step s-1 into D2[piece & 1];
+//   warps 2-5          the T pass of step s (D1 -> B2[s & 1], scaled and
+//                      re-split) while GEMM1 of step s+1 runs, and the
+//                      epilogue of a piece (D2 -> Y) while the next piece's
+//                      first steps run.
+// The L ring holds every slice of one step (pc * K chunks <= WS_S2), so the
+// copy role never waits on a slot that only a later step's MMAs free.  Every
+// wait is bounded; after a timeout every role stops, the copy and MMA roles
+// wait (with the full bound) for their own copies and MMAs, and the CTA
+// releases its tensor memory before it exits.
+// ---------------------------------------------------------------------------
+constexpr int WS_NT = 192;
+constexpr int WS_S1 = 3;
+
+template <int TF32>
+struct WsSmem {
+  static constexpr int NS = TF32 ? 1 : 2;
+  static constexpr int ES = TF32 ? 4 : 2;
+  static constexpr int S2 = TF32 ? 16 : 8;                  // pc (<= 8) x K chunks of GEMM2 per step
+  static constexpr int A1 = TC_M * CH_BYTES, B1 = TC_MC * CH_BYTES;
+  static constexpr int G1 = NS * (A1 + B1);                 // one GEMM1 slot (all planes)
+  static constexpr int CB2 = TC_M * CH_BYTES;
+  static constexpr int B2 = TC_MC * ES / CH_BYTES * CB2;    // one plane of one T buffer
+  static constexpr int A2 = TC_M * CH_BYTES;
+  static constexpr int off_b2 = WS_S1 * G1;
+  static constexpr int off_l = off_b2 + 2 * NS * B2;
+  static constexpr int total = off_l + S2 * NS * A2;
+};
+
+__device__ __forceinline__ void bar_init_n(uint64_t* bar, int n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(n));
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int TF32>
+__global__ void __launch_bounds__(WS_NT, 1)
+    k_tasks_tc_ws(const TcTask* __restrict__ tasks, const Group* __restrict__ groups, const TcTile* __restrict__ tiles,
+                  int ntiles, const TcChunk* __restrict__ chunks, const unsigned char* __restrict__ ops_hi,
+                  const unsigned char* __restrict__ ops_lo, const unsigned char* __restrict__ x_hi,
+                  const unsigned char* __restrict__ x_lo, long long x_bytes, const XBlock* __restrict__ xblocks,
+                  double* yv, long long ys, int* flag, double* part_all, long long psize, int nv,
+                  unsigned long long wait_ns) {
+  using S = WsSmem<TF32>;
+  constexpr int ES = S::ES, NS = S::NS;
+  constexpr int NPROD = TF32 ? 1 : 3;
+  constexpr int EPC = CH_BYTES / ES;
+  constexpr uint32_t SBO_FULL = (CH_BYTES / 16) * 128;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t full1[WS_S1], empty1[WS_S1], full2[S::S2], empty2[S::S2];
+  __shared__ uint64_t d1_full[2], d1_empty[2], b2_full[2], b2_empty[2], d2_full[2], d2_empty[2], drain_bar;
+  __shared__ uint32_t tbase;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nitems = ntiles * nv;
+
+  if (tid == 0) {
+    for (int i = 0; i < WS_S1; ++i) {
+      bar_init_n(&full1[i], 1);
+      bar_init_n(&empty1[i], 1);
+    }
+    for (int i = 0; i < S::S2; ++i) {
+      bar_init_n(&full2[i], 1);
+      bar_init_n(&empty2[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      bar_init_n(&d1_full[i], 1);
+      bar_init_n(&d1_empty[i], 128);
+      bar_init_n(&b2_full[i], 128);
+      bar_init_n(&b2_empty[i], 1);
+      bar_init_n(&d2_full[i], 1);
+      bar_init_n(&d2_empty[i], 128);
+    }
+    bar_init_n(&drain_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tbase)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tD1[2] = {tbase, tbase + 32}, tD2[2] = {tbase + 64, tbase + 128};
+
+  // bounded wait on phase parity ph; on timeout the first role to give up
+  // records where and every role stops at its next wait
+  auto wait = [&](uint64_t* bar, uint32_t ph, int where, unsigned long long bound) -> bool {
+    if (abort_flag) return false;
+    if (wait_bar(bar, ph, bound)) return true;
+    if (atomicCAS(flag, 0, 1) == 0) {
+      flag[1] = blockIdx.x;
+      flag[2] = where;
+      flag[3] = warp;
+    }
+    abort_flag = 1;
+    return false;
+  };
+
+  if (warp == 0) {
+    // ------------------------------ copies ------------------------------
+    if (lane == 0) {
+      long long i1 = 0, i2 = 0;  // running slot counters of the two rings
+      int armed1[WS_S1], armed2[S::S2];
+      for (int i = 0; i < WS_S1; ++i) armed1[i] = 0;
+      for (int i = 0; i < S::S2; ++i) armed2[i] = 0;
+      bool go = true;
+      for (int w = blockIdx.x; w < nitems && go; w += gridDim.x) {
+        const TcTile TL = tiles[w / nv];
+        const int vec = w % nv;
+        const unsigned char* xh = x_hi + (long long)vec * x_bytes;
+        const unsigned char* xl = TF32 ? nullptr : x_lo + (long long)vec * x_bytes;
+        const int rp = (TL.ncols + 15) & ~15;
+        for (int c = TL.c0; c < TL.c1 && go; ++c) {
+          const TcChunk C = chunks[c];
+          const int pc = C.t1 - C.t0;
+          const XBlock XB = xblocks[tasks[C.t0].xb];
+          const int nch = (XB.img.kb + CH_BYTES - 1) / CH_BYTES;
+          for (int m0 = 0; m0 < XB.m && go; m0 += TC_MC) {
+            const int mc16 = (min(TC_MC, XB.m - m0) + 15) & ~15;
+            const int xg0 = m0 / 8, xng = min(mc16 / 8, XB.img.rg - xg0);
+            for (int kc = 0; kc < nch; ++kc, ++i1) {
+              const int sl = (int)(i1 % WS_S1);
+              if (!wait(&empty1[sl], (uint32_t)(((i1 / WS_S1) & 1) ^ 1), 1, wait_ns)) {
+                go = false;
+                break;
+              }
+              unsigned char* a = smem + sl * S::G1;
+              unsigned char* b = a + NS * S::A1;
+              const uint32_t rowb = (chunk_w(XB.img, kc) / 16) * 128;
+              uint32_t bytes = (xng > 0 ? xng * rowb : 0) * NS;
+              for (int t = 0; t < pc; ++t) {
+                const int ng = min(rp / 8, tasks[C.t0 + t].R.rg - TL.col0 / 8);
+                if (ng > 0) bytes += ng * rowb * NS;
+              }
+              expect_tx(&full1[sl], bytes);
+              armed1[sl] = (int)(i1 / WS_S1) + 1;
+              if (xng > 0) {
+                const long long xo = chunk_off(XB.img, kc) + (long long)xg0 * rowb;
+                bulk_g2s(b, xh + xo, xng * rowb, &full1[sl]);
+                if (!TF32) bulk_g2s(b + S::B1, xl + xo, xng * rowb, &full1[sl]);
+              }
+              for (int t = 0; t < pc; ++t) {
+                const Img R = tasks[C.t0 + t].R;
+                const int ng = min(rp / 8, R.rg - TL.col0 / 8);
+                if (ng <= 0) continue;
+                const long long ro = chunk_off(R, kc) + (long long)(TL.col0 / 8) * rowb;
+                const uint32_t dst = (uint32_t)(t * rp / 8) * rowb;
+                bulk_g2s(a + dst, ops_hi + ro, ng * rowb, &full1[sl]);
+                if (!TF32) bulk_g2s(a + S::A1 + dst, ops_lo + ro, ng * rowb, &full1[sl]);
+              }
+            }
+            if (!go) break;
+            const int nch2 = (mc16 * ES + CH_BYTES - 1) / CH_BYTES;
+            for (int t = 0; t < pc && go; ++t) {
+              const Img Lm = tasks[C.t0 + t].L;
+              const int lg0 = TL.row0 / 8, lng = min(TC_M / 8, Lm.rg - lg0);
+              for (int c2 = 0; c2 < nch2; ++c2, ++i2) {
+                const int sl = (int)(i2 % S::S2);
+                if (!wait(&empty2[sl], (uint32_t)(((i2 / S::S2) & 1) ^ 1), 2, wait_ns)) {
+                  go = false;
+                  break;
+                }
+                const int lc = (m0 * ES) / CH_BYTES + c2;
+                const uint32_t rowb = (chunk_w(Lm, lc) / 16) * 128;
+                unsigned char* a2 = smem + S::off_l + sl * NS * S::A2;
+                expect_tx(&full2[sl], lng * rowb * NS);
+                armed2[sl] = (int)(i2 / S::S2) + 1;
+                const long long lo_ = chunk_off(Lm, lc) + (long long)lg0 * rowb;
+                bulk_g2s(a2, ops_hi + lo_, lng * rowb, &full2[sl]);
+                if (!TF32) bulk_g2s(a2 + S::A2, ops_lo + lo_, lng * rowb, &full2[sl]);
+              }
+            }
+          }
+        }
+      }
+      // every copy issued by this role has landed (the last arm of a slot
+      // completing implies the earlier ones did) before the CTA can exit
+      for (int i = 0; i < WS_S1; ++i)
+        if (armed1[i]) wait_bar(&full1[i], (uint32_t)((armed1[i] - 1) & 1), TC_WAIT_NS);
+      for (int i = 0; i < S::S2; ++i)
+        if (armed2[i]) wait_bar(&full2[i], (uint32_t)((armed2[i] - 1) & 1), TC_WAIT_NS);
+    }
+  } else if (warp == 1) {
+    // ------------------------------- MMAs -------------------------------
+    if (lane == 0) {
+      long long i1 = 0, i2 = 0, s = 0;
+      int piece = 0;  // pieces with work of this CTA so far (D2 buffer and its phase)
+      bool go = true;
+      // the GEMM2 of the previous step, issued after the GEMM1 of the current one
+      struct Prev {
+        bool valid;
+        int c, m0, mc16, rp, first, last, piece;
+        long long s;
+      } prev = {false, 0, 0, 0, 0, 0, 0, 0, 0};
+      auto gemm2 = [&](const Prev& P) -> bool {
+        const TcChunk C = chunks[P.c];
+        const int pc = C.t1 - C.t0;
+        const int bb = (int)(P.s & 1);
+        if (!wait(&b2_full[bb], (uint32_t)((P.s >> 1) & 1), 3, wait_ns)) return false;
+        if (P.first && !wait(&d2_empty[P.piece & 1], (uint32_t)(((P.piece >> 1) & 1) ^ 1), 4, wait_ns)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int nch2 = (P.mc16 * ES + CH_BYTES - 1) / CH_BYTES;
+        const int nk2 = P.mc16 * ES / 32;
+        const uint32_t id = idesc(TF32 ? 2 : 1, P.rp);
+        const unsigned char* b2 = smem + S::off_b2 + bb * NS * S::B2;
+        bool acc_any = !P.first;
+        for (int t = 0; t < pc; ++t)
+          for (int c2 = 0; c2 < nch2; ++c2, ++i2) {
+            const int sl = (int)(i2 % S::S2);
+            if (!wait(&full2[sl], (uint32_t)((i2 / S::S2) & 1), 5, wait_ns)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const Img Lm = tasks[C.t0 + t].L;
+            const int lc = (P.m0 * ES) / CH_BYTES + c2;
+            const int kcm = chunk_w(Lm, lc) / 16;
+            const uint32_t rowb = kcm * 128;
+            const unsigned char* a2 = smem + S::off_l + sl * NS * S::A2;
+            const uint32_t bt = (uint32_t)(t * P.rp / 8) * SBO_FULL;
+            const int ks_here = min(kcm / 2, nk2 - c2 * (CH_BYTES / 32));
+            for (int ks = 0; ks < ks_here; ++ks)
+              for (int pr = 0; pr < NPROD; ++pr) {
+                const unsigned char* a = a2 + (pr == 2 ? S::A2 : 0);
+                const unsigned char* bbp = b2 + (pr == 1 ? S::B2 : 0) + c2 * S::CB2 + bt;
+                mma<TF32>(tD2[P.piece & 1], sdesc(smem_u32(a) + ks * 256, rowb),
+                          sdesc(smem_u32(bbp) + ks * 256, SBO_FULL), id, acc_any ? 1u : 0u);
+                acc_any = true;
+              }
+            commit(&empty2[sl]);
+          }
+        commit(&b2_empty[bb]);
+        if (P.last) commit(&d2_full[P.piece & 1]);
+        return true;
+      };
+      for (int w = blockIdx.x; w < nitems && go; w += gridDim.x) {
+        const TcTile TL = tiles[w / nv];
+        const int rp = (TL.ncols + 15) & ~15;
+        if (TL.c1 <= TL.c0) continue;
+        for (int c = TL.c0; c < TL.c1 && go; ++c) {
+          const TcChunk C = chunks[c];
+          const XBlock XB = xblocks[tasks[C.t0].xb];
+          const int nch = (XB.img.kb + CH_BYTES - 1) / CH_BYTES;
+          for (int m0 = 0; m0 < XB.m && go; m0 += TC_MC, ++s) {
+            const int mc16 = (min(TC_MC, XB.m - m0) + 15) & ~15;
+            // GEMM1 of step s into D1[s & 1] (free once the T pass of s-2 read it)
+            const int db = (int)(s & 1);
+            if (!wait(&d1_empty[db], (uint32_t)(((s >> 1) & 1) ^ 1), 6, wait_ns)) {
+              go = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t id = idesc(TF32 ? 2 : 1, mc16);
+            for (int kc = 0; kc < nch; ++kc, ++i1) {
+              const int sl = (int)(i1 % WS_S1);
+              if (!wait(&full1[sl], (uint32_t)((i1 / WS_S1) & 1), 7, wait_ns)) {
+                go = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;");
+              const unsigned char* a = smem + sl * S::G1;
+              const unsigned char* b = a + NS * S::A1;
+              const int kcm = chunk_w(XB.img, kc) / 16;
+              const uint32_t rowb = kcm * 128;
+              for (int ks = 0; ks < kcm / 2; ++ks)
+                for (int pr = 0; pr < NPROD; ++pr) {
+                  const unsigned char* aa = a + (pr == 2 ? S::A1 : 0);
+                  const unsigned char* bbp = b + (pr == 1 ? S::B1 : 0);
+                  const uint32_t acc = (kc > 0 || ks > 0 || pr > 0) ? 1u : 0u;
+                  mma<TF32>(tD1[db], sdesc(smem_u32(aa) + ks * 256, rowb), sdesc(smem_u32(bbp) + ks * 256, rowb),
+                            id, acc);
+                }
+              commit(&empty1[sl]);
+            }
+            if (!go) break;
+            commit(&d1_full[db]);
+            // GEMM2 of the previous step
+            if (prev.valid && !gemm2(prev)) {
+              go = false;
+              break;
+            }
+            prev.valid = true;
+            prev.c = c;
+            prev.m0 = m0;
+            prev.mc16 = mc16;
+            prev.rp = rp;
+            prev.first = (c == TL.c0 && m0 == 0) ? 1 : 0;
+            prev.last = (c == TL.c1 - 1 && m0 + TC_MC >= XB.m) ? 1 : 0;
+            prev.piece = piece;
+            prev.s = s;
+          }
+        }
+        ++piece;
+      }
+      if (go && prev.valid) gemm2(prev);
+      // every MMA of this role completed before the CTA can exit
+      commit(&drain_bar);
+      wait_bar(&drain_bar, 0, TC_WAIT_NS);
+    }
+  } else {
+    // ------------------------ T pass and epilogue ------------------------
+    const int q = warp & 3;               // TMEM lane quadrant of this warp
+    const int row = q * 32 + lane;        // TMEM lane = stacked R row (T pass) = tile row (epilogue)
+    long long s = 0;
+    int piece = 0;  // pieces with work so far (as counted by the MMA role)
+    bool go = true;
+    for (int w = blockIdx.x; w < nitems && go; w += gridDim.x) {
+      const TcTile TL = tiles[w / nv];
+      const Group G = groups[TL.g];
+      const int vec = w % nv;
+      const int rp = (TL.ncols + 15) & ~15;
+      const bool has_work = TL.c1 > TL.c0;
+      for (int c = TL.c0; c < TL.c1 && go; ++c) {
+        const TcChunk C = chunks[c];
+        const int pc = C.t1 - C.t0;
+        const XBlock XB = xblocks[tasks[C.t0].xb];
+        const int t = row / rp;
+        const float al = t < pc ? tasks[C.t0 + t].alpha : 0.f;
+        for (int m0 = 0; m0 < XB.m && go; m0 += TC_MC, ++s) {
+          const int mc = min(TC_MC, XB.m - m0), mc16 = (mc + 15) & ~15;
+          const int db = (int)(s & 1);
+          if (!wait(&d1_full[db], (uint32_t)((s >> 1) & 1), 8, wait_ns)) {
+            go = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          uint32_t r[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) r[j] = 0u;
+#pragma unroll
+          for (int i0 = 0; i0 < 32; i0 += 8) {
+            if (i0 < mc16) {
+              const uint32_t addr = tD1[db] + ((uint32_t)(q * 32) << 16) + (uint32_t)i0;
+              asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                           : "=r"(r[i0]), "=r"(r[i0 + 1]), "=r"(r[i0 + 2]), "=r"(r[i0 + 3]), "=r"(r[i0 + 4]),
+                             "=r"(r[i0 + 5]), "=r"(r[i0 + 6]), "=r"(r[i0 + 7])
+                           : "r"(addr));
+            }
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          bar_arrive(&d1_empty[db]);
+          if (!wait(&b2_empty[db], (uint32_t)(((s >> 1) & 1) ^ 1), 9, wait_ns)) {
+            go = false;
+            break;
+          }
+          unsigned char* b2 = smem + S::off_b2 + db * NS * S::B2;
+#pragma unroll
+          for (int i0 = 0; i0 < 32; i0 += 8) {
+            if (i0 >= mc16) continue;
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = (t < pc && i0 + e < mc) ? al * __uint_as_float(r[i0 + e]) : 0.f;
+            if (TF32) {
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh) {
+                const int i = i0 + 4 * hh;
+                const int off = (i / EPC) * S::CB2 + ((row >> 3) * (CH_BYTES / 16) + (i % EPC) * ES / 16) * 128 +
+                                (row & 7) * 16;
+                uint32_t qq[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(qq[e]) : "f"(v[4 * hh + e]));
+                *(uint4*)(b2 + off) = make_uint4(qq[0], qq[1], qq[2], qq[3]);
+              }
+            } else {
+              const int off = (i0 / EPC) * S::CB2 + ((row >> 3) * (CH_BYTES / 16) + (i0 % EPC) * ES / 16) * 128 +
+                              (row & 7) * 16;
+              __align__(16) __nv_bfloat16 hh[8], ll[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                hh[e] = __float2bfloat16_rn(v[e]);
+                ll[e] = __float2bfloat16_rn(v[e] - __bfloat162float(hh[e]));
+              }
+              *(uint4*)(b2 + off) = *(const uint4*)hh;
+              *(uint4*)(b2 + S::B2 + off) = *(const uint4*)ll;
+            }
+          }
+          asm volatile("fence.proxy.async.shared::cta;");
+          bar_arrive(&b2_full[db]);
+        }
+      }
+      if (!go) break;
+      // epilogue of the piece: D2 -> Y (or its partial tile)
+      double* Y = yv + (long long)vec * ys + G.yoff;
+      double* part = TL.poff >= 0 ? part_all + (long long)vec * psize + TL.poff : nullptr;
+      const int pb = piece & 1;
+      if (has_work) {
+        if (!wait(&d2_full[pb], (uint32_t)((piece >> 1) & 1), 10, wait_ns)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+      }
+      for (int j0 = 0; j0 < rp; j0 += 8) {
+        uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (has_work) {
+          const uint32_t addr = tD2[pb] + ((uint32_t)(q * 32) << 16) + (uint32_t)j0;
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                         "=r"(r[7])
+                       : "r"(addr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+        }
+        if (row < TL.nrows)
+          for (int e = 0; e < 8; ++e)
+            if (j0 + e < TL.ncols) {
+              const double val = (double)__uint_as_float(r[e]);
+              if (part)
+                part[row * TL.ncols + j0 + e] = val;
+              else
+                Y[(long long)(TL.row0 + row) * G.r + TL.col0 + j0 + e] = val;
+            }
+      }
+      if (has_work) {
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        bar_arrive(&d2_empty[pb]);
+        ++piece;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tbase));
+}
+
+// ---------------------------------------------------------------------------
 // host planning
 // ---------------------------------------------------------------------------
 Img make_img(int rows, int cols, int es, long long& arena) {
@@ -1094,6 +1524,10 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
     be.note(cudaFuncSetAttribute(k_tasks_tc<1>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared),
             "k_tasks_tc carve-out");
+    be.note(cudaFuncSetAttribute(k_tasks_tc_ws<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, WsSmem<0>::total),
+            "k_tasks_tc_ws shared memory");
+    be.note(cudaFuncSetAttribute(k_tasks_tc_ws<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, WsSmem<1>::total),
+            "k_tasks_tc_ws shared memory");
     attr = true;
   }
   return be.ok();
@@ -1114,6 +1548,23 @@ void enqueue_tasks_tc(CudaBackend& be, DevList& d, const double* xv, double* yv,
       k_img_x<0><<<gx, 256, 0, be.stream()>>>(plan->xblocks, xv, xs, plan->x_hi, plan->x_lo, plan->x_bytes);
     be.launches++;
     be.note(cudaGetLastError(), "input images");
+  }
+  if (variant == kWsVariant) {
+    // persistent warp-specialised kernel: one CTA per SM over all pieces
+    const unsigned items = (unsigned)V.ntiles * (unsigned)nvec;
+    const unsigned grid = std::min<unsigned>(items, (unsigned)plan->sms);
+    if (precision == TNS_TF32)
+      k_tasks_tc_ws<1><<<grid, WS_NT, WsSmem<1>::total, be.stream()>>>(
+          plan->tasks, d.groups, V.tiles, V.ntiles, plan->chunks, plan->ops_hi, plan->ops_lo, plan->x_hi, plan->x_lo,
+          plan->x_bytes, plan->xblocks, yv, ys, plan->flag, V.part, V.psize, nvec, be.tc_wait_ns);
+    else
+      k_tasks_tc_ws<0><<<grid, WS_NT, WsSmem<0>::total, be.stream()>>>(
+          plan->tasks, d.groups, V.tiles, V.ntiles, plan->chunks, plan->ops_hi, plan->ops_lo, plan->x_hi, plan->x_lo,
+          plan->x_bytes, plan->xblocks, yv, ys, plan->flag, V.part, V.psize, nvec, be.tc_wait_ns);
+    be.launches++;
+    be.note(cudaGetLastError(), "k_tasks_tc_ws");
+    if (V.nreds > 0) launch_reduce_splits(be, V.reds, V.nreds, d.groups, V.part, V.psize, yv, ys, nvec);
+    return;
   }
   const unsigned grid = (unsigned)V.ntiles * (unsigned)nvec;
   if (precision == TNS_TF32)

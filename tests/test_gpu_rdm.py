@@ -117,3 +117,47 @@ def test_rdm_identities_n30():
     assert np.max(np.abs(gamma - gamma.T)) < 1e-12
     e = _energy(ctx, k, x)
     assert abs(e - (np.sum(h * gamma) + 0.5 * np.sum(v * Gamma))) < 1e-9 * abs(e)
+
+
+def test_rdm_finite_differences_n30_d512():
+    """The differentiation-form workload (30 orbitals, 30 electrons, D = 512, random
+    MPS at the middle bond): dE/dh and dE/dv through the torch.autograd.Function
+    over the library (tns_rdm in backward) against central differences (step
+    1e-5) of E(theta) = <psi|H_eff(theta)|psi>/<psi|psi>, the MPS fixed, on two
+    entries of h and two orbits of (ij|kl): relative error <= 1e-6."""
+    from paper_2305_05581_gb300.autograd import integral_energy
+    c = synth.WORKLOADS["n30"]
+    N, n, s2, D = c["N"], c["n_elec"], c["two_sz"], c["D"]
+    k = N // 2 - 1
+    ctx, h, v, bonds, sites = _setup(N, n, s2, D, k, c["seed"], lam=c["lam"])
+    desc, length = ctx.psi_layout(k)
+    g = torch.Generator(device="cuda").manual_seed(6)
+    x = torch.randn(length, device="cuda", dtype=torch.float64, generator=g)
+    ht = torch.tensor(h, requires_grad=True)
+    vt = torch.tensor(v, requires_grad=True)
+    e = integral_energy(ht, vt, x, ctx, k)
+    gh, gv = torch.autograd.grad(e, (ht, vt))
+    gh, gv = gh.numpy(), gv.numpy()
+    d = 1e-5
+
+    def energy_at(hh, vv):
+        ctx.load_integrals(hh, vv)
+        ctx.build_env(k)
+        return _energy(ctx, k, x)
+
+    for (i, j) in [(3, 3), (14, 16)]:
+        p = np.zeros((N, N))
+        p[i, j] += 1.0
+        if i != j:
+            p[j, i] += 1.0
+        fd = (energy_at(h + d * p, v) - energy_at(h - d * p, v)) / (2 * d)
+        an = float(np.sum(p * gh))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (i, j, fd, an)
+    for idx in [(14, 14, 15, 15), (13, 16, 14, 15)]:
+        imgs = {tuple(idx[q] for q in perm) for perm in PERMS}
+        p = np.zeros((N, N, N, N))
+        for im in imgs:
+            p[im] = 1.0
+        fd = (energy_at(h, v + d * p) - energy_at(h, v - d * p)) / (2 * d)
+        an = float(np.sum(p * gv))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (idx, fd, an)
