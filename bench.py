@@ -409,6 +409,7 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     mem = ctx.memory_stats()
+    sched = ctx.schedule_stats()
     elapsed = e0.elapsed_time(e1) * 1e-3
     elapsed, flops_all = combine_ranks(dist, elapsed, flops, "cuda")
     value = flops_all / elapsed / 1e12
@@ -516,7 +517,7 @@ def main():
                 "fp64_arm": fp64_arm, "precision_arm": prec_arm, "speedup_vs_fp64": speedup,
                 "env": env, "memory": {k2: mem[k2] for k2 in ("device_peak", "device_limit", "host_peak", "staged",
                                                               "restored", "dropped", "built")},
-                "peaks": peaks,
+                "peaks": peaks, "schedules": sched,
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -328,6 +328,22 @@ int tns_heff_flops(tns_ctx* ctx, int site, double* flops, long long* nproducts);
 int tns_checkpoint_save(tns_ctx* ctx, const char* path, int site, int left_to_right);
 int tns_checkpoint_load(tns_ctx* ctx, const char* path, int* site, int* left_to_right);
 
+/* Schedules of the grouped product (the batched form's autotuner): each new
+ * work list of a precision and vector count first runs its schedule
+ * variants in turn (split-K targets of 1, 2 and 4 rounds over the SMs; for the
+ * tensor-core forms also the persistent warp-specialised kernel), timed with
+ * CUDA events, and keeps the fastest; the choice is cached under a shape
+ * signature of the list (product and block counts, histogram of output-block
+ * sizes), so later lists of the same shape take it without tuning.
+ * runs[p][v]: steady-state products of precision p (TNS_FP64, TNS_TF32,
+ * TNS_BF16X3) that ran variant v. */
+typedef struct tns_sched_stats {
+  long long tuned;       /* work lists tuned */
+  long long cache_hits;  /* work lists that took a cached choice */
+  long long runs[3][4];
+} tns_sched_stats;
+int tns_schedule_stats(tns_ctx* ctx, tns_sched_stats* out);
+
 /* Out-of-HBM environments (the tree-traversal cache of Alg. 1, Sec. "Tree-
  * Traversal Optimized Virtual Memory Addressing", applied to the chain of
  * left and right blocks).  The operator catalogues of all blocks of a sweep

@@ -24,7 +24,8 @@ SYMBOLS = ["create", "destroy", "last_error", "load_integrals", "mps_init", "mps
            "psi_layout", "heff_apply", "heff_diag", "davidson", "sweep", "heff_flops", "step", "psi_guess",
            "heff_diag_noalloc", "env_arena", "heff_adjoint", "sym_eig", "rdm", "set_memory_budget",
            "memory_stats", "heff_apply_part",
-           "checkpoint_save", "checkpoint_load"]
+           "checkpoint_save", "checkpoint_load",
+           "schedule_stats"]
 
 
 class TnsError(RuntimeError):
@@ -51,6 +52,15 @@ class StepStats(C.Structure):
                 ("svd_seconds", C.c_double), ("seconds", C.c_double), ("length", C.c_longlong),
                 ("bond_dim", C.c_int), ("kernel_launches", C.c_longlong), ("exact_products", C.c_int),
                 ("exact_seconds", C.c_double), ("env_flops", C.c_double), ("env_bytes", C.c_double)]
+
+
+class SchedStats(C.Structure):
+    _fields_ = [("tuned", C.c_longlong), ("cache_hits", C.c_longlong), ("runs", (C.c_longlong * 4) * 3)]
+
+    def as_dict(self):
+        names = ["fp64", "tf32", "bf16x3"]
+        return {"tuned": int(self.tuned), "cache_hits": int(self.cache_hits),
+                "runs": {names[p]: [int(self.runs[p][v]) for v in range(4)] for p in range(3)}}
 
 
 class MemStats(C.Structure):
@@ -104,6 +114,7 @@ def load_library(path: str = DEFAULT_LIB, prefix: str = "tns_"):
         "rdm": (C.c_int, [vp, C.c_int, vp, dp, dp]),
         "set_memory_budget": (C.c_int, [vp, C.c_longlong, C.c_longlong]),
         "checkpoint_save": (C.c_int, [vp, C.c_char_p, C.c_int, C.c_int]),
+        "schedule_stats": (C.c_int, [vp, C.POINTER(SchedStats)]),
         "checkpoint_load": (C.c_int, [vp, C.c_char_p, ip, ip]),
         "memory_stats": (C.c_int, [vp, C.POINTER(MemStats), C.c_int]),
     }
@@ -292,6 +303,12 @@ class Context:
         s, d = C.c_int(), C.c_int()
         self._check(self._fn("checkpoint_load")(self._h, os.fsencode(path), C.byref(s), C.byref(d)))
         return s.value, bool(d.value)
+
+    def schedule_stats(self) -> dict:
+        """Autotuner counters (tns_schedule_stats)."""
+        st = SchedStats()
+        self._check(self._fn("schedule_stats")(self._h, C.byref(st)))
+        return st.as_dict()
 
     def set_memory_budget(self, device_bytes: int = 0, host_bytes: int = 0):
         """Device budget and pinned host memory for staged catalogues (0 = none)."""

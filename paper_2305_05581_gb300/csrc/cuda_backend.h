@@ -94,6 +94,7 @@ struct GraphSlot {
 // device copy of a work list
 struct DevList {
   long long gen = -1;
+  unsigned long long shape = 0;  // shape signature of the list (schedule cache key)
   Task* tasks = nullptr;
   Group* groups = nullptr;
   Tile* wtiles = nullptr;    // 32 x 16 warp tiles of the FP64 tensor (DMMA) kernel
@@ -177,6 +178,10 @@ class CudaBackend : public Backend {
   void* scratch(size_t bytes, int slot);
   // counted launches of the engine's own kernels
   long long launches = 0;
+  // schedule tuning: lists tuned, lists that took a cached choice, and how
+  // often each variant ran as the chosen one (per precision: 0 FP64, 1 TF32, 2 BF16X3)
+  long long tuned = 0, tune_cache_hits = 0;
+  long long variant_runs[3][kNumVariants] = {};
   float last_ms = 0.f;
 
  private:
@@ -185,6 +190,9 @@ class CudaBackend : public Backend {
   bool own_;
   std::string err_;
   std::map<const TaskList*, DevList> lists_;
+  // best schedule variant per (precision, nvec, shape signature): work lists
+  // of later steps with the same shape take it without tuning again
+  std::map<std::pair<int, unsigned long long>, int> tune_cache_;
   std::vector<std::pair<void*, size_t>> scratch_ = std::vector<std::pair<void*, size_t>>(8, {nullptr, 0});
   cudaStream_t gstream_ = nullptr;  // side stream for graph capture and replay
   cudaEvent_t gev_[2] = {nullptr, nullptr};

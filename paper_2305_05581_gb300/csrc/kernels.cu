@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
@@ -1125,6 +1126,26 @@ void CudaBackend::free_list(DevList& d) {
   d = DevList();
 }
 
+// shape signature of a work list: the number of products and output blocks
+// (half-octave buckets) and the histogram of output-block sizes q*r over
+// octaves, each bin's share of the products in eighths -- lists of the same
+// bond in successive sweeps (and of neighbouring bonds) share it
+static unsigned long long shape_signature(const TaskList& tl) {
+  unsigned long long h = 1469598103934665603ULL;
+  auto mix = [&](long long x) { h = (h ^ (unsigned long long)x) * 1099511628211ULL; };
+  auto b2 = [](double x) { return (long long)std::floor(2.0 * std::log2(x + 1.0)); };
+  mix(b2((double)tl.tasks.size()));
+  mix(b2((double)tl.groups.size()));
+  long long hist[24] = {};
+  for (const Group& g : tl.groups) {
+    const int b = std::min(23, (int)std::log2((double)g.q * g.r + 1.0));
+    hist[b] += g.t1 - g.t0;
+  }
+  const double n = std::max<double>(1.0, (double)tl.tasks.size());
+  for (long long c : hist) mix((long long)std::floor(8.0 * c / n));
+  return h;
+}
+
 void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
   free_list(d);
   d.tasks = dev_copy(tl.tasks, *this);
@@ -1149,6 +1170,7 @@ void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
   d.nwtiles = (int)wt.size();
   d.wtiles = dev_copy(wt, *this);
   d.gen = tl.gen;
+  d.shape = shape_signature(tl);
   note(cudaStreamSynchronize(stream_), "work list upload");
 }
 
@@ -1529,6 +1551,14 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
   if (!autotune && tu.best < 0) tu.best = 1;
   const int nvar = precision != 0 ? kNumVariants : kFp64Variants;
   if (precision != 0 && forced_tc_variant >= 0) tu.best = forced_tc_variant;
+  const auto ckey = std::make_pair(key, d.shape);
+  if (tu.best < 0 && tu.step == 0 && autotune) {
+    auto it = tune_cache_.find(ckey);
+    if (it != tune_cache_.end()) {
+      tu.best = it->second;
+      ++tune_cache_hits;
+    }
+  }
   const bool tuning = tu.best < 0;
   const bool timing = tuning && tu.step > 0;
   const int v = !tuning ? tu.best : timing ? (tu.step - 1) % nvar : 1;
@@ -1564,9 +1594,12 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
       tu.best = 0;
       for (int i = 1; i < nvar; ++i)
         if (tu.ms[i] < tu.ms[tu.best]) tu.best = i;
+      tune_cache_[ckey] = tu.best;
+      ++tuned;
     }
   } else {
     launch_graphed(d, key, xv, yv, nvec, xs, ys, enqueue);
+    if (precision >= 0 && precision < 3) ++variant_runs[precision][v];
   }
   if (precision != 0) check_tasks_tc(*this, d);
 }

@@ -912,6 +912,14 @@ static int backend_diag_noalloc(tns::Engine& E, double* diag, std::string& err) 
   return tns::heff_diag_noalloc(be, E.step(), diag, err);
 }
 
+static void backend_sched_stats(tns::Engine& E, tns_sched_stats* out) {
+  tns::CudaBackend& be = *static_cast<tns::CudaBackend*>(E.be());
+  out->tuned = be.tuned;
+  out->cache_hits = be.tune_cache_hits;
+  for (int p = 0; p < 3; ++p)
+    for (int v = 0; v < 4; ++v) out->runs[p][v] = v < tns::kNumVariants ? be.variant_runs[p][v] : 0;
+}
+
 static long long backend_mem_peak(tns::Engine& E, bool reset) {
   tns::CudaBackend& be = *static_cast<tns::CudaBackend*>(E.be());
   const long long p = tns::dmem(be.device()).peak;

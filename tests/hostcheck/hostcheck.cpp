@@ -157,6 +157,8 @@ static int backend_sweep(tns::Engine&, const tns_sweep_opts*, double*, tns_sweep
   err = "not available in the host-logic check library";
   return -2;
 }
+static void backend_sched_stats(tns::Engine&, tns_sched_stats* out) { *out = tns_sched_stats{}; }
+
 static long long backend_mem_peak(tns::Engine& e, bool reset) {
   HostBackend& b = *static_cast<HostBackend*>(e.be());
   const long long p = b.peak;

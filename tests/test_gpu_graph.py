@@ -112,3 +112,29 @@ def test_graph_replay_matches_oracle():
     ref = blocks_to_vector(desc, length, O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2).apply(X))
     for y in ys:
         assert np.linalg.norm(y.cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec", [TNS_FP64, TNS_BF16X3])
+def test_tuned_schedule_is_cached_by_shape(prec):
+    """A work list of the same shape (the step's list rebuilt) takes the cached
+    schedule without tuning again, and its products equal the tuned list's."""
+    N, n, s2, D, k = CASE
+    ctx = _ctx()
+    _load(ctx)
+    ctx.build_env(k)
+    desc, length = ctx.psi_layout(k)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(length, device="cuda", dtype=torch.float64, generator=g)
+    y = torch.empty_like(x)
+    for _ in range(12):  # one untimed product, two timed samples of every variant, then the graph
+        ctx.heff_apply_ptr(k, x.data_ptr(), y.data_ptr(), 1, prec)
+    st0 = ctx.schedule_stats()
+    assert st0["tuned"] == 1 and st0["cache_hits"] == 0
+    ctx.build_env(k)  # a new work list of the same shape
+    y2 = torch.empty_like(x)
+    ctx.heff_apply_ptr(k, x.data_ptr(), y2.data_ptr(), 1, prec)
+    torch.cuda.synchronize()
+    st1 = ctx.schedule_stats()
+    assert st1["tuned"] == 1 and st1["cache_hits"] == 1
+    assert torch.equal(y, y2)  # same schedule, same summation order
+    ctx.close()
