@@ -991,6 +991,13 @@ __global__ void __launch_bounds__(WS_NT, 1)
     // ------------------------ T pass and epilogue ------------------------
     const int q = warp & 3;               // TMEM lane quadrant of this warp
     const int row = q * 32 + lane;        // TMEM lane = stacked R row (T pass) = tile row (epilogue)
+    // the warp-collective TMEM loads below need the whole warp: a wait that
+    // gives up on any lane stops all of them
+    auto wait_w = [&](uint64_t* bar, uint32_t ph, int where) -> bool {
+      const bool ok = __all_sync(0xffffffffu, wait(bar, ph, where, wait_ns) ? 1 : 0);
+      if (!ok) abort_flag = 1;
+      return ok;
+    };
     long long s = 0;
     int piece = 0;  // pieces with work so far (as counted by the MMA role)
     bool go = true;
@@ -1009,7 +1016,7 @@ __global__ void __launch_bounds__(WS_NT, 1)
         for (int m0 = 0; m0 < XB.m && go; m0 += TC_MC, ++s) {
           const int mc = min(TC_MC, XB.m - m0), mc16 = (mc + 15) & ~15;
           const int db = (int)(s & 1);
-          if (!wait(&d1_full[db], (uint32_t)((s >> 1) & 1), 8, wait_ns)) {
+          if (!wait_w(&d1_full[db], (uint32_t)((s >> 1) & 1), 8)) {
             go = false;
             break;
           }
@@ -1030,7 +1037,7 @@ __global__ void __launch_bounds__(WS_NT, 1)
           asm volatile("tcgen05.wait::ld.sync.aligned;");
           asm volatile("tcgen05.fence::before_thread_sync;");
           bar_arrive(&d1_empty[db]);
-          if (!wait(&b2_empty[db], (uint32_t)(((s >> 1) & 1) ^ 1), 9, wait_ns)) {
+          if (!wait_w(&b2_empty[db], (uint32_t)(((s >> 1) & 1) ^ 1), 9)) {
             go = false;
             break;
           }
@@ -1075,7 +1082,7 @@ __global__ void __launch_bounds__(WS_NT, 1)
       double* part = TL.poff >= 0 ? part_all + (long long)vec * psize + TL.poff : nullptr;
       const int pb = piece & 1;
       if (has_work) {
-        if (!wait(&d2_full[pb], (uint32_t)((piece >> 1) & 1), 10, wait_ns)) break;
+        if (!wait_w(&d2_full[pb], (uint32_t)((piece >> 1) & 1), 10)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
       }
       for (int j0 = 0; j0 < rp; j0 += 8) {
