@@ -174,6 +174,10 @@ class CudaBackend : public Backend {
   // launches of the FP64 product kernels of variant v (no allocation, no
   // synchronisation: capturable)
   void enqueue_fp64(const DevList& d, int v, const double* xv, double* yv, int nvec, long long xs, long long ys);
+  // room for `bytes` of the backend's own allocations (the engine's hook)
+  void need(long long bytes) {
+    if (room && bytes > (64LL << 20)) room(bytes);
+  }
   // scratch device memory owned by the backend (grows, never shrinks)
   void* scratch(size_t bytes, int slot);
   // counted launches of the engine's own kernels

@@ -321,16 +321,15 @@ void launch_syev(CudaBackend& be, double* A, double* Z, double* w, const long lo
   double* DE = (double*)be.scratch(sizeof(double) * 2 * (size_t)nmat * maxn + 64, 3);
   if (!DE) return;
   const size_t smem = sizeof(double) * 4 * (size_t)maxn, smem_q = sizeof(double) * 6 * (size_t)maxn;
-  if (smem > 48 * 1024) {
+  // the dynamic shared memory of both kernels is set on every call: with the
+  // kernels' static shared memory a request just below 48 KB can already
+  // exceed the default limit
+  {
     cudaError_t e = cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q);
     if (e != cudaSuccess) {
-      be.note(e, "syev: shared memory attribute");
-      return;
-    }
-  }
-  if (smem_q > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_tqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_q);
-    if (e != cudaSuccess) {
+      cudaGetLastError();
       be.note(e, "syev: shared memory attribute");
       return;
     }

@@ -28,6 +28,7 @@
 #pragma once
 
 #include <array>
+#include <functional>
 #include <cstdint>
 #include <map>
 #include <string>
@@ -351,6 +352,9 @@ struct Backend {
   // device bytes the backend will allocate to run a step's H_eff work list on
   // vectors of psi_length (work-list copy, operand images, solver vectors)
   virtual long long step_bytes(const TaskList& tl, long long psi_length) = 0;
+  // called by the backend before a large allocation of its own: the engine
+  // moves catalogues it does not need off the device to make room
+  std::function<int(long long)> room;
   virtual void sync() = 0;
   virtual std::string error() = 0;  // "" if fine
 };
@@ -430,7 +434,12 @@ struct MemStats {
 
 class Engine {
  public:
-  explicit Engine(Backend* be) : be_(be) {}
+  explicit Engine(Backend* be) : be_(be) {
+    be_->room = [this](long long bytes) {
+      std::string e;
+      return make_room(bytes, e);
+    };
+  }
   ~Engine();
 
   int load_integrals(int N, const double* h, const double* v, double e_core, std::string& err);

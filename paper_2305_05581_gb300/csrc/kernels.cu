@@ -1005,11 +1005,12 @@ void CudaBackend::release(double* p) {
 long long CudaBackend::step_bytes(const TaskList& tl, long long psi_length) {
   long long b = (long long)tl.tasks.size() * (long long)sizeof(Task) * 3 / 2 +
                 (long long)tl.groups.size() * (long long)sizeof(Group) * 4;
-  std::unordered_set<const double*> seenL, seenR;
+  std::unordered_set<uintptr_t> seenL, seenR;
   auto pad = [](long long rows, long long cols) { return ((rows + 7) / 8 * 8) * ((cols * 4 + 31) / 32 * 32); };
+  // an operator block used plain and transposed gets two images
   for (const Task& t : tl.tasks) {
-    if (!(t.flags & TF_LI) && seenL.insert(t.L).second) b += pad(t.q, t.m);
-    if (!(t.flags & TF_RI) && seenR.insert(t.R).second) b += pad(t.r, t.n);
+    if (!(t.flags & TF_LI) && seenL.insert((uintptr_t)t.L ^ ((t.flags & TF_LT) ? 1u : 0u)).second) b += pad(t.q, t.m);
+    if (!(t.flags & TF_RI) && seenR.insert((uintptr_t)t.R ^ ((t.flags & TF_RT) ? 1u : 0u)).second) b += pad(t.r, t.n);
   }
   // + split-K partial tiles and scratch
   return b + psi_length * 8LL * 120 + (1LL << 30);
@@ -1148,6 +1149,8 @@ static unsigned long long shape_signature(const TaskList& tl) {
 
 void CudaBackend::upload_list(const TaskList& tl, DevList& d) {
   free_list(d);
+  need((long long)tl.tasks.size() * (long long)sizeof(Task) * 3 / 2 +
+       (long long)tl.groups.size() * (long long)sizeof(Group) * 4);
   d.tasks = dev_copy(tl.tasks, *this);
   d.groups = dev_copy(tl.groups, *this);
   std::vector<Tile> wt;
@@ -1445,6 +1448,7 @@ template <class F>
 void CudaBackend::launch_graphed(DevList& d, int key, const double* xv, double* yv, int nvec, long long xs,
                                  long long ys, F&& enqueue) {
   GraphSlot& gs = d.graphs[key];
+  if (!gs.exec && !gs.failed) need(2LL * (long long)sizeof(double) * nvec * std::max(xs, ys));
   const long long elems = (long long)nvec * xs;
   if (!use_graphs || gs.failed || xs != ys) {
     enqueue(xv, yv);

@@ -1427,6 +1427,9 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
     std::vector<ImgJob> jobs;
     std::vector<XBlock> xbs;
     build_plan(tl, es, *plan, jobs, xbs);
+    be.need(plan->ops_bytes * (es == 2 ? 2 : 1) + (long long)plan->tasks_h.size() * (long long)sizeof(TcTask) +
+            (long long)plan->chunks_h.size() * (long long)sizeof(TcChunk) +
+            (long long)jobs.size() * (long long)sizeof(ImgJob));
     bool ok = true;
     plan->tasks = upload_vec(be, plan->tasks_h, ok);
     plan->chunks = upload_vec(be, plan->chunks_h, ok);
@@ -1469,6 +1472,7 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
     plan->x_hi = plan->x_lo = nullptr;
     plan->x_nvec = 0;
     const size_t xb = (size_t)std::max<long long>(plan->x_bytes, 16) * nvec;
+    be.need((long long)xb * (es == 2 ? 2 : 1));
     bool ok = dmalloc(&plan->x_hi, xb) == cudaSuccess;
     if (es == 2) ok = ok && dmalloc(&plan->x_lo, xb) == cudaSuccess;
     if (!ok) {
@@ -1509,6 +1513,7 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
     }
     V.part = nullptr;
     V.part_nvec = 0;
+    be.need((long long)sizeof(double) * V.psize * nvec);
     if (dmalloc(&V.part, sizeof(double) * V.psize * nvec) != cudaSuccess) {
       cudaGetLastError();
       be.note(cudaErrorMemoryAllocation, "tensor-core partial tiles");

@@ -102,12 +102,14 @@ def ground_state_rdms(ctx, site: int, N: int, precision: int, tol: float = 1e-9)
 
 
 def optimise(ctx, h, v, N: int, D: int, macro: int = 4, sweeps: int = 2, precision: int = 0,
-             e_core: float = 0.0, tol: float = 1e-9, max_step: float = 0.2, site: int | None = None):
+             e_core: float = 0.0, tol: float = 1e-9, max_step: float = 0.2, site: int = 1):
     """DMRG with orbital optimisation: `macro` rounds of (sweeps in the current
-    orbitals, RDMs at the middle step, one orbital step, integrals rotated).
-    The context must hold an MPS for (h, v).  Returns (history, U_total, h, v)
-    with history entries {energy, grad_norm, predicted}."""
-    site = N // 2 - 1 if site is None else site
+    orbitals, RDMs at step (site, site+1), one orbital step, integrals
+    rotated).  A sweep ends right to left at step (1, 2), where sites 0 and
+    3.. are left- and right-canonical: the default site=1 is a step at which
+    H_eff is the projected Hamiltonian.  The context must hold an MPS for
+    (h, v).  Returns (history, U_total, h, v) with history entries {energy,
+    grad_norm, predicted}."""
     U_tot = np.eye(N)
     hist = []
     for _ in range(macro):
