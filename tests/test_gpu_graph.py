@@ -74,14 +74,16 @@ def test_autotuned_graph_replays_match_fixed_schedule(prec, tol, nvec):
     ref = _apply(ref_ctx, x, nvec, prec, 1)[0]
     ctx = _ctx()
     _load(ctx)
-    # 7 tuning products (one untimed, then two timed samples of each of the
-    # three variants), then capture and replays of the chosen schedule
-    ys = _apply(ctx, x, nvec, prec, 11)
+    # tuning products (one untimed, then two timed samples of each variant:
+    # three split-K schedules, and for the tensor-core form also the
+    # persistent kernel), then capture and replays of the chosen schedule
+    ntune = 1 + 2 * (3 if prec == TNS_FP64 else 4)
+    ys = _apply(ctx, x, nvec, prec, ntune + 4)
     scale = float(torch.linalg.norm(ref))
     for y in ys:
         assert float(torch.linalg.norm(y - ref)) <= tol * scale
-    for y in ys[8:]:
-        assert torch.equal(y, ys[7])
+    for y in ys[ntune + 1:]:
+        assert torch.equal(y, ys[ntune])
 
 
 @pytest.mark.parametrize("prec", [TNS_FP64, TNS_BF16X3])
