@@ -117,7 +117,15 @@ def run_heff_case(args):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     dt = e0.elapsed_time(e1) * 1e-3 / args.steps
+    relerr = None
+    if prec != TNS_FP64:
+        # error of the reduced-precision product against the FP64 GPU path
+        y64 = torch.empty_like(x)
+        ctx.heff_apply_ptr(k, x.data_ptr(), y64.data_ptr(), args.nvec, TNS_FP64)
+        torch.cuda.synchronize()
+        relerr = float(torch.linalg.norm(y - y64) / torch.linalg.norm(y64))
     print(json.dumps({"case": "heff", "workload": args.workload, "state": args.state, "precision": args.precision,
+                      "relerr_vs_fp64": relerr,
                       "nvec": args.nvec,
                       "psi_blocks": int(len(desc)), "psi_length": int(length), "products": int(nprod),
                       "useful_flops": flops * args.nvec, "ms": dt * 1e3,

@@ -1127,23 +1127,24 @@ void CudaBackend::free_list(DevList& d) {
   d = DevList();
 }
 
-// shape signature of a work list: the number of products and output blocks
-// (half-octave buckets) and the histogram of output-block sizes q*r over
-// octaves, each bin's share of the products in eighths -- lists of the same
-// bond in successive sweeps (and of neighbouring bonds) share it
+// shape signature of a work list: the number of products (octave), the
+// product-weighted mean output-block size q*r (octave) and the share of
+// products on blocks larger than 64 x 64 (quarters) -- lists of one bond in
+// successive sweeps and of neighbouring bonds share it, lists of a very
+// different sector structure do not
 static unsigned long long shape_signature(const TaskList& tl) {
   unsigned long long h = 1469598103934665603ULL;
   auto mix = [&](long long x) { h = (h ^ (unsigned long long)x) * 1099511628211ULL; };
-  auto b2 = [](double x) { return (long long)std::floor(2.0 * std::log2(x + 1.0)); };
-  mix(b2((double)tl.tasks.size()));
-  mix(b2((double)tl.groups.size()));
-  long long hist[24] = {};
-  for (const Group& g : tl.groups) {
-    const int b = std::min(23, (int)std::log2((double)g.q * g.r + 1.0));
-    hist[b] += g.t1 - g.t0;
-  }
   const double n = std::max<double>(1.0, (double)tl.tasks.size());
-  for (long long c : hist) mix((long long)std::floor(8.0 * c / n));
+  double wsum = 0.0, big = 0.0;
+  for (const Group& g : tl.groups) {
+    const double c = g.t1 - g.t0, a = (double)g.q * g.r;
+    wsum += c * a;
+    if (a > 4096.0) big += c;
+  }
+  mix((long long)std::floor(std::log2(n)));
+  mix((long long)std::floor(std::log2(wsum / n + 1.0)));
+  mix((long long)std::floor(4.0 * big / n));
   return h;
 }
 
