@@ -76,6 +76,8 @@ struct TcTile {
 
 struct TcChunk {
   int t0, t1;  // products sharing one X block
+  int xb;      // that X block
+  int pad;
 };
 
 struct XBlock {
@@ -95,6 +97,10 @@ struct TcVariant {
   bool planned = false;
   TcTile* tiles = nullptr;
   int ntiles = 0;
+  // persistent kernel: pieces of CTA b are ws_order[ws_off[b] .. ws_off[b+1])
+  int* ws_order = nullptr;
+  int* ws_off = nullptr;
+  int ws_ctas = 0;
   SplitRed* reds = nullptr;
   int nreds = 0;
   long long psize = 0;
@@ -432,7 +438,7 @@ __global__ void __launch_bounds__(TC_NT, TC_CTAS)
     }
     if (tid == 0) {
       M.pc = pc;
-      M.xb = xblocks[tasks[C.t0].xb];
+      M.xb = xblocks[C.xb];
     }
   };
   auto issue1 = [&](int c, int m0, int kc, int b) {
@@ -728,7 +734,8 @@ __device__ __forceinline__ void bar_arrive(uint64_t* bar) {
 template <int TF32>
 __global__ void __launch_bounds__(WS_NT, 1)
     k_tasks_tc_ws(const TcTask* __restrict__ tasks, const Group* __restrict__ groups, const TcTile* __restrict__ tiles,
-                  int ntiles, const TcChunk* __restrict__ chunks, const unsigned char* __restrict__ ops_hi,
+                  const int* __restrict__ order, const int* __restrict__ order_off,
+                  const TcChunk* __restrict__ chunks, const unsigned char* __restrict__ ops_hi,
                   const unsigned char* __restrict__ ops_lo, const unsigned char* __restrict__ x_hi,
                   const unsigned char* __restrict__ x_lo, long long x_bytes, const XBlock* __restrict__ xblocks,
                   double* yv, long long ys, int* flag, double* part_all, long long psize, int nv,
@@ -744,7 +751,9 @@ __global__ void __launch_bounds__(WS_NT, 1)
   __shared__ uint32_t tbase;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nitems = ntiles * nv;
+  // this CTA's items: its pieces (balanced on the host by estimated cost) x vectors
+  const int it0 = order_off[blockIdx.x] * nv, it1 = order_off[blockIdx.x + 1] * nv;
+  auto item_tile = [&](int w) { return tiles[order[w / nv]]; };
 
   if (tid == 0) {
     for (int i = 0; i < WS_S1; ++i) {
@@ -797,8 +806,8 @@ __global__ void __launch_bounds__(WS_NT, 1)
       for (int i = 0; i < WS_S1; ++i) armed1[i] = 0;
       for (int i = 0; i < S::S2; ++i) armed2[i] = 0;
       bool go = true;
-      for (int w = blockIdx.x; w < nitems && go; w += gridDim.x) {
-        const TcTile TL = tiles[w / nv];
+      for (int w = it0; w < it1 && go; ++w) {
+        const TcTile TL = item_tile(w);
         const int vec = w % nv;
         const unsigned char* xh = x_hi + (long long)vec * x_bytes;
         const unsigned char* xl = TF32 ? nullptr : x_lo + (long long)vec * x_bytes;
@@ -806,7 +815,15 @@ __global__ void __launch_bounds__(WS_NT, 1)
         for (int c = TL.c0; c < TL.c1 && go; ++c) {
           const TcChunk C = chunks[c];
           const int pc = C.t1 - C.t0;
-          const XBlock XB = xblocks[tasks[C.t0].xb];
+          const XBlock XB = xblocks[C.xb];
+          // the operand images of the chunk's products, loaded together
+          Img Rs[TC_M / 16], Ls[TC_M / 16];
+#pragma unroll
+          for (int t = 0; t < TC_M / 16; ++t)
+            if (t < pc) {
+              Rs[t] = tasks[C.t0 + t].R;
+              Ls[t] = tasks[C.t0 + t].L;
+            }
           const int nch = (XB.img.kb + CH_BYTES - 1) / CH_BYTES;
           for (int m0 = 0; m0 < XB.m && go; m0 += TC_MC) {
             const int mc16 = (min(TC_MC, XB.m - m0) + 15) & ~15;
@@ -821,10 +838,12 @@ __global__ void __launch_bounds__(WS_NT, 1)
               unsigned char* b = a + NS * S::A1;
               const uint32_t rowb = (chunk_w(XB.img, kc) / 16) * 128;
               uint32_t bytes = (xng > 0 ? xng * rowb : 0) * NS;
-              for (int t = 0; t < pc; ++t) {
-                const int ng = min(rp / 8, tasks[C.t0 + t].R.rg - TL.col0 / 8);
-                if (ng > 0) bytes += ng * rowb * NS;
-              }
+#pragma unroll
+              for (int t = 0; t < TC_M / 16; ++t)
+                if (t < pc) {
+                  const int ng = min(rp / 8, Rs[t].rg - TL.col0 / 8);
+                  if (ng > 0) bytes += ng * rowb * NS;
+                }
               expect_tx(&full1[sl], bytes);
               armed1[sl] = (int)(i1 / WS_S1) + 1;
               if (xng > 0) {
@@ -832,8 +851,10 @@ __global__ void __launch_bounds__(WS_NT, 1)
                 bulk_g2s(b, xh + xo, xng * rowb, &full1[sl]);
                 if (!TF32) bulk_g2s(b + S::B1, xl + xo, xng * rowb, &full1[sl]);
               }
-              for (int t = 0; t < pc; ++t) {
-                const Img R = tasks[C.t0 + t].R;
+#pragma unroll
+              for (int t = 0; t < TC_M / 16; ++t) {
+                if (t >= pc) continue;
+                const Img R = Rs[t];
                 const int ng = min(rp / 8, R.rg - TL.col0 / 8);
                 if (ng <= 0) continue;
                 const long long ro = chunk_off(R, kc) + (long long)(TL.col0 / 8) * rowb;
@@ -844,8 +865,10 @@ __global__ void __launch_bounds__(WS_NT, 1)
             }
             if (!go) break;
             const int nch2 = (mc16 * ES + CH_BYTES - 1) / CH_BYTES;
-            for (int t = 0; t < pc && go; ++t) {
-              const Img Lm = tasks[C.t0 + t].L;
+#pragma unroll
+            for (int t = 0; t < TC_M / 16; ++t) {
+              if (t >= pc || !go) continue;
+              const Img Lm = Ls[t];
               const int lg0 = TL.row0 / 8, lng = min(TC_M / 8, Lm.rg - lg0);
               for (int c2 = 0; c2 < nch2; ++c2, ++i2) {
                 const int sl = (int)(i2 % S::S2);
@@ -897,12 +920,18 @@ __global__ void __launch_bounds__(WS_NT, 1)
         const uint32_t id = idesc(TF32 ? 2 : 1, P.rp);
         const unsigned char* b2 = smem + S::off_b2 + bb * NS * S::B2;
         bool acc_any = !P.first;
-        for (int t = 0; t < pc; ++t)
+        Img Ls[TC_M / 16];
+#pragma unroll
+        for (int t = 0; t < TC_M / 16; ++t)
+          if (t < pc) Ls[t] = tasks[C.t0 + t].L;
+#pragma unroll
+        for (int t = 0; t < TC_M / 16; ++t) {
+          if (t >= pc) continue;
           for (int c2 = 0; c2 < nch2; ++c2, ++i2) {
             const int sl = (int)(i2 % S::S2);
             if (!wait(&full2[sl], (uint32_t)((i2 / S::S2) & 1), 5, wait_ns)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const Img Lm = tasks[C.t0 + t].L;
+            const Img Lm = Ls[t];
             const int lc = (P.m0 * ES) / CH_BYTES + c2;
             const int kcm = chunk_w(Lm, lc) / 16;
             const uint32_t rowb = kcm * 128;
@@ -919,17 +948,18 @@ __global__ void __launch_bounds__(WS_NT, 1)
               }
             commit(&empty2[sl]);
           }
+        }
         commit(&b2_empty[bb]);
         if (P.last) commit(&d2_full[P.piece & 1]);
         return true;
       };
-      for (int w = blockIdx.x; w < nitems && go; w += gridDim.x) {
-        const TcTile TL = tiles[w / nv];
+      for (int w = it0; w < it1 && go; ++w) {
+        const TcTile TL = item_tile(w);
         const int rp = (TL.ncols + 15) & ~15;
         if (TL.c1 <= TL.c0) continue;
         for (int c = TL.c0; c < TL.c1 && go; ++c) {
           const TcChunk C = chunks[c];
-          const XBlock XB = xblocks[tasks[C.t0].xb];
+          const XBlock XB = xblocks[C.xb];
           const int nch = (XB.img.kb + CH_BYTES - 1) / CH_BYTES;
           for (int m0 = 0; m0 < XB.m && go; m0 += TC_MC, ++s) {
             const int mc16 = (min(TC_MC, XB.m - m0) + 15) & ~15;
@@ -1001,8 +1031,8 @@ __global__ void __launch_bounds__(WS_NT, 1)
     long long s = 0;
     int piece = 0;  // pieces with work so far (as counted by the MMA role)
     bool go = true;
-    for (int w = blockIdx.x; w < nitems && go; w += gridDim.x) {
-      const TcTile TL = tiles[w / nv];
+    for (int w = it0; w < it1 && go; ++w) {
+      const TcTile TL = item_tile(w);
       const Group G = groups[TL.g];
       const int vec = w % nv;
       const int rp = (TL.ncols + 15) & ~15;
@@ -1010,7 +1040,7 @@ __global__ void __launch_bounds__(WS_NT, 1)
       for (int c = TL.c0; c < TL.c1 && go; ++c) {
         const TcChunk C = chunks[c];
         const int pc = C.t1 - C.t0;
-        const XBlock XB = xblocks[tasks[C.t0].xb];
+        const XBlock XB = xblocks[C.xb];
         const int t = row / rp;
         const float al = t < pc ? tasks[C.t0 + t].alpha : 0.f;
         for (int m0 = 0; m0 < XB.m && go; m0 += TC_MC, ++s) {
@@ -1196,7 +1226,7 @@ void build_plan(const TaskList& tl, int es, TcPlan& P, std::vector<ImgJob>& jobs
           const TcTask& a = P.tasks_h[base + i];
           int j = i + 1;
           while (j < nt && j - i < cap && P.tasks_h[base + j].xb == a.xb) ++j;
-          P.chunks_h.push_back({base + i, base + j});
+          P.chunks_h.push_back({base + i, base + j, a.xb, 0});
           i = j;
         }
         T.c1 = (int)P.chunks_h.size();
@@ -1211,17 +1241,54 @@ void build_plan(const TaskList& tl, int es, TcPlan& P, std::vector<ImgJob>& jobs
 // cut tiles whose chunk lists are long into pieces of similar cost (each piece
 // accumulates its own TMEM tile and writes a partial tile; the pieces are
 // summed in order afterwards), so the CTAs of one launch finish together
+// estimated cost of one chunk of a tile piece (MMA work with padding, plus a
+// fixed cost for its copies, T pass and barriers)
+double chunk_cost(const std::vector<TcTask>& tasks, const TcChunk& C, const TcTile& T) {
+  double s = 1.5e4;
+  const TcTask& a = tasks[C.t0];
+  const int p = C.t1 - C.t0;
+  const int rp = (T.ncols + 15) & ~15;
+  const double mm = ((a.m + 15) / 16) * 16.0, nn = ((a.n + 15) / 16) * 16.0;
+  s += 2.0 * TC_M * mm * nn + p * 2.0 * TC_M * mm * rp;
+  return s;
+}
+
+// pieces of the persistent kernel per CTA: longest first onto the least
+// loaded of `ctas` CTAs (the kernel walks each CTA's list in order)
+void ws_assign(const std::vector<TcTask>& tasks, const std::vector<TcTile>& tiles, const std::vector<TcChunk>& chunks,
+               int ctas, std::vector<int>& order, std::vector<int>& off) {
+  const int n = (int)tiles.size();
+  std::vector<double> cost(n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int c = tiles[i].c0; c < tiles[i].c1; ++c) cost[i] += chunk_cost(tasks, chunks[c], tiles[i]);
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<std::vector<int>> per(ctas);
+  std::vector<std::pair<double, int>> heap;  // (load, cta), min-heap
+  for (int b = 0; b < ctas; ++b) heap.push_back({0.0, b});
+  auto cmp = [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+    return x.first > y.first || (x.first == y.first && x.second > y.second);
+  };
+  std::make_heap(heap.begin(), heap.end(), cmp);
+  for (int i : idx) {
+    std::pop_heap(heap.begin(), heap.end(), cmp);
+    auto& h = heap.back();
+    per[h.second].push_back(i);
+    h.first += cost[i];
+    std::push_heap(heap.begin(), heap.end(), cmp);
+  }
+  order.clear();
+  off.assign(1, 0);
+  for (int b = 0; b < ctas; ++b) {
+    for (int i : per[b]) order.push_back(i);
+    off.push_back((int)order.size());
+  }
+}
+
 void split_plan(const std::vector<TcTask>& tasks, std::vector<TcTile>& tiles, const std::vector<TcChunk>& chunks,
                 std::vector<SplitRed>& reds, long long& psize, int sms, double rounds) {
-  auto ccost = [&](const TcChunk& C, const TcTile& T) {
-    double s = 1.5e4;  // fixed cost of one chunk (copies, T pass, barriers)
-    const TcTask& a = tasks[C.t0];
-    const int p = C.t1 - C.t0;
-    const int rp = (T.ncols + 15) & ~15;
-    const double mm = ((a.m + 15) / 16) * 16.0, nn = ((a.n + 15) / 16) * 16.0;
-    s += 2.0 * TC_M * mm * nn + p * 2.0 * TC_M * mm * rp;
-    return s;
-  };
+  auto ccost = [&](const TcChunk& C, const TcTile& T) { return chunk_cost(tasks, C, T); };
   std::vector<double> tcost(tiles.size(), 0.0);
   double tot = 0;
   for (size_t i = 0; i < tiles.size(); ++i) {
@@ -1314,6 +1381,10 @@ bool check_plan(const TcPlan& P, const std::vector<TcTile>& tiles, const std::ve
         return false;
       }
       const TcTask& t0 = P.tasks_h[C.t0];
+      if (C.xb != t0.xb) {
+        why = "chunk X block";
+        return false;
+      }
       const XBlock& XB = xbs[t0.xb];
       for (int t = C.t0; t < C.t1; ++t) {
         const TcTask& k = P.tasks_h[t];
@@ -1496,6 +1567,13 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
     bool ok = true;
     V.tiles = upload_vec(be, tiles, ok);
     V.reds = upload_vec(be, reds, ok);
+    if (variant == kWsVariant) {
+      std::vector<int> order, off;
+      V.ws_ctas = std::max(1, std::min((int)tiles.size(), plan->sms));
+      ws_assign(plan->tasks_h, tiles, plan->chunks_h, V.ws_ctas, order, off);
+      V.ws_order = upload_vec(be, order, ok);
+      V.ws_off = upload_vec(be, off, ok);
+    }
     if (!ok) {
       be.note(cudaErrorMemoryAllocation, "tensor-core schedule");
       return false;
@@ -1562,17 +1640,17 @@ void enqueue_tasks_tc(CudaBackend& be, DevList& d, const double* xv, double* yv,
     be.note(cudaGetLastError(), "input images");
   }
   if (variant == kWsVariant) {
-    // persistent warp-specialised kernel: one CTA per SM over all pieces
-    const unsigned items = (unsigned)V.ntiles * (unsigned)nvec;
-    const unsigned grid = std::min<unsigned>(items, (unsigned)plan->sms);
+    // persistent warp-specialised kernel: one CTA per SM, each over its list
+    // of pieces (balanced by estimated cost) and all vectors
+    const unsigned grid = (unsigned)V.ws_ctas;
     if (precision == TNS_TF32)
       k_tasks_tc_ws<1><<<grid, WS_NT, WsSmem<1>::total, be.stream()>>>(
-          plan->tasks, d.groups, V.tiles, V.ntiles, plan->chunks, plan->ops_hi, plan->ops_lo, plan->x_hi, plan->x_lo,
-          plan->x_bytes, plan->xblocks, yv, ys, plan->flag, V.part, V.psize, nvec, be.tc_wait_ns);
+          plan->tasks, d.groups, V.tiles, V.ws_order, V.ws_off, plan->chunks, plan->ops_hi, plan->ops_lo, plan->x_hi,
+          plan->x_lo, plan->x_bytes, plan->xblocks, yv, ys, plan->flag, V.part, V.psize, nvec, be.tc_wait_ns);
     else
       k_tasks_tc_ws<0><<<grid, WS_NT, WsSmem<0>::total, be.stream()>>>(
-          plan->tasks, d.groups, V.tiles, V.ntiles, plan->chunks, plan->ops_hi, plan->ops_lo, plan->x_hi, plan->x_lo,
-          plan->x_bytes, plan->xblocks, yv, ys, plan->flag, V.part, V.psize, nvec, be.tc_wait_ns);
+          plan->tasks, d.groups, V.tiles, V.ws_order, V.ws_off, plan->chunks, plan->ops_hi, plan->ops_lo, plan->x_hi,
+          plan->x_lo, plan->x_bytes, plan->xblocks, yv, ys, plan->flag, V.part, V.psize, nvec, be.tc_wait_ns);
     be.launches++;
     be.note(cudaGetLastError(), "k_tasks_tc_ws");
     if (V.nreds > 0) launch_reduce_splits(be, V.reds, V.nreds, d.groups, V.part, V.psize, yv, ys, nvec);
@@ -1613,6 +1691,8 @@ void release_tc_plan(void* p) {
   TcPlan* plan = (TcPlan*)p;
   if (!plan) return;
   for (TcVariant& V : plan->var) {
+    if (V.ws_order) dfree(V.ws_order);
+    if (V.ws_off) dfree(V.ws_off);
     if (V.tiles) dfree(V.tiles);
     if (V.reds) dfree(V.reds);
     if (V.part) dfree(V.part);
