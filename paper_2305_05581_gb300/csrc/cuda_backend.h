@@ -122,11 +122,18 @@ class CudaBackend : public Backend {
   // bound of one wait inside the tensor-core product loop (ns); the
   // environment variable TNS_TC_WAIT_NS overrides the default 0.2 s when the
   // backend is created (a test makes the waits run out with it and checks the
-  // reported error and that the context stays usable)
+  // reported error and that the context stays usable; with 0 every warp of
+  // the small-block kernel first waits on a barrier that nothing completes,
+  // since its copies may land before any wait could run out)
   unsigned long long tc_wait_ns = 200000000ull;
   // TNS_TC_VARIANT=v (0..kNumVariants-1) fixes the tensor-core schedule
   // variant instead of tuning it (tests run each kernel this way)
   int forced_tc_variant = -1;
+  // output blocks whose dimensions, and those of every X block they read, are
+  // at most tc_small go to the warp-level small-block kernel of the
+  // tensor-core form (0: every block to the tile kernel; at most 32);
+  // environment TNS_TC_SMALL
+  int tc_small = 32;
   ~CudaBackend() override;
   double* alloc(long long n) override;
   void release(double* p) override;

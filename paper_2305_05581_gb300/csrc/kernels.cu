@@ -934,6 +934,8 @@ CudaBackend::CudaBackend(int device, cudaStream_t s, bool own) : device_(device)
     const int x = std::atoi(tv);
     if (x >= 0 && x < kNumVariants) forced_tc_variant = x;
   }
+  const char* sm = std::getenv("TNS_TC_SMALL");
+  if (sm && *sm) tc_small = std::max(0, std::min(32, std::atoi(sm)));
 }
 
 CudaBackend::~CudaBackend() {

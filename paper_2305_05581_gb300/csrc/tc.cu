@@ -33,6 +33,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <string>
 #include <tuple>
@@ -95,8 +96,10 @@ struct ImgJob {  // convert one operand block into its image
 
 struct TcVariant {
   bool planned = false;
-  TcTile* tiles = nullptr;
+  TcTile* tiles = nullptr;  // pieces of the tile kernel
   int ntiles = 0;
+  TcTile* wtiles[2] = {nullptr, nullptr};  // pieces of the small-block warp kernel (blocks <= 16, <= 32)
+  int nwtiles[2] = {0, 0};
   // persistent kernel: pieces of CTA b are ws_order[ws_off[b] .. ws_off[b+1])
   int* ws_order = nullptr;
   int* ws_off = nullptr;
@@ -108,9 +111,12 @@ struct TcVariant {
   int part_nvec = 0;
 };
 
+struct SwRec;
+
 struct TcPlan {
   int precision = 0;
   TcTask* tasks = nullptr;
+  SwRec* swrec = nullptr;  // the products as 16-byte records of the small-block kernel
   TcChunk* chunks = nullptr;
   XBlock* xblocks = nullptr;
   int nxb = 0;
@@ -123,7 +129,8 @@ struct TcPlan {
   long long x_bytes = 0;  // per vector
   int x_nvec = 0;
   std::vector<TcTask> tasks_h;
-  std::vector<TcTile> tiles_h;
+  std::vector<TcTile> tiles_h;   // tiles of the tile kernel
+  std::vector<TcTile> wtiles_h[2];  // output blocks of the small-block warp kernel (<= 16, <= 32)
   std::vector<TcChunk> chunks_h;
   std::vector<XBlock> xbs_h;
   TcVariant var[kNumVariants];
@@ -1147,6 +1154,8 @@ __global__ void __launch_bounds__(WS_NT, 1)
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tbase));
 }
 
+#include "tc_small.inc"
+
 // ---------------------------------------------------------------------------
 // host planning
 // ---------------------------------------------------------------------------
@@ -1160,8 +1169,11 @@ Img make_img(int rows, int cols, int es, long long& arena) {
 }
 
 // products of a group ordered by X block; tiles of 128 rows x 64 columns;
-// chunks of products sharing X with (products x padded tile columns) <= 128
-void build_plan(const TaskList& tl, int es, TcPlan& P, std::vector<ImgJob>& jobs, std::vector<XBlock>& xbs) {
+// chunks of products sharing X with (products x padded tile columns) <= 128.
+// A group whose block and X blocks all have dimensions <= small is one tile
+// of the small-block warp kernel instead (its chunks only delimit pieces).
+void build_plan(const TaskList& tl, int es, int small, TcPlan& P, std::vector<ImgJob>& jobs,
+                std::vector<XBlock>& xbs) {
   std::map<std::tuple<const double*, int, int, int>, Img> imgs;  // (src, trans, rows, cols)
   std::map<long long, int> xidx;
   long long arena = 0, xarena = 0;
@@ -1176,6 +1188,8 @@ void build_plan(const TaskList& tl, int es, TcPlan& P, std::vector<ImgJob>& jobs
   };
   P.tasks_h.clear();
   P.tiles_h.clear();
+  P.wtiles_h[0].clear();
+  P.wtiles_h[1].clear();
   P.chunks_h.clear();
   for (int g = 0; g < (int)tl.groups.size(); ++g) {
     const Group& G = tl.groups[g];
@@ -1210,6 +1224,28 @@ void build_plan(const TaskList& tl, int es, TcPlan& P, std::vector<ImgJob>& jobs
       P.tasks_h.push_back(c);
     }
     const int nt = (int)idx.size();
+    int dmax = std::max(G.q, G.r);
+    for (int i = 0; i < nt; ++i) dmax = std::max(dmax, std::max(P.tasks_h[base + i].m, P.tasks_h[base + i].n));
+    if (small > 0 && dmax <= small && dmax <= SW_MAXD) {
+      TcTile T;
+      T.g = g;
+      T.row0 = T.col0 = 0;
+      T.nrows = G.q;
+      T.ncols = G.r;
+      T.c0 = (int)P.chunks_h.size();
+      int i = 0;
+      while (i < nt) {
+        const TcTask& a = P.tasks_h[base + i];
+        int j = i + 1;
+        while (j < nt && j - i < 8 && P.tasks_h[base + j].xb == a.xb) ++j;
+        P.chunks_h.push_back({base + i, base + j, a.xb, 0});
+        i = j;
+      }
+      T.c1 = (int)P.chunks_h.size();
+      T.poff = -1;
+      P.wtiles_h[dmax <= 16 ? 0 : 1].push_back(T);
+      continue;
+    }
     for (int r0 = 0; r0 < G.q; r0 += TC_M)
       for (int c0 = 0; c0 < G.r; c0 += TC_NC) {
         TcTile T;
@@ -1286,16 +1322,32 @@ void ws_assign(const std::vector<TcTask>& tasks, const std::vector<TcTile>& tile
   }
 }
 
-void split_plan(const std::vector<TcTask>& tasks, std::vector<TcTile>& tiles, const std::vector<TcChunk>& chunks,
-                std::vector<SplitRed>& reds, long long& psize, int sms, double rounds) {
-  auto ccost = [&](const TcChunk& C, const TcTile& T) { return chunk_cost(tasks, C, T); };
+// estimated cost of one chunk of the small-block warp kernel: its MMAs and a
+// fixed cost per product (metadata, copies, waits)
+double sw_chunk_cost(const std::vector<TcTask>& tasks, const TcChunk& C, const TcTile& T, int es) {
+  const int nprod = es == 2 ? 3 : 1;
+  const int MT = (T.ncols + 15) / 16, QT = (T.nrows + 7) / 8;
+  double s = 0.0;
+  for (int t = C.t0; t < C.t1; ++t) {
+    const TcTask& k = tasks[t];
+    const int NT1 = (k.m + 7) / 8, K1 = k.R.kb / 32, K2 = es == 2 ? (k.m + 15) / 16 : NT1;
+    s += 120.0 + 8.0 * nprod * (MT * NT1 * K1 + MT * QT * K2);
+  }
+  return s;
+}
+
+// cut tiles into pieces of similar estimated cost: the split target is the
+// total cost over (resident units x rounds); pieces costliest first
+template <class Cost>
+void split_plan(std::vector<TcTile>& tiles, const std::vector<TcChunk>& chunks, std::vector<SplitRed>& reds,
+                long long& psize, double units, double rounds, Cost ccost) {
   std::vector<double> tcost(tiles.size(), 0.0);
   double tot = 0;
   for (size_t i = 0; i < tiles.size(); ++i) {
     for (int c = tiles[i].c0; c < tiles[i].c1; ++c) tcost[i] += ccost(chunks[c], tiles[i]);
     tot += tcost[i];
   }
-  const double target = std::max(tot / ((double)TC_CTAS * sms * rounds), 1.0);
+  const double target = std::max(tot / (units * rounds), 1.0);
   std::vector<TcTile> out;
   psize = 0;
   reds.clear();
@@ -1457,6 +1509,59 @@ bool check_plan(const TcPlan& P, const std::vector<TcTile>& tiles, const std::ve
   return true;
 }
 
+// The small-block warp kernel's assumptions, checked for every product of
+// every piece before a launch: whole-block images with the row groups and K
+// widths it indexes, a product's images within its ring, an X image within
+// one X buffer, all copies inside their arenas and 16-byte aligned.
+template <int D>
+bool check_small_plan(const TcPlan& P, const std::vector<TcTile>& tiles, const std::vector<XBlock>& xbs,
+                      const std::vector<Group>& groups, int es, std::string& why) {
+  const int ns = es == 2 ? 2 : 1;
+  auto kbw = [&](int cols) { return ((cols * es + 31) / 32) * 32; };
+  auto fits = [&](const Img& g, long long arena) {
+    return g.off >= 0 && g.off % 16 == 0 && img_bytes(g) % 16 == 0 && g.off + img_bytes(g) <= arena;
+  };
+  for (const TcTile& T : tiles) {
+    const Group& G = groups[T.g];
+    if (T.row0 != 0 || T.col0 != 0 || T.nrows != G.q || T.ncols != G.r || G.q > D || G.r > D ||
+        G.q < 1 || G.r < 1) {
+      why = "small tile shape";
+      return false;
+    }
+    for (int c = T.c0; c < T.c1; ++c) {
+      const TcChunk& C = P.chunks_h[c];
+      for (int t = C.t0; t < C.t1; ++t) {
+        const TcTask& k = P.tasks_h[t];
+        if (k.xb < 0 || k.xb >= (int)xbs.size()) {
+          why = "small: X block index";
+          return false;
+        }
+        const XBlock& X = xbs[k.xb];
+        if (k.m < 1 || k.n < 1 || k.m > D || k.n > D || X.m != k.m || X.n != k.n ||
+            X.img.rg != (k.m + 7) / 8 || X.img.kb != kbw(k.n) || k.L.rg != (G.q + 7) / 8 || k.L.kb != kbw(k.m) ||
+            k.R.rg != (G.r + 7) / 8 || k.R.kb != kbw(k.n)) {
+          why = "small: operand shapes";
+          return false;
+        }
+        if (k.L.off % 256 || k.R.off % 256 || (k.L.off >> 8) > 0xFFFFFFFFll || (k.R.off >> 8) > 0xFFFFFFFFll ||
+            k.xb >= (1 << 20)) {
+          why = "small: product record fields";
+          return false;
+        }
+        if ((img_bytes(k.L) + img_bytes(k.R)) * ns > SwCfg<D>::RING || img_bytes(X.img) * ns > SwCfg<D>::XBUF) {
+          why = "small: staging capacity";
+          return false;
+        }
+        if (!fits(k.L, P.ops_bytes) || !fits(k.R, P.ops_bytes) || !fits(X.img, P.x_bytes)) {
+          why = "small: image copy";
+          return false;
+        }
+      }
+    }
+  }
+  return true;
+}
+
 template <class T>
 T* upload_vec(CudaBackend& be, const std::vector<T>& v, bool& ok) {
   T* p = nullptr;
@@ -1497,12 +1602,49 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
     cudaDeviceGetAttribute(&plan->sms, cudaDevAttrMultiProcessorCount, be.device());
     std::vector<ImgJob> jobs;
     std::vector<XBlock> xbs;
-    build_plan(tl, es, *plan, jobs, xbs);
+    build_plan(tl, es, be.tc_small, *plan, jobs, xbs);
+    if (const char* vp = std::getenv("TNS_VERBOSE_PLAN")) {
+      if (*vp && *vp != '0') {
+        // products and useful flops by the output block's larger dimension
+        // (<= 16, <= 32, larger) and the X block's larger dimension
+        double cnt[3][3] = {}, fl[3][3] = {};
+        auto cls = [](int d) { return d <= 16 ? 0 : d <= 32 ? 1 : 2; };
+        for (const Group& G : tl.groups)
+          for (int t = G.t0; t < G.t1; ++t) {
+            const Task& k = tl.tasks[t];
+            const int a = cls(std::max(G.q, G.r)), b = cls(std::max(k.m, k.n));
+            cnt[a][b] += 1;
+            fl[a][b] += 2.0 * k.r * k.m * k.n + 2.0 * k.q * k.m * k.r;
+          }
+        std::fprintf(stderr, "[tns plan] groups %zu products %zu: tile kernel %zu tiles, small kernels %zu + %zu blocks\n",
+                     tl.groups.size(), tl.tasks.size(), plan->tiles_h.size(), plan->wtiles_h[0].size(),
+                     plan->wtiles_h[1].size());
+        const char* nm[3] = {"<=16", "<=32", ">32"};
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            if (cnt[a][b] > 0)
+              std::fprintf(stderr, "[tns plan]   output %s, X %s: %.0f products, %.3g flops\n", nm[a], nm[b],
+                           cnt[a][b], fl[a][b]);
+      }
+    }
     be.need(plan->ops_bytes * (es == 2 ? 2 : 1) + (long long)plan->tasks_h.size() * (long long)sizeof(TcTask) +
             (long long)plan->chunks_h.size() * (long long)sizeof(TcChunk) +
             (long long)jobs.size() * (long long)sizeof(ImgJob));
     bool ok = true;
     plan->tasks = upload_vec(be, plan->tasks_h, ok);
+    {
+      std::vector<SwRec> recs(plan->tasks_h.size());
+      for (size_t i = 0; i < recs.size(); ++i) {
+        const TcTask& k = plan->tasks_h[i];
+        recs[i].loff = (uint32_t)(k.L.off >> 8);
+        recs[i].roff = (uint32_t)(k.R.off >> 8);
+        recs[i].alpha = k.alpha;
+        recs[i].pk = ((uint32_t)k.xb & 0xFFFFFu) | ((uint32_t)((k.m - 1) & 31) << 20) |
+                     ((uint32_t)((k.n - 1) & 31) << 25);
+      }
+      be.need((long long)recs.size() * (long long)sizeof(SwRec));
+      plan->swrec = upload_vec(be, recs, ok);
+    }
     plan->chunks = upload_vec(be, plan->chunks_h, ok);
     plan->xblocks = upload_vec(be, xbs, ok);
     plan->nxb = (int)xbs.size();
@@ -1556,16 +1698,41 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
   TcVariant& V = plan->var[variant];
   if (!V.planned) {
     std::vector<TcTile> tiles = plan->tiles_h;
+    std::vector<TcTile> wtiles[2] = {plan->wtiles_h[0], plan->wtiles_h[1]};
     std::vector<SplitRed> reds;
     long long psize = 0;
-    split_plan(plan->tasks_h, tiles, plan->chunks_h, reds, psize, plan->sms, kRounds[variant]);
+    const std::vector<TcTask>& tk = plan->tasks_h;
+    split_plan(tiles, plan->chunks_h, reds, psize, (double)TC_CTAS * plan->sms, kRounds[variant],
+               [&](const TcChunk& C, const TcTile& T) { return chunk_cost(tk, C, T); });
+    const double wunits[2] = {(double)SwCfg<16>::WARPS * SwCfg<16>::CTAS * plan->sms,
+                              (double)SwCfg<32>::WARPS * SwCfg<32>::CTAS * plan->sms};
+    for (int w = 0; w < 2; ++w) {
+      // one partial-tile arena: each kernel's partial tiles after the previous ones
+      std::vector<SplitRed> wreds;
+      long long wpsize = 0;
+      split_plan(wtiles[w], plan->chunks_h, wreds, wpsize, wunits[w], kRounds[variant],
+                 [&](const TcChunk& C, const TcTile& T) { return sw_chunk_cost(tk, C, T, es); });
+      for (TcTile& T : wtiles[w])
+        if (T.poff >= 0) T.poff += psize;
+      for (SplitRed& R : wreds) {
+        R.poff += psize;
+        reds.push_back(R);
+      }
+      psize += wpsize;
+    }
     std::string why;
-    if (!check_plan(*plan, tiles, plan->xbs_h, es, why)) {
+    if (!check_plan(*plan, tiles, plan->xbs_h, es, why) ||
+        !check_small_plan<16>(*plan, wtiles[0], plan->xbs_h, tl.groups, es, why) ||
+        !check_small_plan<32>(*plan, wtiles[1], plan->xbs_h, tl.groups, es, why)) {
       be.note(cudaErrorInvalidValue, ("tensor-core plan check failed: " + why).c_str());
       return false;
     }
     bool ok = true;
     V.tiles = upload_vec(be, tiles, ok);
+    for (int w = 0; w < 2; ++w) {
+      V.wtiles[w] = upload_vec(be, wtiles[w], ok);
+      V.nwtiles[w] = (int)wtiles[w].size();
+    }
     V.reds = upload_vec(be, reds, ok);
     if (variant == kWsVariant) {
       std::vector<int> order, off;
@@ -1618,6 +1785,15 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
             "k_tasks_tc_ws shared memory");
     be.note(cudaFuncSetAttribute(k_tasks_tc_ws<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, WsSmem<1>::total),
             "k_tasks_tc_ws shared memory");
+    auto sw_attr = [&](const void* f, int bytes) {
+      be.note(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes), "k_tasks_sw shared memory");
+      be.note(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared),
+              "k_tasks_sw carve-out");
+    };
+    sw_attr((const void*)k_tasks_sw<0, 16>, (int)sizeof(SwWarp<16>) * SwCfg<16>::WARPS);
+    sw_attr((const void*)k_tasks_sw<1, 16>, (int)sizeof(SwWarp<16>) * SwCfg<16>::WARPS);
+    sw_attr((const void*)k_tasks_sw<0, 32>, (int)sizeof(SwWarp<32>) * SwCfg<32>::WARPS);
+    sw_attr((const void*)k_tasks_sw<1, 32>, (int)sizeof(SwWarp<32>) * SwCfg<32>::WARPS);
     attr = true;
   }
   return be.ok();
@@ -1628,7 +1804,7 @@ void enqueue_tasks_tc(CudaBackend& be, DevList& d, const double* xv, double* yv,
   TcPlan* plan = (TcPlan*)d.tc;
   if (!plan || !be.ok()) return;
   TcVariant& V = plan->var[variant];
-  if (V.ntiles == 0) return;
+  if (V.ntiles == 0 && V.nwtiles[0] == 0 && V.nwtiles[1] == 0) return;
   be.note(cudaMemsetAsync(plan->flag, 0, 8 * sizeof(int), be.stream()), "tensor-core flag");
   if (plan->nxb > 0) {
     dim3 gx(plan->nxb, nvec);
@@ -1638,6 +1814,30 @@ void enqueue_tasks_tc(CudaBackend& be, DevList& d, const double* xv, double* yv,
       k_img_x<0><<<gx, 256, 0, be.stream()>>>(plan->xblocks, xv, xs, plan->x_hi, plan->x_lo, plan->x_bytes);
     be.launches++;
     be.note(cudaGetLastError(), "input images");
+  }
+  // small blocks: one warp per (piece, vector), the vectors of a piece in adjacent warps
+  auto launch_sw = [&](auto kern, int warps, int bytes, const TcTile* wt, int nwt) {
+    if (nwt <= 0) return;
+    const long long nw = (long long)nwt * nvec;
+    const unsigned grid = (unsigned)((nw + warps - 1) / warps);
+    kern<<<grid, 32 * warps, bytes, be.stream()>>>(plan->swrec, d.groups, wt, nwt, plan->chunks, plan->ops_hi,
+                                                    plan->ops_lo, plan->x_hi, plan->x_lo, plan->x_bytes,
+                                                    plan->xblocks, yv, ys, plan->flag, V.part, V.psize, nvec,
+                                                    be.tc_wait_ns);
+    be.launches++;
+    be.note(cudaGetLastError(), "k_tasks_sw");
+  };
+  const int b16 = (int)sizeof(SwWarp<16>) * SwCfg<16>::WARPS, b32 = (int)sizeof(SwWarp<32>) * SwCfg<32>::WARPS;
+  if (precision == TNS_TF32) {
+    launch_sw(k_tasks_sw<1, 16>, SwCfg<16>::WARPS, b16, V.wtiles[0], V.nwtiles[0]);
+    launch_sw(k_tasks_sw<1, 32>, SwCfg<32>::WARPS, b32, V.wtiles[1], V.nwtiles[1]);
+  } else {
+    launch_sw(k_tasks_sw<0, 16>, SwCfg<16>::WARPS, b16, V.wtiles[0], V.nwtiles[0]);
+    launch_sw(k_tasks_sw<0, 32>, SwCfg<32>::WARPS, b32, V.wtiles[1], V.nwtiles[1]);
+  }
+  if (V.ntiles == 0) {
+    if (V.nreds > 0) launch_reduce_splits(be, V.reds, V.nreds, d.groups, V.part, V.psize, yv, ys, nvec);
+    return;
   }
   if (variant == kWsVariant) {
     // persistent warp-specialised kernel: one CTA per SM, each over its list
@@ -1678,7 +1878,11 @@ void check_tasks_tc(CudaBackend& be, DevList& d) {
   int h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   cudaMemcpyAsync(h, plan->flag, sizeof(h), cudaMemcpyDeviceToHost, be.stream());
   be.note(cudaStreamSynchronize(be.stream()), "k_tasks_tc");
-  if (h[0]) {
+  if (h[0] && h[2] == 20) {
+    char msg[256];
+    std::snprintf(msg, sizeof(msg), "k_tasks_sw: wait timed out (piece %d, product %d, %d issued)", h[1], h[3], h[4]);
+    be.note(cudaErrorLaunchTimeout, msg);
+  } else if (h[0]) {
     char msg[256];
     std::snprintf(msg, sizeof(msg),
                   "k_tasks_tc: wait timed out (tile piece %d, barrier %d, chunk %d, row offset %d, step %d, phase %d)",
@@ -1691,6 +1895,8 @@ void release_tc_plan(void* p) {
   TcPlan* plan = (TcPlan*)p;
   if (!plan) return;
   for (TcVariant& V : plan->var) {
+    for (TcTile* w : V.wtiles)
+      if (w) dfree(w);
     if (V.ws_order) dfree(V.ws_order);
     if (V.ws_off) dfree(V.ws_off);
     if (V.tiles) dfree(V.tiles);
@@ -1698,6 +1904,7 @@ void release_tc_plan(void* p) {
     if (V.part) dfree(V.part);
   }
   if (plan->tasks) dfree(plan->tasks);
+  if (plan->swrec) dfree(plan->swrec);
   if (plan->chunks) dfree(plan->chunks);
   if (plan->xblocks) dfree(plan->xblocks);
   if (plan->flag) dfree(plan->flag);

@@ -18,7 +18,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_tensor_core_wait_timeout_is_reported_and_context_survives():
+@pytest.mark.parametrize("small", ["0", "32"], ids=["tile-kernel", "small-block-kernel"])
+def test_tensor_core_wait_timeout_is_reported_and_context_survives(small):
     from paper_2305_05581_gb300 import Context, TNS_BF16X3, TNS_FP64, blocks_to_vector, vector_to_blocks
     from paper_2305_05581_gb300.binding import TnsError
     N, n, s2, D, k = 6, 6, 0, 16, 2
@@ -28,10 +29,12 @@ def test_tensor_core_wait_timeout_is_reported_and_context_survives():
     X = synth.random_psi(keys, seed=5)[0]
     ref = O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2).apply(X)
     os.environ["TNS_TC_WAIT_NS"] = "0"
+    os.environ["TNS_TC_SMALL"] = small  # every block of this step is small: "0" keeps it on the tile kernel
     try:
         ctx = Context(device=0, stream=torch.cuda.current_stream().cuda_stream)
     finally:
         del os.environ["TNS_TC_WAIT_NS"]
+        del os.environ["TNS_TC_SMALL"]
     ctx.load_integrals(h, v)
     ctx.mps_import(N, n, s2, D, bonds, sites)
     ctx.build_env(k)
