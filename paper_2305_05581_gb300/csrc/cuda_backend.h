@@ -134,6 +134,10 @@ class CudaBackend : public Backend {
   // tensor-core form (0: every block to the tile kernel; at most 32);
   // environment TNS_TC_SMALL
   int tc_small = 32;
+  // destroy the CUDA graphs captured for a work list (after both streams
+  // have drained): every buffer a graph reads or writes is baked into it, so
+  // they go before any such buffer is freed or reallocated
+  void free_graphs(DevList& d);
   ~CudaBackend() override;
   double* alloc(long long n) override;
   void release(double* p) override;
@@ -213,9 +217,8 @@ class CudaBackend : public Backend {
   bool fork_ready();
   void upload_list(const TaskList& tl, DevList& d);
   void plan_variant(const TaskList& tl, DevList& d, int v);
-  bool ensure_part(FpVariant& f, int nvec);
+  bool ensure_part(DevList& d, FpVariant& f, int nvec);
   void free_list(DevList& d);
-  void free_graphs(DevList& d);
   template <class F>
   void launch_graphed(DevList& d, int key, const double* xv, double* yv, int nvec, long long xs, long long ys,
                       F&& enqueue);

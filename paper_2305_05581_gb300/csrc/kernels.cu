@@ -1105,6 +1105,9 @@ static T* dev_copy(const std::vector<T>& v, CudaBackend& be) {
 }
 
 void CudaBackend::free_graphs(DevList& d) {
+  if (d.graphs.empty()) return;
+  cudaStreamSynchronize(stream_);
+  if (gstream_) cudaStreamSynchronize(gstream_);
   for (auto& kv : d.graphs) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (kv.second.xbuf) dfree(kv.second.xbuf);
@@ -1351,9 +1354,11 @@ void CudaBackend::plan_variant(const TaskList& tl, DevList& d, int v) {
   note(cudaStreamSynchronize(stream_), "schedule upload");
 }
 
-bool CudaBackend::ensure_part(FpVariant& f, int nvec) {
+bool CudaBackend::ensure_part(DevList& d, FpVariant& f, int nvec) {
   if (f.psize == 0 || f.part_nvec >= nvec) return true;
   if (f.part) {
+    // graphs captured with the smaller buffer would write through a freed pointer
+    free_graphs(d);
     cudaStreamSynchronize(stream_);
     if (gstream_) cudaStreamSynchronize(gstream_);
     dfree(f.part);
@@ -1534,7 +1539,7 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
       }
     } else {
       plan_variant(tl, tmp, 1);
-      if (ok() && tmp.tasks && tmp.groups && ensure_part(tmp.fv[1], nvec)) enqueue_fp64(tmp, 1, xv, yv, nvec, xs, ys);
+      if (ok() && tmp.tasks && tmp.groups && ensure_part(tmp, tmp.fv[1], nvec)) enqueue_fp64(tmp, 1, xv, yv, nvec, xs, ys);
     }
     free_list(tmp);
     return;
@@ -1573,7 +1578,7 @@ void CudaBackend::run(const TaskList& tl, const double* xv, double* yv, int nvec
     if (!prepare_tasks_tc(*this, tl, d, nvec, v, precision)) return;
   } else {
     plan_variant(tl, d, v);
-    if (!ok() || !ensure_part(d.fv[v], nvec)) return;
+    if (!ok() || !ensure_part(d, d.fv[v], nvec)) return;
   }
   auto enqueue = [&](const double* x, double* y) {
     if (precision != 0)

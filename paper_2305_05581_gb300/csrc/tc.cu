@@ -1585,6 +1585,7 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
   if (!be.ok()) return false;
   TcPlan* plan = (TcPlan*)d.tc;
   if (plan && (d.tc_gen != tl.gen || plan->precision != precision)) {
+    be.free_graphs(d);  // they hold the plan's buffers
     cudaStreamSynchronize(be.stream());
     release_tc_plan(plan);
     d.tc = nullptr;
@@ -1678,6 +1679,7 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
   }
   if (plan->x_nvec < nvec) {
     if (plan->x_hi) {
+      be.free_graphs(d);  // graphs captured with the smaller images would write through freed pointers
       cudaStreamSynchronize(be.stream());
       dfree(plan->x_hi);
       if (plan->x_lo) dfree(plan->x_lo);
@@ -1753,6 +1755,7 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
   }
   if (V.psize > 0 && V.part_nvec < nvec) {
     if (V.part) {
+      be.free_graphs(d);  // the same for the partial tiles
       cudaStreamSynchronize(be.stream());
       dfree(V.part);
     }

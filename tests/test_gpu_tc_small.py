@@ -55,6 +55,23 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+_ORACLE = {}
+
+
+def _system(N, n, s2, D, k, seed, ms=0):
+    """Integrals, MPS, four input vectors and their oracle products (shared
+    by the precisions and routing limits that use the same system)."""
+    key = (N, n, s2, D, k, seed, ms)
+    if key not in _ORACLE:
+        h, v = synth.integrals(N, 3.0, seed)
+        bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=seed + 1, max_sectors=ms)
+        keys = synth.psi_keys(bonds, N, n, s2, k)
+        Xs = synth.random_psi(keys, seed=seed + 2, nvec=4)
+        dense = O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2)
+        _ORACLE[key] = (h, v, bonds, sites, Xs, [dense.apply(X) for X in Xs])
+    return _ORACLE[key]
+
+
 # sectors of 1..32 states with ragged edges (odd sizes, a single state, full 32)
 # (largest sectors at the step: 3, 8, 20, 32, 31, 32 with 18, edge steps)
 CASES = [(6, 6, 0, 12, 2, 0), (8, 7, 1, 60, 3, 0), (10, 10, 0, 140, 4, 0), (12, 12, 0, 330, 5, 0),
@@ -65,22 +82,17 @@ CASES = [(6, 6, 0, 12, 2, 0), (8, 7, 1, 60, 3, 0), (10, 10, 0, 140, 4, 0), (12, 
 @pytest.mark.parametrize("N,n,s2,D,k,ms", CASES)
 def test_small_kernel_matches_oracle_and_tile_kernel(prec, N, n, s2, D, k, ms):
     from paper_2305_05581_gb300 import blocks_to_vector
-    h, v = synth.integrals(N, 3.0, 60 + N + k)
-    bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=61 + k, max_sectors=ms)
-    keys = synth.psi_keys(bonds, N, n, s2, k)
-    Xs = synth.random_psi(keys, seed=62, nvec=4)
-    dense = O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2)
+    h, v, bonds, sites, Xs, refs = _system(N, n, s2, D, k, 60 + N + k, ms)
     out = {}
     for small in (32, 0):
         ctx = _ctx(small=small)
         out[small] = _products(ctx, h, v, N, n, s2, D, bonds, sites, k, Xs, prec)
         ctx.close()
     y1, y4, desc, length = out[32]
-    for i, X in enumerate(Xs):
-        r = blocks_to_vector(desc, length, dense.apply(X))
+    for i in range(4):
+        r = blocks_to_vector(desc, length, refs[i])
         assert _rel(y4[i * length:(i + 1) * length], r) < TOL[prec]
-    r0 = blocks_to_vector(desc, length, dense.apply(Xs[0]))
-    assert _rel(y1, r0) < TOL[prec]
+    assert _rel(y1, blocks_to_vector(desc, length, refs[0])) < TOL[prec]
     # vector 0 of the four-vector launch equals the one-vector product bitwise
     assert np.array_equal(y4[:length], y1)
     t1, t4 = out[0][0], out[0][1]
@@ -94,17 +106,13 @@ def test_mixed_work_list_both_kernels(prec, limit):
     the small kernel and the rest to the tile kernel in the same product."""
     from paper_2305_05581_gb300 import blocks_to_vector
     N, n, s2, D, k = 12, 12, 0, 330, 5
-    h, v = synth.integrals(N, 3.0, 71)
-    bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=72)
-    keys = synth.psi_keys(bonds, N, n, s2, k)
-    Xs = synth.random_psi(keys, seed=73, nvec=4)
+    h, v, bonds, sites, Xs, refs = _system(N, n, s2, D, k, 71)
     dims = [d for _, d in bonds[k]] + [d for _, d in bonds[k + 2]]
     assert min(dims) <= limit < max(dims)
     ctx = _ctx(small=limit)
     y1, y4, desc, length = _products(ctx, h, v, N, n, s2, D, bonds, sites, k, Xs, prec)
     ctx.close()
-    dense = O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2)
-    r = np.concatenate([blocks_to_vector(desc, length, dense.apply(X)) for X in Xs])
+    r = np.concatenate([blocks_to_vector(desc, length, R) for R in refs])
     assert _rel(y4, r) < TOL[prec]
     assert np.array_equal(y4[:length], y1)
 
@@ -116,13 +124,9 @@ def test_small_kernel_under_every_schedule_variant(variant):
     all agree with the oracle."""
     from paper_2305_05581_gb300 import blocks_to_vector
     N, n, s2, D, k = 10, 10, 0, 140, 4
-    h, v = synth.integrals(N, 3.0, 81)
-    bonds, sites = synth.random_mps(N, n, s2, D, center=k, seed=82)
-    keys = synth.psi_keys(bonds, N, n, s2, k)
-    Xs = synth.random_psi(keys, seed=83, nvec=4)
+    h, v, bonds, sites, Xs, refs = _system(N, n, s2, D, k, 81)
     ctx = _ctx(variant=variant)
     y1, y4, desc, length = _products(ctx, h, v, N, n, s2, D, bonds, sites, k, Xs, 2)
     ctx.close()
-    dense = O3.DenseHeff(O3.Integrals(h, v), bonds, sites, k, n, s2)
-    r = np.concatenate([blocks_to_vector(desc, length, dense.apply(X)) for X in Xs])
+    r = np.concatenate([blocks_to_vector(desc, length, R) for R in refs])
     assert _rel(y4, r) < TOL[2]
