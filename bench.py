@@ -493,7 +493,7 @@ def main():
                        "CUDA-event time (the FP64 refresh products are timed apart: fp64_s in steps_detail)")
     kernel = ("k_tasks_fp64 (grouped triple product, FP64 DFMA) + split reduction" if prec == TNS_FP64 else
               f"k_tasks_tc<{'TF32' if prec == TNS_TF32 else 'BF16x3'}> (tcgen05 grouped triple product) "
-              f"+ split reduction")
+              f"and k_tasks_sw (warp-level tiles for blocks of <= 32 states) + split reduction")
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None,
                 "traffic": TRAFFIC_BYTES_PER_HEFF.get((args.workload, args.precision)),

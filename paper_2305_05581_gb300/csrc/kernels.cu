@@ -1000,12 +1000,13 @@ void CudaBackend::release(double* p) {
 }
 
 // the device memory of a step beyond its catalogues and partial sums: the
-// work list with its schedules, the tensor-core operand images (every distinct
-// operator block, rows padded to 8 and K to 32 bytes, 4 bytes per element)
-// and the vectors of a block Davidson (subspace, products, X images, graph
-// buffers: about 120 vectors)
+// work list with its schedules, the tensor-core product records (48 bytes
+// for the tile kernel, 16 for the small-block kernels, chunk records), the
+// operand images (every distinct operator block, rows padded to 8 and K to
+// 32 bytes, 4 bytes per element) and the vectors of a block Davidson
+// (subspace, products, X images, graph buffers: about 120 vectors)
 long long CudaBackend::step_bytes(const TaskList& tl, long long psi_length) {
-  long long b = (long long)tl.tasks.size() * (long long)sizeof(Task) * 3 / 2 +
+  long long b = (long long)tl.tasks.size() * ((long long)sizeof(Task) * 3 / 2 + 48 + 16 + 8) +
                 (long long)tl.groups.size() * (long long)sizeof(Group) * 4;
   std::unordered_set<uintptr_t> seenL, seenR;
   auto pad = [](long long rows, long long cols) { return ((rows + 7) / 8 * 8) * ((cols * 4 + 31) / 32 * 32); };
