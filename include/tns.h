@@ -44,8 +44,8 @@ extern "C" {
 
 /* arithmetic of the sector GEMMs in tns_heff_apply */
 #define TNS_FP64 0    /* native FP64 (DFMA) */
-#define TNS_TF32 1    /* tcgen05 kind::tf32, FP32 accumulation */
-#define TNS_BF16X3 2  /* split-BF16 hi/lo, 3 products, FP32 accumulation */
+#define TNS_TF32 1    /* TF32 operands, FP32 accumulation (tcgen05 kind::tf32; mma.sync m16n8k8 for blocks <= 32) */
+#define TNS_BF16X3 2  /* split-BF16 hi/lo, 3 products, FP32 accumulation (tcgen05 kind::f16; mma.sync m16n8k16) */
 
 typedef struct tns_ctx tns_ctx;
 
@@ -120,8 +120,12 @@ int tns_psi_layout(tns_ctx* ctx, int site, int* n_blocks, const long long** desc
  * pointers to nvec vectors of `length` doubles each (vector j at offset
  * j*length), in the layout of tns_psi_layout; they must not overlap.  Y is
  * overwritten.  precision: TNS_FP64, TNS_TF32 or TNS_BF16X3 (the latter two
- * run the sector products on tensor cores with FP32 accumulation).  Requires
- * tns_build_env(site).  Runs on the context stream and synchronises it. */
+ * run the sector products on tensor cores with FP32 accumulation: tcgen05
+ * tiles for output blocks above 32 states, warp-level tiles for output blocks
+ * whose dimensions and those of all X blocks they read are at most 32 -- the
+ * limit is the environment variable TNS_TC_SMALL read when the context is
+ * created).  Requires tns_build_env(site).  Runs on the context stream and
+ * synchronises it. */
 int tns_heff_apply(tns_ctx* ctx, int site, const double* X, double* Y, int nvec, int precision);
 
 /* One part of an operator-row split of tns_heff_apply (Sec. "Independent
