@@ -32,11 +32,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <map>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/tns.h"
@@ -132,6 +134,7 @@ struct TcPlan {
   std::vector<TcTile> tiles_h;   // tiles of the tile kernel
   std::vector<TcTile> wtiles_h[2];  // output blocks of the small-block warp kernel (<= 16, <= 32)
   std::vector<TcChunk> chunks_h;
+  std::vector<double> ccost_h;  // estimated cost of each chunk (its tile's kernel), shared by every variant's split
   std::vector<XBlock> xbs_h;
   TcVariant var[kNumVariants];
   int sms = 152;
@@ -1172,18 +1175,72 @@ Img make_img(int rows, int cols, int es, long long& arena) {
 // chunks of products sharing X with (products x padded tile columns) <= 128.
 // A group whose block and X blocks all have dimensions <= small is one tile
 // of the small-block warp kernel instead (its chunks only delimit pieces).
+// operand image key: (source block, stored transposed, rows, cols of op(M))
+struct ImgKey {
+  const double* src;
+  int trans, rows, cols;
+  bool operator==(const ImgKey& o) const {
+    return src == o.src && trans == o.trans && rows == o.rows && cols == o.cols;
+  }
+};
+struct ImgKeyHash {
+  size_t operator()(const ImgKey& k) const {
+    unsigned long long h = (unsigned long long)(uintptr_t)k.src * 0x9E3779B97F4A7C15ull;
+    h ^= ((unsigned long long)k.trans << 62) ^ ((unsigned long long)(unsigned)k.rows << 32) ^ (unsigned)k.cols;
+    h ^= h >> 29;
+    h *= 0xBF58476D1CE4E5B9ull;
+    return (size_t)(h ^ (h >> 32));
+  }
+};
+
+// stable sort of (X offset, product) pairs by X offset: least-significant-digit
+// radix sort, 8 bits per pass over the bits the largest offset uses (a
+// group's products number thousands, its X offsets fit in ~20 bits)
+void stable_sort_by_x(std::vector<std::pair<size_t, int>>& v, std::vector<std::pair<size_t, int>>& tmp) {
+  const size_t n = v.size();
+  if (n < 64) {
+    std::stable_sort(v.begin(), v.end(),
+                     [](const std::pair<size_t, int>& a, const std::pair<size_t, int>& b) { return a.first < b.first; });
+    return;
+  }
+  size_t mx = 0;
+  for (const auto& e : v) mx = std::max(mx, e.first);
+  tmp.resize(n);
+  for (int shift = 0; shift < 64 && (mx >> shift) != 0; shift += 8) {
+    size_t cnt[257] = {};
+    for (const auto& e : v) ++cnt[((e.first >> shift) & 255) + 1];
+    for (int b = 0; b < 256; ++b) cnt[b + 1] += cnt[b];
+    for (const auto& e : v) tmp[cnt[(e.first >> shift) & 255]++] = e;
+    v.swap(tmp);
+  }
+}
+
 void build_plan(const TaskList& tl, int es, int small, TcPlan& P, std::vector<ImgJob>& jobs,
                 std::vector<XBlock>& xbs) {
-  std::map<std::tuple<const double*, int, int, int>, Img> imgs;  // (src, trans, rows, cols)
-  std::map<long long, int> xidx;
+  // hashed lookups (two per product) with a one-entry memo per operand:
+  // products of a group come X-ordered and often repeat an operator block;
+  // images and X blocks get their offsets in first-use order
+  std::unordered_map<ImgKey, Img, ImgKeyHash> imgs;
+  std::unordered_map<long long, int> xidx;
+  imgs.reserve(1 << 16);
+  xidx.reserve(1 << 12);
   long long arena = 0, xarena = 0;
-  auto image = [&](const double* src, int trans, int rows, int cols) {
-    auto key = std::make_tuple(src, trans, rows, cols);
+  ImgKey lastk[2] = {{nullptr, -1, -1, -1}, {nullptr, -1, -1, -1}};
+  Img lastg[2] = {};
+  auto image = [&](int side, const double* src, int trans, int rows, int cols) {
+    const ImgKey key{src, trans, rows, cols};
+    if (key == lastk[side]) return lastg[side];
     auto it = imgs.find(key);
-    if (it != imgs.end()) return it->second;
-    Img g = make_img(rows, cols, es, arena);
-    imgs[key] = g;
-    jobs.push_back({src, rows, cols, trans, g});
+    Img g;
+    if (it != imgs.end()) {
+      g = it->second;
+    } else {
+      g = make_img(rows, cols, es, arena);
+      imgs.emplace(key, g);
+      jobs.push_back({src, rows, cols, trans, g});
+    }
+    lastk[side] = key;
+    lastg[side] = g;
     return g;
   };
   P.tasks_h.clear();
@@ -1191,36 +1248,43 @@ void build_plan(const TaskList& tl, int es, int small, TcPlan& P, std::vector<Im
   P.wtiles_h[0].clear();
   P.wtiles_h[1].clear();
   P.chunks_h.clear();
+  P.tasks_h.reserve(tl.tasks.size());
+  std::vector<std::pair<size_t, int>> idx, tmp;  // (X offset, product): sorted by X, stable
+  long long last_xo = -1;
+  int last_xb = -1;
   for (int g = 0; g < (int)tl.groups.size(); ++g) {
     const Group& G = tl.groups[g];
-    std::vector<int> idx;
-    for (int t = G.t0; t < G.t1; ++t) idx.push_back(t);
-    std::stable_sort(idx.begin(), idx.end(),
-                     [&](int a, int b) { return (size_t)tl.tasks[a].X < (size_t)tl.tasks[b].X; });
+    idx.clear();
+    for (int t = G.t0; t < G.t1; ++t) idx.push_back({(size_t)tl.tasks[t].X, t});
+    stable_sort_by_x(idx, tmp);
     const int base = (int)P.tasks_h.size();
-    for (int t : idx) {
-      const Task& k = tl.tasks[t];
+    for (const auto& e : idx) {
+      const Task& k = tl.tasks[e.second];
       TcTask c;
       c.alpha = (float)k.alpha;
       c.m = k.m;
       c.n = k.n;
       // op(L): q x m ; op(R): r x n ; identities become identity images
-      c.L = (k.flags & TF_LI) ? image(nullptr, 0, k.q, k.m) : image(k.L, (k.flags & TF_LT) ? 1 : 0, k.q, k.m);
-      c.R = (k.flags & TF_RI) ? image(nullptr, 0, k.r, k.n) : image(k.R, (k.flags & TF_RT) ? 1 : 0, k.r, k.n);
+      c.L = (k.flags & TF_LI) ? image(0, nullptr, 0, k.q, k.m) : image(0, k.L, (k.flags & TF_LT) ? 1 : 0, k.q, k.m);
+      c.R = (k.flags & TF_RI) ? image(1, nullptr, 0, k.r, k.n) : image(1, k.R, (k.flags & TF_RT) ? 1 : 0, k.r, k.n);
       const long long xo = (long long)(size_t)k.X;
-      auto it = xidx.find(xo);
-      if (it == xidx.end()) {
-        XBlock B;
-        B.src = xo;
-        B.m = k.m;
-        B.n = k.n;
-        B.img = make_img(k.m, k.n, es, xarena);
-        xidx[xo] = (int)xbs.size();
-        xbs.push_back(B);
-        c.xb = (int)xbs.size() - 1;
-      } else {
-        c.xb = it->second;
+      if (xo != last_xo) {
+        auto it = xidx.find(xo);
+        if (it == xidx.end()) {
+          XBlock B;
+          B.src = xo;
+          B.m = k.m;
+          B.n = k.n;
+          B.img = make_img(k.m, k.n, es, xarena);
+          xidx.emplace(xo, (int)xbs.size());
+          xbs.push_back(B);
+          last_xb = (int)xbs.size() - 1;
+        } else {
+          last_xb = it->second;
+        }
+        last_xo = xo;
       }
+      c.xb = last_xb;
       P.tasks_h.push_back(c);
     }
     const int nt = (int)idx.size();
@@ -1334,6 +1398,16 @@ double sw_chunk_cost(const std::vector<TcTask>& tasks, const TcChunk& C, const T
     s += 120.0 + 8.0 * nprod * (MT * NT1 * K1 + MT * QT * K2);
   }
   return s;
+}
+
+// the estimated cost of every chunk, once per plan (chunks belong to one tile each)
+void plan_chunk_costs(TcPlan& P, int es) {
+  P.ccost_h.assign(P.chunks_h.size(), 0.0);
+  for (const TcTile& T : P.tiles_h)
+    for (int c = T.c0; c < T.c1; ++c) P.ccost_h[c] = chunk_cost(P.tasks_h, P.chunks_h[c], T);
+  for (int w = 0; w < 2; ++w)
+    for (const TcTile& T : P.wtiles_h[w])
+      for (int c = T.c0; c < T.c1; ++c) P.ccost_h[c] = sw_chunk_cost(P.tasks_h, P.chunks_h[c], T, es);
 }
 
 // cut tiles into pieces of similar estimated cost: the split target is the
@@ -1604,6 +1678,7 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
     std::vector<ImgJob> jobs;
     std::vector<XBlock> xbs;
     build_plan(tl, es, be.tc_small, *plan, jobs, xbs);
+    plan_chunk_costs(*plan, es);
     if (const char* vp = std::getenv("TNS_VERBOSE_PLAN")) {
       if (*vp && *vp != '0') {
         // products and useful flops by the output block's larger dimension
@@ -1628,12 +1703,17 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
                            cnt[a][b], fl[a][b]);
       }
     }
-    be.need(plan->ops_bytes * (es == 2 ? 2 : 1) + (long long)plan->tasks_h.size() * (long long)sizeof(TcTask) +
+    // each kernel's product records go up only if that kernel has blocks
+    const bool any_tile = !plan->tiles_h.empty();
+    const bool any_small = !plan->wtiles_h[0].empty() || !plan->wtiles_h[1].empty();
+    be.need(plan->ops_bytes * (es == 2 ? 2 : 1) +
+            (long long)plan->tasks_h.size() *
+                ((any_tile ? (long long)sizeof(TcTask) : 0) + (any_small ? (long long)sizeof(SwRec) : 0)) +
             (long long)plan->chunks_h.size() * (long long)sizeof(TcChunk) +
             (long long)jobs.size() * (long long)sizeof(ImgJob));
     bool ok = true;
-    plan->tasks = upload_vec(be, plan->tasks_h, ok);
-    {
+    if (any_tile) plan->tasks = upload_vec(be, plan->tasks_h, ok);
+    if (any_small) {
       std::vector<SwRec> recs(plan->tasks_h.size());
       for (size_t i = 0; i < recs.size(); ++i) {
         const TcTask& k = plan->tasks_h[i];
@@ -1643,7 +1723,6 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
         recs[i].pk = ((uint32_t)k.xb & 0xFFFFFu) | ((uint32_t)((k.m - 1) & 31) << 20) |
                      ((uint32_t)((k.n - 1) & 31) << 25);
       }
-      be.need((long long)recs.size() * (long long)sizeof(SwRec));
       plan->swrec = upload_vec(be, recs, ok);
     }
     plan->chunks = upload_vec(be, plan->chunks_h, ok);
@@ -1703,17 +1782,17 @@ bool prepare_tasks_tc(CudaBackend& be, const TaskList& tl, DevList& d, int nvec,
     std::vector<TcTile> wtiles[2] = {plan->wtiles_h[0], plan->wtiles_h[1]};
     std::vector<SplitRed> reds;
     long long psize = 0;
-    const std::vector<TcTask>& tk = plan->tasks_h;
-    split_plan(tiles, plan->chunks_h, reds, psize, (double)TC_CTAS * plan->sms, kRounds[variant],
-               [&](const TcChunk& C, const TcTile& T) { return chunk_cost(tk, C, T); });
+    const std::vector<TcChunk>& ch = plan->chunks_h;
+    const std::vector<double>& cc = plan->ccost_h;
+    auto cost = [&](const TcChunk& C, const TcTile&) { return cc[&C - ch.data()]; };
+    split_plan(tiles, plan->chunks_h, reds, psize, (double)TC_CTAS * plan->sms, kRounds[variant], cost);
     const double wunits[2] = {(double)SwCfg<16>::WARPS * SwCfg<16>::CTAS * plan->sms,
                               (double)SwCfg<32>::WARPS * SwCfg<32>::CTAS * plan->sms};
     for (int w = 0; w < 2; ++w) {
       // one partial-tile arena: each kernel's partial tiles after the previous ones
       std::vector<SplitRed> wreds;
       long long wpsize = 0;
-      split_plan(wtiles[w], plan->chunks_h, wreds, wpsize, wunits[w], kRounds[variant],
-                 [&](const TcChunk& C, const TcTile& T) { return sw_chunk_cost(tk, C, T, es); });
+      split_plan(wtiles[w], plan->chunks_h, wreds, wpsize, wunits[w], kRounds[variant], cost);
       for (TcTile& T : wtiles[w])
         if (T.poff >= 0) T.poff += psize;
       for (SplitRed& R : wreds) {

@@ -221,18 +221,24 @@ bool run(unsigned seed, int small, int es) {
     for (int t = G.t0 + 1; t < G.t1; ++t)
       CHECK(xbs[P.tasks_h[t - 1].xb].src <= xbs[P.tasks_h[t].xb].src, "products not ordered by X block");
   // splits of every variant, and the launch checks
+  // chunk costs computed once per plan, as the launch path does, equal the
+  // direct estimates of each chunk's kernel
+  plan_chunk_costs(P, es);
   const std::vector<TcTask>& tk = P.tasks_h;
+  for (const TcTile& T : P.tiles_h)
+    for (int c = T.c0; c < T.c1; ++c) CHECK(P.ccost_h[c] == chunk_cost(tk, P.chunks_h[c], T), "chunk cost");
+  for (int w = 0; w < 2; ++w)
+    for (const TcTile& T : P.wtiles_h[w])
+      for (int c = T.c0; c < T.c1; ++c) CHECK(P.ccost_h[c] == sw_chunk_cost(tk, P.chunks_h[c], T, es), "chunk cost");
+  auto cost = [&](const TcChunk& C, const TcTile&) { return P.ccost_h[&C - P.chunks_h.data()]; };
   size_t nsplit = 0;  // split tiles at rounds 4
   for (double rounds : {1.0, 2.0, 4.0}) {
     std::vector<TcTile> tiles = P.tiles_h, w16 = P.wtiles_h[0], w32 = P.wtiles_h[1];
     std::vector<SplitRed> r0, r1, r2;
     long long p0 = 0, p1 = 0, p2 = 0;
-    split_plan(tiles, P.chunks_h, r0, p0, (double)TC_CTAS * 152, rounds,
-               [&](const TcChunk& C, const TcTile& T) { return chunk_cost(tk, C, T); });
-    split_plan(w16, P.chunks_h, r1, p1, (double)SwCfg<16>::WARPS * SwCfg<16>::CTAS * 152, rounds,
-               [&](const TcChunk& C, const TcTile& T) { return sw_chunk_cost(tk, C, T, es); });
-    split_plan(w32, P.chunks_h, r2, p2, (double)SwCfg<32>::WARPS * SwCfg<32>::CTAS * 152, rounds,
-               [&](const TcChunk& C, const TcTile& T) { return sw_chunk_cost(tk, C, T, es); });
+    split_plan(tiles, P.chunks_h, r0, p0, (double)TC_CTAS * 152, rounds, cost);
+    split_plan(w16, P.chunks_h, r1, p1, (double)SwCfg<16>::WARPS * SwCfg<16>::CTAS * 152, rounds, cost);
+    split_plan(w32, P.chunks_h, r2, p2, (double)SwCfg<32>::WARPS * SwCfg<32>::CTAS * 152, rounds, cost);
     if (!check_split(P.tiles_h, tiles, r0, p0) || !check_split(P.wtiles_h[0], w16, r1, p1) ||
         !check_split(P.wtiles_h[1], w32, r2, p2))
       return false;
